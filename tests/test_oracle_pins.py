@@ -1,0 +1,343 @@
+"""The Monte Carlo oracle against what the paper and the mathematics fix.
+
+* Poisson kernel of the disc / ball (paper Sec. 1) integrated per cell.
+* Concentric annulus and shell totals (ln r / ln a, (1/r - 1)/(1/a - 1)) and
+  the annulus' per-arc Fourier series.
+* Exact recovery of K-harmonic polynomials: u(X_n) is a bounded martingale of
+  the chain (Eq. (wos chain)), so E[u(X_{N_eps})] = u(x) with no eps bias
+  (paper Eq. (2D-sol1)-(2D-sol4), (3D-sol1)).
+* Row sums equal N exactly (mu_x is a probability measure).
+* Rotation / reflection symmetry in law.
+* Walk-length law E[N_eps] = O(log 1/eps) and the convex tail bound
+  P(N_eps > M) <= (1 - 1/(4d))^M sqrt(dist / eps) (Sec. 4.2.1).
+* Finite differences of div(K grad u) = 0 on a fine grid of the square
+  (brute force, covers the anisotropic K).
+* The paper's printed averaged harmonic measure 0.1126 of the perforated disc
+  (Sec. 1 / Ex. 5.4).
+
+The statistical band of an entry is 4 sqrt(p (1 - p) / N) + beta(eps) with
+beta(eps) = 2 (2/pi) rho_max eps (1 + ln(1/eps)), rho_max the largest density.
+"""
+import math
+from pathlib import Path
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+from scipy import stats
+
+from oracle import closed_forms as CF
+from oracle import oracle as O
+from paper_2409_03686_gb300 import workloads as W
+
+GOLDEN = Path(__file__).resolve().parent / "golden"
+
+
+from stats_util import beta_eps as beta
+from stats_util import check_band
+
+
+def band(p, N, b):
+    return 4 * np.sqrt(np.maximum(p * (1 - p), 1.0 / N) / N) + b
+
+
+def test_golden_disc_arcs_match_closed_form():
+    rows = [l.split() for l in open(GOLDEN / "poisson_disc_arcs.txt")
+            if not l.startswith("#")]
+    stored = np.array([float(r[1]) for r in rows])
+    np.testing.assert_allclose(stored, CF.disc_row((0.5, 0.0), 32), atol=1e-14)
+    # independent quadrature of the kernel itself
+    from scipy.integrate import quad
+    for j in (0, 3, 16, 29):
+        a, b = 2 * math.pi * j / 32, 2 * math.pi * (j + 1) / 32
+        val, _ = quad(lambda t: (1 - 0.25) / (2 * math.pi * (1.25 - math.cos(t))), a, b,
+                      epsabs=1e-14)
+        assert stored[j] == pytest.approx(val, abs=1e-12)
+    assert stored[16:].sum() == pytest.approx(0.5, abs=1e-14)
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_disc_poisson_kernel_all_rows(fp64):
+    inst = W.disc_config(N=20_000, fp64=fp64)
+    C, U, steps = O.build_counts(inst)
+    assert (C.sum(1).astype(np.int64) + U == inst.N).all()
+    A = C / inst.N
+    rho_max = 0.75 / (2 * math.pi * 0.25)
+    P = np.array([CF.disc_row(x, 32) for x in inst.points])
+    ok, info = check_band(A, P, inst.N, beta(inst.eps, rho_max))
+    assert ok, info
+
+
+def test_disc_row_chi2_goodness_of_fit():
+    inst = W.disc_config(N=20_000)
+    C, U, _ = O.build_counts(inst)
+    pv = []
+    for i, x in enumerate(inst.points):
+        p = CF.disc_row(x, 32)
+        pv.append(stats.chisquare(C[i], p * inst.N).pvalue)
+    assert min(pv) > 1e-3 / len(pv)  # Bonferroni over rows
+
+
+def test_ball_poisson_kernel_patches():
+    inst = W.ball_config(N=20_000, n_points=6, nb=4, ns=6, K=np.eye(3), eps=1e-4)
+    C, U, _ = O.build_counts(inst)
+    A = C / inst.N
+    P = np.array([CF.ball_patch_row(x, 4, 6) for x in inst.points])
+    np.testing.assert_allclose(P.sum(1), 1.0, atol=1e-10)
+    r = np.linalg.norm(inst.points, axis=1).max()
+    rho_max = (1 - r * r) / (4 * math.pi * (1 - r) ** 3)
+    ok, info = check_band(A, P, inst.N, beta(inst.eps, rho_max))
+    assert ok, info
+
+
+def test_annulus_and_shell_inner_measure():
+    a = 0.5
+    inst = W.annulus_config(N=40_000, K=np.eye(2), m_each=8, grid=2)
+    pts = np.array([[0.95, 0.0], [0.0, -0.7], [0.4, 0.4]])
+    inst = inst.replace(points=pts, eps=1e-5)
+    C, U, _ = O.build_counts(inst)
+    A = C / inst.N
+    for i, x in enumerate(pts):
+        r = np.linalg.norm(x)
+        p_in = CF.annulus_inner_total(r, a)
+        assert abs(A[i, 8:].sum() - p_in) <= band(p_in, inst.N, 0), i
+        row = CF.annulus_arc_measures(x, a, 8, 8)
+        assert row.sum() == pytest.approx(1.0, abs=1e-10)
+        assert row[8:].sum() == pytest.approx(p_in, abs=1e-10)
+        ok, info = check_band(A[i], row, inst.N, beta(inst.eps, 2.0))
+        assert ok, (i, info)
+    # the printed pin values of the survey's closed-form table
+    assert CF.annulus_inner_total(0.95, 0.5) == pytest.approx(0.0740005814, abs=1e-10)
+    assert CF.annulus_inner_total(0.95, 0.2) == pytest.approx(0.0318703157, abs=1e-10)
+    assert CF.shell_inner_total(0.95, 0.5) == pytest.approx(0.0526315789, abs=1e-10)
+    shell = W.shell_config(N=20_000, nb=2, ns=2, eps=1e-4)
+    pts3 = np.array([[0.95, 0.0, 0.0], [0.0, 0.0, -0.7]])
+    shell = shell.replace(points=pts3)
+    C3, U3, _ = O.build_counts(shell)
+    for i, x in enumerate(pts3):
+        p_in = CF.shell_inner_total(np.linalg.norm(x), 0.5)
+        assert abs(C3[i, 4:].sum() / shell.N - p_in) <= band(p_in, shell.N, 2e-3), i
+
+
+def _harmonic_check(inst, u, n_walks):
+    i = np.repeat(np.arange(inst.M_D), n_walks)
+    k = np.tile(np.arange(n_walks), inst.M_D)
+    xe, el, ns = O.walks(inst, i, k)
+    assert (el >= 0).all()
+    vals = u(xe).reshape(inst.M_D, n_walks)
+    mean = vals.mean(1)
+    sd = vals.std(1, ddof=1)
+    err = np.abs(mean - u(inst.points))
+    assert (err <= 4.5 * sd / math.sqrt(n_walks) + 1e-12).all(), err / (sd / math.sqrt(n_walks))
+
+
+@pytest.mark.parametrize("fp64", [False, True])
+def test_exact_recovery_of_harmonic_polynomials_2d(fp64):
+    # Eq. (2D-sol2) and (2D-sol3); Eq. (2D-sol1) is not harmonic as printed
+    # (see test_paper_solutions_harmonicity) and is not a martingale pin.
+    sols = [SOL2, SOL3]
+    sq = W.square_config(N=4000, grid=3, K=np.eye(2)).replace(fp64=fp64, eps=1e-4)
+    for u in sols:
+        _harmonic_check(sq, u, 4000)
+    # anisotropic: the cubic of Eq. (2D-sol4) for the paper's K and for the
+    # benchmark K, on the annulus and the L-shape
+    for K in (np.array([[1.0, 0.3], [0.3, 0.4]]), W.K_CONFIG2):
+        u = W.k_harmonic_cubic(K)
+        ann = W.annulus_config(N=4000, grid=3, K=K).replace(fp64=fp64, eps=1e-4)
+        _harmonic_check(ann, u, 4000)
+        L = W.lshape_config(N=4000, n_points=6, K=K).replace(fp64=fp64)
+        _harmonic_check(L, u, 4000)
+
+
+SOL1 = lambda x: 0.75 * (1 - x[..., 0] ** 2) + 0.25 * x[..., 1] ** 3  # noqa: E731
+SOL2 = lambda x: (-x[..., 0] ** 3 / 3 - x[..., 0] ** 2 * x[..., 1]  # noqa: E731
+                  + x[..., 0] * x[..., 1] ** 2 + x[..., 1] ** 3 / 3)
+SOL3 = lambda x: x[..., 0] ** 2 - x[..., 1] ** 2  # noqa: E731
+
+
+def _laplacian(u, x, h=1e-3, K=None):
+    d = len(x)
+    K = np.eye(d) if K is None else K
+    H = np.zeros((d, d))
+    for a in range(d):
+        for b in range(d):
+            ea, eb = np.eye(d)[a] * h, np.eye(d)[b] * h
+            H[a, b] = (u(x + ea + eb) - u(x + ea - eb) - u(x - ea + eb)
+                       + u(x - ea - eb)) / (4 * h * h)
+    return float(np.sum(K * H))
+
+
+def test_paper_solutions_harmonicity():
+    """Eq. (2D-sol2), (2D-sol3) are harmonic; Eq. (2D-sol1) = (3D-sol3) as
+    printed, 3/4 (1 - x1^2) + 1/4 x2^3, has Laplacian 1.5 (x2 - 1) != 0, so it
+    is not a solution of the paper's problem and cannot pin the chain."""
+    x = np.array([0.1, -0.3])
+    assert abs(_laplacian(SOL2, x)) < 1e-6
+    assert abs(_laplacian(SOL3, x)) < 1e-6
+    assert _laplacian(SOL1, x) == pytest.approx(1.5 * (x[1] - 1), abs=1e-6)
+
+
+def test_harmonic_cubic_is_k_harmonic():
+    # check div(K grad u) = 0 symbolically through finite second differences
+    rng = np.random.default_rng(3)
+    for K in (W.K_CONFIG2, np.diag([1.0, 2.0, 4.0]), W.random_spd(rng, 3, 0.5, 4)):
+        u = W.k_harmonic_cubic(K)
+        d = K.shape[0]
+        x = rng.uniform(-0.5, 0.5, d)
+        h = 1e-3
+        H = np.zeros((d, d))
+        for a in range(d):
+            for b in range(d):
+                ea, eb = np.eye(d)[a] * h, np.eye(d)[b] * h
+                H[a, b] = (u(x + ea + eb) - u(x + ea - eb) - u(x - ea + eb)
+                           + u(x - ea - eb)) / (4 * h * h)
+        assert abs(np.sum(K * H)) < 1e-6
+
+
+def test_exact_recovery_3d():
+    rng = np.random.default_rng(6)
+    for K in (np.diag([1.0, 2.0, 4.0]), W.random_spd(rng, 3, 0.5, 4.0)):
+        u = W.k_harmonic_cubic(K)
+        ball = W.ball_config(N=3000, n_points=4, nb=4, ns=4, K=K)
+        _harmonic_check(ball, u, 3000)
+        cube = W.cube_config(N=3000, n_points=4, n_face=2, K=K)
+        _harmonic_check(cube, u, 3000)
+    # 1/|x| (Eq. (3D-sol2)) on the shell with K = I
+    shell = W.shell_config(N=3000, nb=2, ns=2).replace(points=W.bauer_spiral(4, 0.8))
+    _harmonic_check(shell, lambda x: 1 / np.linalg.norm(x, axis=-1), 3000)
+
+
+def test_rotation_symmetry_of_the_disc():
+    inst = W.disc_config(N=20_000)
+    C, _, _ = O.build_counts(inst)
+    for k in range(1, 32, 5):
+        shifted = np.roll(C[k], -k)  # row k seen from row 0's frame
+        tab = np.stack([C[0], shifted])
+        tab = tab[:, tab.sum(0) > 0]
+        assert stats.chi2_contingency(tab)[1] > 1e-4
+
+
+def test_reflection_symmetry_of_the_square():
+    sq = W.square_config(N=40_000, n_side=4, K=np.eye(2), eps=1e-4)
+    pts = np.array([[0.2, -0.1], [-0.2, -0.1]])  # mirror images in x = 0
+    C, _, _ = O.build_counts(sq.replace(points=pts))
+    # reflection x -> -x maps bottom cell c to 3 - c, right edge to left edge
+    # (reversed), top cell c to 3 - c
+    perm = np.array([3, 2, 1, 0, 15, 14, 13, 12, 11, 10, 9, 8, 7, 6, 5, 4])
+    tab = np.stack([C[0], C[1][perm]])
+    tab = tab[:, tab.sum(0) > 0]
+    assert stats.chi2_contingency(tab)[1] > 1e-4
+
+
+def test_walk_length_law():
+    # (from the centre the first sphere is the whole disc: one step always)
+    base = W.disc_config(N=4000).replace(points=np.array([[0.3, 0.2]]))
+    dist0 = 1.0 - math.hypot(0.3, 0.2)
+    eps_list = [1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7]
+    means = []
+    for e in eps_list:
+        inst = base.replace(eps=e)
+        i = np.zeros(inst.N, int)
+        xe, el, ns = O.walks(inst, i, np.arange(inst.N))
+        means.append(ns.mean())
+        # convex tail bound (Sec. 4.2.1), d = 2
+        for M in (20, 40, 60, 80):
+            bound = (1 - 1 / 8) ** M * math.sqrt(dist0 / e)
+            assert (ns > M).mean() <= bound + 4 * math.sqrt(max(bound, 1e-4) / inst.N)
+    L = np.log(1 / np.array(eps_list))
+    slope, icpt, r, _, _ = stats.linregress(L, means)
+    assert slope > 0 and r > 0.995, (slope, r, means)
+
+
+def _fd_side_measure(K, n=128):
+    """Discrete harmonic measure of the bottom side of [-1/2, 1/2]^2 for
+    div(K grad u) = 0: 9-point stencil (centred mixed derivative), Dirichlet
+    data 1 on the bottom side, 0 elsewhere, corners 1/2."""
+    h = 1.0 / n
+    m = n - 1
+    idx = -np.ones((n + 1, n + 1), int)
+    idx[1:n, 1:n] = np.arange(m * m).reshape(m, m)
+    g = np.zeros((n + 1, n + 1))
+    g[:, 0] = 1.0  # bottom (second index = y)
+    g[0, 0] = g[n, 0] = 0.5
+    k11, k12, k22 = K[0, 0], K[0, 1], K[1, 1]
+    stencil = {(1, 0): k11, (-1, 0): k11, (0, 1): k22, (0, -1): k22,
+               (1, 1): k12 / 2, (-1, -1): k12 / 2, (1, -1): -k12 / 2, (-1, 1): -k12 / 2}
+    rows, cols, vals = [], [], []
+    rhs = np.zeros(m * m)
+    for i in range(1, n):
+        for j in range(1, n):
+            r = idx[i, j]
+            rows.append(r)
+            cols.append(r)
+            vals.append(-2 * (k11 + k22))
+            for (di, dj), w in stencil.items():
+                ii, jj = i + di, j + dj
+                if idx[ii, jj] >= 0:
+                    rows.append(r)
+                    cols.append(idx[ii, jj])
+                    vals.append(w)
+                else:
+                    rhs[r] -= w * g[ii, jj]
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(m * m, m * m))
+    u = spla.spsolve(A, rhs)
+    full = g.copy()
+    full[1:n, 1:n] = u.reshape(m, m)
+
+    def at(x, y):  # bilinear interpolation, x, y in [-1/2, 1/2]
+        fx, fy = (x + 0.5) * n, (y + 0.5) * n
+        i0, j0 = int(fx), int(fy)
+        tx, ty = fx - i0, fy - j0
+        return ((1 - tx) * (1 - ty) * full[i0, j0] + tx * (1 - ty) * full[i0 + 1, j0]
+                + (1 - tx) * ty * full[i0, j0 + 1] + tx * ty * full[i0 + 1, j0 + 1])
+    return at
+
+
+def test_finite_difference_brute_force_square():
+    pts = np.array([[0.0, 0.0], [-0.2, -0.3], [0.25, 0.1], [0.3, -0.2], [-0.1, 0.3]])
+    for K in (np.eye(2), W.K_CONFIG2):
+        fd = _fd_side_measure(K, n=128)
+        if np.allclose(K, np.eye(2)):
+            # the FD solver itself against the sine series (K = I)
+            for x, y in pts:
+                assert fd(x, y) == pytest.approx(CF.square_side_measure(x + 0.5, y + 0.5),
+                                                 abs=3e-4)
+            assert CF.square_side_measure(0.5, 0.5) == pytest.approx(0.25, abs=1e-12)
+        sq = W.square_config(N=100_000, n_side=4, K=K, eps=1e-5).replace(points=pts)
+        C, U, _ = O.build_counts(sq)
+        mu_bottom = C[:, :4].sum(1) / sq.N
+        for q, (x, y) in enumerate(pts):
+            p = fd(x, y)
+            assert abs(mu_bottom[q] - p) <= band(p, sq.N, 1e-3), (K, q, mu_bottom[q], p)
+
+
+def test_printed_value_perforated_disc():
+    vals = {}
+    for line in open(GOLDEN / "paper_printed_values.txt"):
+        if line.strip() and not line.startswith("#"):
+            key, v, _ = line.split()
+            vals[key] = float(v)
+    inst = W.perforated_disc_config(N=20_000, eps=1e-6, m_outer=10, m_hole=2)
+    C, U, _ = O.build_counts(inst)
+    g1 = inst.partition.gamma1.astype(bool)
+    mu1 = C[:, g1].sum(1) / inst.N
+    avg = mu1.mean()
+    # four printed digits: a sanity band, not parity
+    assert abs(avg - vals["avg_mu_gamma1_on_dotted_circle"]) < 2e-3, avg
+    assert abs((1 - avg) - vals["avg_mu_gamma0_on_dotted_circle"]) < 2e-3
+    # the single-pole value 0.0961 lies within the range over the circle
+    assert mu1.min() - 2e-3 <= vals["one_pole_mu_gamma1"] <= mu1.max() + 2e-3
+
+
+def test_row_sums_and_step_cap():
+    inst = W.square_config(N=2000, grid=2).replace(step_cap=5)
+    C, U, steps = O.build_counts(inst)
+    assert (C.sum(1).astype(np.int64) + U == inst.N).all()
+    assert U.sum() > 0
+    # resuming over [k0, k1) ranges adds up to the uninterrupted build
+    C1, U1, s1 = O.build_counts(inst, 0, 700)
+    C2, U2, s2 = O.build_counts(inst, 700, 2000)
+    np.testing.assert_array_equal(C1 + C2, C)
+    np.testing.assert_array_equal(U1 + U2, U)
+    assert s1 + s2 == steps
