@@ -1,0 +1,260 @@
+/*
+ * wos.h -- C ABI of the GB300 walk-on-ellipsoids operator library.
+ *
+ * The library builds, on one GPU, the Monte Carlo estimate of the discretised
+ * direct operator of the Cauchy / data-completion problem of Cimpean, Grecu
+ * & Marin, "Numerical spectral analysis of Cauchy-type inverse problems: a
+ * probabilistic approach" (arXiv:2409.03686), then its FP64 SVD and the
+ * truncated-SVD reconstruction of the Dirichlet data on Gamma_1.
+ *
+ * Conventions for every entry point
+ *   - Array arguments marked "device" are pointers to memory of the device
+ *     the context was created on; "host" arrays are read during the call and
+ *     may be freed when it returns.  The caller owns every array it passes.
+ *   - Descriptor structs are copied during the call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Device work is enqueued on it; unless stated otherwise a call
+ *     returns without waiting for that work.
+ *   - Errors are returned as wos_status and never abort the process.  On an
+ *     error other than a warning nothing was enqueued.
+ *   - Matrices are row-major.  Element (boundary cell) indices run over the
+ *     outer boundary component first, then hole 0, hole 1, ...
+ */
+#ifndef WOS_H
+#define WOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WOS_OK = 0,
+    WOS_INVALID_ARG = 1,        /* a size, pointer or descriptor field is bad */
+    WOS_K_NOT_SPD = 2,          /* K is not symmetric positive definite */
+    WOS_POINT_OUTSIDE = 3,      /* an observation point lies outside D */
+    WOS_EPS_BELOW_FP32_FLOOR = 4, /* FP32 walks need eps >= the floor below */
+    WOS_COUNT_OVERFLOW = 5,     /* a count could exceed 2^32 - 1 */
+    WOS_STEP_CAP_HIT = 6,       /* warning: some walks hit the step cap; the
+                                   counts are valid and unterminated > 0 */
+    WOS_DEVICE_TIMEOUT = 7,     /* a bounded device-side wait gave up */
+    WOS_OOM = 8,                /* a device allocation failed */
+    WOS_CUDA_ERROR = 9,         /* a CUDA runtime call failed */
+    WOS_NO_CONVERGENCE = 10,    /* Jacobi SVD did not converge in max sweeps */
+    WOS_TRUNCATION_IN_CLUSTER = 11, /* warning: sigma_r / sigma_{r+1} < 1.5 */
+    WOS_NOT_READY = 12          /* a queued request is not finished yet */
+} wos_status;
+
+#define WOS_MAX_VERTICES 64
+#define WOS_MAX_HOLES 16
+
+typedef enum {
+    WOS_OUTER_SPHERE = 1,  /* disc (dim 2) or ball (dim 3) */
+    WOS_OUTER_BOX = 2,     /* axis-aligned rectangle (dim 2) or box (dim 3) */
+    WOS_OUTER_POLYGON = 3  /* simple polygon, vertices counter-clockwise (dim 2) */
+} wos_outer_kind;
+
+/* D = outer body minus disjoint closed holes (discs in 2-D, balls in 3-D).
+ * Unused fields are ignored. */
+typedef struct {
+    int32_t dim;        /* 2 or 3 */
+    int32_t outer_kind; /* wos_outer_kind */
+    double center[3];   /* sphere / box centre */
+    double radius;      /* sphere radius */
+    double half[3];     /* box half-extents */
+    int32_t n_vertices; /* polygon vertex count, 3..WOS_MAX_VERTICES */
+    double vertices[2 * WOS_MAX_VERTICES]; /* (x, y) pairs, counter-clockwise */
+    int32_t n_holes;    /* 0..WOS_MAX_HOLES */
+    double hole_center[WOS_MAX_HOLES][3];
+    double hole_radius[WOS_MAX_HOLES];
+} wos_domain;
+
+/* Partition of dD into boundary elements (the cells of the intrinsic Voronoi
+ * weights, paper App. A, Ex. A.3, or of the extrinsic ones, Ex. A.2).
+ *   circle (2-D sphere / hole): m arcs counter-clockwise from theta0,
+ *       arc j = [theta0 + 2 pi j/m, theta0 + 2 pi (j+1)/m).
+ *   polygon / 2-D box: edge e (v_e -> v_{e+1}; for a box the edges are
+ *       bottom, right, top, left from the corner c - h) in edge_m[e] equal
+ *       cells.
+ *   3-D sphere / hole: nb equal-height z-bands (band 0 at the south pole)
+ *       times ns phi-sectors from phi = 0; cell = band * ns + sector.
+ *   3-D box: faces -x, -y, -z, +x, +y, +z, each face_n1 x face_n2 cells over
+ *       its two other axes in increasing axis order.
+ * A point is assigned through its nearest boundary point (the projection pi
+ * of App. A); ties go to the lowest element index (Ex. A.3).
+ * voronoi_n > 0 replaces all of the above by the extrinsic Voronoi cells of
+ * the given sites (nearest site, lowest index on ties, Ex. A.2). */
+typedef struct {
+    int32_t outer_m;
+    double outer_theta0;
+    int32_t edge_m[WOS_MAX_VERTICES];
+    int32_t outer_nb, outer_ns;
+    int32_t face_n1, face_n2;
+    int32_t hole_m[WOS_MAX_HOLES];
+    double hole_theta0[WOS_MAX_HOLES];
+    int32_t hole_nb[WOS_MAX_HOLES];
+    int32_t hole_ns[WOS_MAX_HOLES];
+    int32_t voronoi_n;            /* 0 = use the cells above */
+    const double *voronoi_sites;  /* host, voronoi_n x dim */
+} wos_partition;
+
+typedef enum { WOS_FP32 = 0, WOS_FP64 = 1 } wos_precision;
+
+/* Options of a build; zero-initialise and set what you need. */
+typedef struct {
+    int32_t precision;   /* wos_precision of the walk arithmetic */
+    uint32_t step_cap;   /* 0 = 1,000,000; walks reaching it stay unterminated */
+    uint32_t stream_id;  /* fourth Philox counter word (instance id) */
+    uint32_t k0, k1;     /* walk range [k0, k1) of every point; k1 = 0 -> N */
+    int32_t accumulate;  /* 0: counts/unterminated are zeroed first; 1: added */
+    int32_t block_size;  /* 0 = tuned default; else a multiple of 32, <= 1024 */
+    int32_t blocks_per_sm; /* 0 = as many as fit */
+    int32_t tile_walks;  /* walks per warp tile (0 = automatic) */
+    int32_t hist_slots;  /* shared-memory histogram slots per warp: 0 = auto,
+                            1 or 2; -1 = tally straight to global memory */
+    int32_t *trace_elem; /* device, optional: M_D x (k1-k0) exit element of
+                            every walk (-1 = unterminated); for tests */
+    uint32_t *trace_steps; /* device, optional: same shape, N_eps per walk */
+    double *trace_x;     /* device, optional: M_D x (k1-k0) x dim exit points */
+    void *kernel_events[2]; /* optional cudaEvent_t pair (caller-created):
+                               recorded on `stream` right before and after
+                               the walk kernel, to time it alone */
+} wos_opts;
+
+/* Per-build statistics (filled after the build's device work finished). */
+typedef struct {
+    uint64_t walks;        /* walks run */
+    uint64_t steps;        /* sum over walks of N_eps (moves of the chain) */
+    uint64_t unterminated; /* walks stopped by the step cap */
+    uint32_t max_steps;    /* largest N_eps seen */
+    int32_t grid, block, tile_walks, hist_slots; /* launch configuration */
+    float kernel_ms;       /* device time of the walk kernel */
+} wos_stats;
+
+typedef struct wos_context wos_context;
+
+/* Create a context on CUDA device `device` (sets it current for the calling
+ * thread).  The context owns small device scratch buffers (work counters,
+ * statistics, descriptor tables) and frees them in wos_destroy.
+ * Errors: WOS_INVALID_ARG (no such device), WOS_OOM, WOS_CUDA_ERROR. */
+wos_status wos_create(int32_t device, wos_context **ctx);
+wos_status wos_destroy(wos_context *ctx);
+
+/* Number of kernels this context has launched so far (all entry points). */
+uint64_t wos_kernel_launches(const wos_context *ctx);
+
+/* Human-readable name of a status code (static string). */
+const char *wos_status_string(wos_status s);
+
+/* Instance set-up of the chain (paper Sec. 4.2, "lambda_max(K) = 1 without
+ * loss of generality"): S = (K / lambda_max(K))^{1/2}, the symmetric square
+ * root.  K, S: host, dim x dim row-major.  Host only (no device work).
+ * Errors: WOS_INVALID_ARG (dim not 2 or 3), WOS_K_NOT_SPD. */
+wos_status wos_conductivity_sqrt(int32_t dim, const double *K, double *S);
+
+/* Number of boundary elements M_tot of a partition, or -1 if invalid. */
+int32_t wos_num_elements(const wos_domain *domain, const wos_partition *part);
+
+/* sigma(omega_j) of every element (arc length, edge-cell length or patch
+ * area: the surface measure of the cell, paper Sec. 3.1, Eq.
+ * (boundary_weights)).  out: host, M_tot doubles.  Extrinsic Voronoi
+ * partitions have no closed form: WOS_INVALID_ARG. */
+wos_status wos_element_measures(const wos_domain *domain,
+                                const wos_partition *part, double *out);
+
+/* The FP32 safety floor of eps: 128 * 2^-24 * max |coordinate| over the
+ * domain's bounding box.  Above it FP32 rounding of the distance and of a
+ * move stays far inside the eps-shell, so no walk can cross dD unstopped. */
+double wos_fp32_eps_floor(const wos_domain *domain);
+
+/* MC-REM (paper Sec. 5.1, Algorithm MC-REM; Sec. 4.2, Eq. (wos chain) and
+ * Eq. (N epsilon x); Sec. 4.3, Eq. (WoE_matrix_MC)).
+ *
+ * For every observation point x_i (i < M_D) and walk k in [k0, k1), runs the
+ * walk-on-ellipsoids chain X_{n+1} = X_n + dist(X_n, dD) S U_n from X_0 = x_i,
+ * S = (K / lambda_max(K))^{1/2}, U_n uniform on the unit sphere drawn from
+ * Philox4x32-10 (key = seed, counter = (block, walk lo, walk hi, stream_id),
+ * walk = i * N + k), stops at the first n with dist(X_n, dD) <= eps and adds
+ * 1 to counts[i][j], j the element holding pi(X_n).  Walks reaching
+ * opts->step_cap add 1 to unterminated[i] instead, so that
+ * sum_j counts[i][j] + unterminated[i] = k1 - k0 exactly (per call).
+ * A = counts / N estimates [mu_{x_i}(omega_j)].
+ *
+ *   K        host, dim x dim row-major, symmetric positive definite.
+ *   points   device, M_D x dim doubles, strictly inside D.
+ *   counts   device, M_D x M_tot uint32 (zeroed first unless accumulate).
+ *   unterminated device, M_D uint32, or NULL (then capped walks are only
+ *            counted in stats).
+ *   stats    host or NULL.  If non-NULL the call waits for the device work
+ *            and fills it; if NULL the call is asynchronous.
+ * Errors: WOS_INVALID_ARG, WOS_K_NOT_SPD, WOS_EPS_BELOW_FP32_FLOOR (FP32
+ * walks only), WOS_COUNT_OVERFLOW, WOS_CUDA_ERROR; WOS_STEP_CAP_HIT is
+ * returned as a warning when stats is non-NULL and a walk was capped.
+ * Points are not checked here (use wos_check_points). */
+wos_status wos_build_operator(wos_context *ctx, const wos_domain *domain,
+                              const double *K, const double *points,
+                              int32_t M_D, const wos_partition *partition,
+                              uint32_t N, double eps, uint64_t seed,
+                              const wos_opts *opts, uint32_t *counts,
+                              uint32_t *unterminated, wos_stats *stats,
+                              void *stream);
+
+/* Check that every point (host, M_D x dim) lies strictly inside D.  Returns
+ * WOS_OK or WOS_POINT_OUTSIDE (first offending index in *bad if non-NULL). */
+wos_status wos_check_points(const wos_domain *domain, const double *points,
+                            int32_t M_D, int32_t *bad);
+
+/* One-sided Jacobi SVD of the scaled operator (paper Sec. 4.3, Eq. (A_r_MC);
+ * Sec. 2, Eq. (SVD)):
+ *     B = diag(nu) (counts[:, Gamma_1] / N) diag(sigma_{Gamma_1})^{-1/2}
+ *       = U diag(S) V^T,
+ * M_1 = number of Gamma_1 elements, k = min(M_D, M_1), S descending, each
+ * right vector signed so that its largest-magnitude entry is positive.
+ * eig(Lambda^nu) = S^2 (Prop. coro:B-Lambda).  FP64 throughout.
+ *   counts   device, M_D x M_tot uint32.
+ *   gamma1   host, M_tot bytes: 1 = element on Gamma_1, 0 = on Gamma_0.
+ *   nu       device, M_D doubles, or NULL for nu_i = 1/sqrt(M_D) (Sec. 5.2).
+ *   sigma    device, M_tot doubles (wos_element_measures).
+ *   U        device, M_D x k;  S  device, k;  V  device, M_1 x k.
+ *   sweeps   host or NULL; if non-NULL the call waits and stores the sweep
+ *            count, returning WOS_NO_CONVERGENCE if max sweeps were used.
+ * Errors: WOS_INVALID_ARG, WOS_OOM, WOS_CUDA_ERROR, WOS_NO_CONVERGENCE. */
+wos_status wos_op_svd(wos_context *ctx, const uint32_t *counts, int32_t M_D,
+                      int32_t M_tot, uint32_t N, const uint8_t *gamma1,
+                      const double *nu, const double *sigma, double *U,
+                      double *S, double *V, int32_t *sweeps, void *stream);
+
+/* r-TSVD reconstruction (paper Sec. 2, Eq. (u1r); Sec. 4.3, Eq.
+ * (u_omega_M1_r_MC A); Sec. 5.1, Rem. (b and u0 simulations), Eq. (tsvd
+ * solution simulations)):
+ *     b      = uD - A_{Gamma_0} u0                (A = counts / N)
+ *     u_g1   = diag(sigma_{Gamma_1})^{-1/2} V_r F_r U_r^T diag(nu) b
+ * with F_r = diag(1 / S_i) (i < r), or the Tikhonov filter
+ * S_i / (S_i^2 + alpha) when tikhonov_alpha > 0; and the fitted interior
+ * data uD_hat = A_{Gamma_1} u_g1 + A_{Gamma_0} u0 (Sec. 5.2, item (iv)).
+ *   U, S, V  device, from wos_op_svd (k columns).
+ *   uD       device, M_D;  u0 device, M_0 (= M_tot - M_1) or NULL (= 0).
+ *   u_gamma1 device, M_1;  uD_hat device, M_D, or NULL.
+ * The truncation r is the caller's; wos_truncation_gap tells whether it
+ * sits at a gap of the spectrum.
+ * Errors: WOS_INVALID_ARG (r outside 1..k), WOS_OOM, WOS_CUDA_ERROR. */
+wos_status wos_reconstruct(wos_context *ctx, const double *U, const double *S,
+                           const double *V, int32_t M_D, int32_t k,
+                           const uint32_t *counts, int32_t M_tot, uint32_t N,
+                           const uint8_t *gamma1, const double *nu,
+                           const double *sigma, const double *uD,
+                           const double *u0, int32_t r, double tikhonov_alpha,
+                           double *u_gamma1, double *uD_hat, void *stream);
+
+/* Truncation rule for degenerate spectra: returns WOS_OK when
+ * S[r-1] / S[r] >= 1.5 (or r = k), else WOS_TRUNCATION_IN_CLUSTER.
+ * S: host, k doubles. */
+wos_status wos_truncation_gap(const double *S, int32_t k, int32_t r);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WOS_H */

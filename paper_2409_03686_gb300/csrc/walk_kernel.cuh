@@ -1,0 +1,275 @@
+// walk_kernel.cuh -- the persistent walk-on-ellipsoids kernel (MC-REM body).
+//
+// Paper: Cimpean, Grecu & Marin, arXiv:2409.03686, Sec. 5.1, Algorithm
+// MC-REM; Sec. 4.2, Eq. (wos chain) and (N epsilon x); Sec. 4.3,
+// Eq. (WoE_matrix_MC).
+//
+// Design (one GB300, no tensor cores: the chain is scalar ALU/SFU work):
+//  * Persistent grid: blocks_per_SM x SMs; every warp loops until the tile
+//    queue is empty and its lanes are idle.
+//  * Work = walks (i, k).  A tile is a run of walks k0..k1 of one point i;
+//    warps take tiles from a global counter (one atomic per tile).
+//  * Every lane owns one walk at a time.  Walks advance in groups of G steps
+//    that share one Philox4x32-10 block (G = 4 words / words per step), so all
+//    lanes call Philox together; a lane whose walk stops mid-group idles to
+//    the group's end.  At a group boundary the finished lanes tally their
+//    exit element and are refilled from the warp's tile (warp-level refill:
+//    ballot + popc ranks), so warps stay full despite geometric walk lengths.
+//  * The Philox counter of step n of walk w is (n / G, w lo, w hi, stream):
+//    results do not depend on scheduling.
+//  * Tally: each warp owns NSLOT shared-memory histograms (one per tile in
+//    flight), two uint16 counts per 32-bit word (a tile has < 65536 walks).
+//    A slot is flushed to HBM with coalesced integer atomics when its tile is
+//    retired; a walk that outlives its slot (generation mismatch) adds to HBM
+//    directly.  No inter-warp synchronisation anywhere.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "wos_device.cuh"
+
+namespace wos {
+
+enum KernelKind : int { kGeneric = 0, kSphereOnly = 1, kBoxOnly = 2 };
+
+template <typename Real> struct WalkParams {
+    Geom<Real> g;
+    Real S[9];            // (K / lambda_max)^{1/2}, row-major DIM x DIM
+    Real eps;
+    uint32_t rk[20];      // Philox key schedule
+    uint32_t stream_id;   // fourth counter word
+    uint32_t N;           // walks per point: walk id = i * N + k
+    uint32_t k0, k1;      // walk range of every point
+    uint32_t step_cap;
+    int32_t M_D;
+    const double *points; // device, M_D x DIM
+    uint32_t *counts;     // device, M_D x M_tot
+    uint32_t *unterm;     // device, M_D (may be null)
+    int32_t *trace_elem;  // optional traces (tests)
+    uint32_t *trace_steps;
+    double *trace_x;
+    // scheduling
+    uint32_t tile_w;           // walks per tile
+    uint32_t tiles_per_point;
+    uint64_t n_tiles;
+    unsigned long long *work;  // [0] tile counter, [1] steps, [2] walks,
+                               // [3] unterminated, [4] max steps
+    int32_t nslot;             // 0 (global tally), 1 or 2
+    int32_t hist_words;        // ceil(M_tot / 2)
+};
+
+template <typename Real, int DIM> struct Steps {
+    // steps served by one Philox block
+    static constexpr int kWordsPerStep = (DIM == 2 ? 1 : 2) * Uniform<Real>::kWords;
+    static constexpr int G = 4 / kWordsPerStep;
+};
+
+template <typename Real, int DIM, int KIND>
+__device__ __forceinline__ Real walk_dist(const Geom<Real> &g, const Real *x)
+{
+    if (KIND == kSphereOnly)
+        return sphere_dist<Real, DIM>(g, x);
+    if (KIND == kBoxOnly)
+        return box_dist_value<Real, DIM>(g, x);
+    return domain_dist<Real, DIM>(g, x);
+}
+
+// Flush one warp-private slot into the counts row of point `pt`.
+__device__ __forceinline__ void flush_slot(uint32_t *slot, int32_t words,
+                                           uint32_t *counts_row, int lane)
+{
+    for (int32_t w = lane; w < words; w += 32) {
+        uint32_t v = slot[w];
+        if (v) {
+            slot[w] = 0u;
+            uint32_t lo = v & 0xFFFFu, hi = v >> 16;
+            if (lo) atomicAdd(counts_row + 2 * w, lo);
+            if (hi) atomicAdd(counts_row + 2 * w + 1, hi);
+        }
+    }
+    __syncwarp();
+}
+
+template <typename Real, int DIM, int KIND>
+__global__ void __launch_bounds__(256, 4)
+walk_kernel(const __grid_constant__ WalkParams<Real> p)
+{
+    constexpr int G = Steps<Real, DIM>::G;
+    constexpr int WPS = Steps<Real, DIM>::kWordsPerStep;
+    constexpr unsigned FULL = 0xFFFFFFFFu;
+    extern __shared__ uint32_t smem[];
+
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int32_t M = p.g.M_tot;
+    uint32_t *hist = smem + (threadIdx.x >> 5) * (p.nslot > 0 ? p.nslot : 1) * p.hist_words;
+    for (int32_t w = lane; w < p.nslot * p.hist_words; w += 32)
+        hist[w] = 0u;
+    __syncwarp();
+
+    // warp-uniform tile / slot state
+    int32_t tile_i = 0;
+    uint32_t tile_k = 0, tile_kend = 0;
+    bool no_more = false;
+    int32_t slot_cur = 0;
+    uint32_t gen0 = 0, gen1 = 0;
+    int32_t pt0 = -1, pt1 = -1;
+
+    // lane state
+    Real X[DIM];
+    int32_t li = 0;
+    uint32_t lk = 0, wlo = 0, whi = 0, nstep = 0;
+    int32_t lslot = 0;
+    uint32_t lgen = 0;
+    bool active = false;
+    unsigned long long my_steps = 0, my_walks = 0, my_unterm = 0;
+    uint32_t my_max = 0;
+
+    bool need = true;
+    for (;;) {
+        // ---- refill: lanes with `need` take walks from the warp's tile -----
+        unsigned need_mask = __ballot_sync(FULL, need);
+        while (need_mask != 0u && !no_more) {
+            uint32_t avail = tile_kend - tile_k;
+            if (avail == 0u) {
+                unsigned long long t = 0;
+                if (lane == 0)
+                    t = atomicAdd(p.work, 1ull);
+                t = __shfl_sync(FULL, t, 0);
+                if (t >= p.n_tiles) {
+                    no_more = true;
+                    break;
+                }
+                uint32_t ti = uint32_t(t / p.tiles_per_point);
+                uint32_t tr = uint32_t(t - uint64_t(ti) * p.tiles_per_point);
+                tile_i = int32_t(ti);
+                tile_k = p.k0 + tr * p.tile_w;
+                tile_kend = min(tile_k + p.tile_w, p.k1);
+                if (p.nslot > 0) {
+                    int32_t s = (p.nslot == 2) ? (slot_cur ^ 1) : 0;
+                    int32_t old_pt = s ? pt1 : pt0;
+                    if (old_pt >= 0)
+                        flush_slot(hist + s * p.hist_words, p.hist_words,
+                                   p.counts + size_t(old_pt) * M, lane);
+                    if (s) { ++gen1; pt1 = tile_i; } else { ++gen0; pt0 = tile_i; }
+                    slot_cur = s;
+                }
+                continue;
+            }
+            bool mine = (need_mask >> lane) & 1u;
+            uint32_t rank = __popc(need_mask & lt_mask);
+            uint32_t n = __popc(need_mask);
+            uint32_t take = n < avail ? n : avail;
+            if (mine && rank < take) {
+                li = tile_i;
+                lk = tile_k + rank;
+                uint64_t wid = uint64_t(li) * p.N + lk;
+                wlo = uint32_t(wid);
+                whi = uint32_t(wid >> 32);
+#pragma unroll
+                for (int a = 0; a < DIM; ++a)
+                    X[a] = Real(p.points[size_t(li) * DIM + a]);
+                nstep = 0;
+                active = true;
+                lslot = slot_cur;
+                lgen = slot_cur ? gen1 : gen0;
+            }
+            tile_k += take;
+            need_mask = __ballot_sync(FULL, mine && rank >= take);
+        }
+        if (!__any_sync(FULL, active))
+            break;
+
+        // ---- one group of G steps of the chain (Eq. (wos chain)) -----------
+        bool stop = false, capped = false;
+        if (active) {
+            uint32_t w[4];
+            philox4x32_10(nstep / G, wlo, whi, p.stream_id, p.rk, w);
+#pragma unroll
+            for (int s = 0; s < G; ++s) {
+                if (!stop) {
+                    Real r = walk_dist<Real, DIM, KIND>(p.g, X);
+                    if (r <= p.eps) {
+                        stop = true;
+                    } else if (nstep >= p.step_cap) {
+                        stop = true;
+                        capped = true;
+                    } else {
+                        Real U[DIM];
+                        direction<Real, DIM>(w + s * WPS, U);
+#pragma unroll
+                        for (int a = 0; a < DIM; ++a) {
+                            Real su = Real(0);
+#pragma unroll
+                            for (int b = 0; b < DIM; ++b)
+                                su += p.S[a * DIM + b] * U[b];
+                            X[a] += r * su;
+                        }
+                        ++nstep;
+                    }
+                }
+            }
+        }
+        bool fin = active && stop;
+        need = !active || fin;
+        if (!__any_sync(FULL, fin))
+            continue;
+
+        // ---- tally the finished walks (Eq. (WoE_matrix_MC)) ----------------
+        if (fin) {
+            int32_t j = capped ? -1 : classify<Real, DIM>(p.g, X);
+            if (p.trace_elem) {
+                size_t q = size_t(li) * (p.k1 - p.k0) + (lk - p.k0);
+                p.trace_elem[q] = j;
+                if (p.trace_steps) p.trace_steps[q] = nstep;
+                if (p.trace_x) {
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a)
+                        p.trace_x[q * DIM + a] = double(X[a]);
+                }
+            }
+            if (j >= 0) {
+                uint32_t g_now = lslot ? gen1 : gen0;
+                if (p.nslot > 0 && lgen == g_now)
+                    atomicAdd(hist + lslot * p.hist_words + (j >> 1),
+                              1u << ((j & 1) * 16));
+                else
+                    atomicAdd(p.counts + size_t(li) * M + j, 1u);
+            } else {
+                ++my_unterm;
+                if (p.unterm)
+                    atomicAdd(p.unterm + li, 1u);
+            }
+            my_steps += nstep;
+            ++my_walks;
+            my_max = nstep > my_max ? nstep : my_max;
+            active = false;
+        }
+        __syncwarp();
+    }
+
+    // ---- retire: flush the slots, add the warp's statistics ----------------
+    if (p.nslot > 0) {
+        if (pt0 >= 0)
+            flush_slot(hist, p.hist_words, p.counts + size_t(pt0) * M, lane);
+        if (p.nslot == 2 && pt1 >= 0)
+            flush_slot(hist + p.hist_words, p.hist_words,
+                       p.counts + size_t(pt1) * M, lane);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        my_steps += __shfl_xor_sync(FULL, my_steps, off);
+        my_walks += __shfl_xor_sync(FULL, my_walks, off);
+        my_unterm += __shfl_xor_sync(FULL, my_unterm, off);
+        uint32_t o = __shfl_xor_sync(FULL, my_max, off);
+        my_max = o > my_max ? o : my_max;
+    }
+    if (lane == 0) {
+        atomicAdd(p.work + 1, my_steps);
+        atomicAdd(p.work + 2, my_walks);
+        if (my_unterm) atomicAdd(p.work + 3, my_unterm);
+        atomicMax(p.work + 4, (unsigned long long)my_max);
+    }
+}
+
+}  // namespace wos

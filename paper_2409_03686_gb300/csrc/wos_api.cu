@@ -1,0 +1,698 @@
+// wos_api.cu -- host side of the C ABI declared in include/wos.h: argument
+// validation, instance set-up (paper Sec. 4.2: K_s = K / lambda_max(K),
+// S = K_s^{1/2}), launch configuration of the persistent walk kernel and the
+// context object.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "wos.h"
+#include "wos_internal.h"
+#include "walk_kernel.cuh"
+
+using namespace wos;
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct wos_context {
+    std::atomic<uint64_t> launches{0};
+    int device = 0;
+    int sm_count = 0;
+    int max_smem_optin = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace wos {
+
+wos_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return WOS_OK;
+    if (e == cudaErrorMemoryAllocation)
+        return WOS_OOM;
+    return WOS_CUDA_ERROR;
+}
+
+int ctx_device(const wos_context *c) { return c->device; }
+void count_launches(wos_context *c, int n) { c->launches += uint64_t(n); }
+int ctx_sm_count(const wos_context *c) { return c->sm_count; }
+
+}  // namespace wos
+
+extern "C" wos_status wos_create(int32_t device, wos_context **out)
+{
+    if (!out)
+        return WOS_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n)
+        return WOS_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess)
+        return WOS_CUDA_ERROR;
+    wos_context *c = new (std::nothrow) wos_context();
+    if (!c)
+        return WOS_OOM;
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&c->max_smem_optin,
+                           cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (cudaEventCreate(&c->ev0) != cudaSuccess ||
+        cudaEventCreate(&c->ev1) != cudaSuccess) {
+        delete c;
+        return WOS_CUDA_ERROR;
+    }
+    *out = c;
+    return WOS_OK;
+}
+
+extern "C" wos_status wos_destroy(wos_context *c)
+{
+    if (!c)
+        return WOS_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    delete c;
+    return WOS_OK;
+}
+
+extern "C" uint64_t wos_kernel_launches(const wos_context *c)
+{
+    return c ? c->launches.load() : 0;
+}
+
+extern "C" const char *wos_status_string(wos_status s)
+{
+    switch (s) {
+    case WOS_OK: return "ok";
+    case WOS_INVALID_ARG: return "invalid argument";
+    case WOS_K_NOT_SPD: return "K is not symmetric positive definite";
+    case WOS_POINT_OUTSIDE: return "observation point outside the domain";
+    case WOS_EPS_BELOW_FP32_FLOOR: return "eps below the FP32 safety floor";
+    case WOS_COUNT_OVERFLOW: return "walk ids or counts overflow";
+    case WOS_STEP_CAP_HIT: return "some walks reached the step cap";
+    case WOS_DEVICE_TIMEOUT: return "device-side wait timed out";
+    case WOS_OOM: return "device out of memory";
+    case WOS_CUDA_ERROR: return "CUDA runtime error";
+    case WOS_NO_CONVERGENCE: return "Jacobi SVD did not converge";
+    case WOS_TRUNCATION_IN_CLUSTER: return "truncation inside a singular-value cluster";
+    case WOS_NOT_READY: return "not ready";
+    }
+    return "unknown status";
+}
+
+// ---------------------------------------------------------------------------
+// descriptors
+// ---------------------------------------------------------------------------
+namespace wos {
+
+static int32_t outer_elements(const wos_domain &d, const wos_partition &p)
+{
+    if (d.outer_kind == WOS_OUTER_SPHERE)
+        return d.dim == 2 ? p.outer_m : p.outer_nb * p.outer_ns;
+    if (d.outer_kind == WOS_OUTER_BOX && d.dim == 3)
+        return 6 * p.face_n1 * p.face_n2;
+    int ne = d.outer_kind == WOS_OUTER_BOX ? 4 : d.n_vertices;
+    int64_t s = 0;
+    for (int e = 0; e < ne; ++e)
+        s += p.edge_m[e];
+    return int32_t(s);
+}
+
+static int32_t hole_elements(const wos_domain &d, const wos_partition &p, int h)
+{
+    return d.dim == 2 ? p.hole_m[h] : p.hole_nb[h] * p.hole_ns[h];
+}
+
+wos_status validate(const wos_domain *dp, const wos_partition *pp)
+{
+    if (!dp || !pp)
+        return WOS_INVALID_ARG;
+    const wos_domain &d = *dp;
+    const wos_partition &p = *pp;
+    if (d.dim != 2 && d.dim != 3)
+        return WOS_INVALID_ARG;
+    if (d.n_holes < 0 || d.n_holes > WOS_MAX_HOLES)
+        return WOS_INVALID_ARG;
+    for (int h = 0; h < d.n_holes; ++h)
+        if (!(d.hole_radius[h] > 0.0))
+            return WOS_INVALID_ARG;
+    bool cells = p.voronoi_n <= 0;
+    switch (d.outer_kind) {
+    case WOS_OUTER_SPHERE:
+        if (!(d.radius > 0.0))
+            return WOS_INVALID_ARG;
+        if (cells && d.dim == 2 && p.outer_m < 1)
+            return WOS_INVALID_ARG;
+        if (cells && d.dim == 3 && (p.outer_nb < 1 || p.outer_ns < 1))
+            return WOS_INVALID_ARG;
+        break;
+    case WOS_OUTER_BOX:
+        for (int a = 0; a < d.dim; ++a)
+            if (!(d.half[a] > 0.0))
+                return WOS_INVALID_ARG;
+        if (cells && d.dim == 2)
+            for (int e = 0; e < 4; ++e)
+                if (p.edge_m[e] < 1)
+                    return WOS_INVALID_ARG;
+        if (cells && d.dim == 3 && (p.face_n1 < 1 || p.face_n2 < 1))
+            return WOS_INVALID_ARG;
+        break;
+    case WOS_OUTER_POLYGON: {
+        if (d.dim != 2 || d.n_vertices < 3 || d.n_vertices > WOS_MAX_VERTICES)
+            return WOS_INVALID_ARG;
+        double area2 = 0.0;
+        for (int e = 0; e < d.n_vertices; ++e) {
+            int e1 = (e + 1) % d.n_vertices;
+            double ax = d.vertices[2 * e], ay = d.vertices[2 * e + 1];
+            double bx = d.vertices[2 * e1], by = d.vertices[2 * e1 + 1];
+            if (ax == bx && ay == by)
+                return WOS_INVALID_ARG;
+            area2 += ax * by - bx * ay;
+            if (cells && p.edge_m[e] < 1)
+                return WOS_INVALID_ARG;
+        }
+        if (!(area2 > 0.0))
+            return WOS_INVALID_ARG;  // vertices must be counter-clockwise
+        break;
+    }
+    default:
+        return WOS_INVALID_ARG;
+    }
+    if (cells)
+        for (int h = 0; h < d.n_holes; ++h)
+            if (hole_elements(d, p, h) < 1 || (d.dim == 3 && (p.hole_nb[h] < 1 || p.hole_ns[h] < 1)))
+                return WOS_INVALID_ARG;
+    if (!cells && !p.voronoi_sites)
+        return WOS_INVALID_ARG;
+    return WOS_OK;
+}
+
+int32_t num_elements(const wos_domain &d, const wos_partition &p)
+{
+    if (p.voronoi_n > 0)
+        return p.voronoi_n;
+    int64_t s = outer_elements(d, p);
+    for (int h = 0; h < d.n_holes; ++h)
+        s += hole_elements(d, p, h);
+    return s > INT32_MAX / 2 ? -1 : int32_t(s);
+}
+
+template <typename Real>
+void fill_geom(const wos_domain &d, const wos_partition &p, Geom<Real> &g)
+{
+    std::memset(&g, 0, sizeof(g));
+    g.dim = d.dim;
+    g.outer_kind = d.outer_kind;
+    g.n_holes = d.n_holes;
+    g.M_tot = num_elements(d, p);
+    g.vn = p.voronoi_n > 0 ? p.voronoi_n : 0;
+    for (int a = 0; a < 3; ++a) {
+        g.c[a] = Real(d.center[a]);
+        g.h[a] = Real(d.half[a]);
+    }
+    g.R = Real(d.radius);
+    const double inv2pi = 0.15915494309189533577;
+    g.outer_m = p.outer_m;
+    g.outer_t0 = Real(p.outer_theta0 * inv2pi);
+    g.nb = p.outer_nb;
+    g.ns = p.outer_ns;
+    g.n1 = p.face_n1;
+    g.n2 = p.face_n2;
+    int ne = 0;
+    if (d.outer_kind == WOS_OUTER_POLYGON) {
+        ne = d.n_vertices;
+        g.n_vert = ne;
+        for (int e = 0; e < ne; ++e) {
+            int e1 = (e + 1) % ne;
+            double ax = d.vertices[2 * e], ay = d.vertices[2 * e + 1];
+            double bx = d.vertices[2 * e1], by = d.vertices[2 * e1 + 1];
+            g.vx[e] = Real(ax);
+            g.vy[e] = Real(ay);
+            g.ex[e] = Real(bx - ax);
+            g.ey[e] = Real(by - ay);
+            g.il2[e] = Real(1.0 / ((bx - ax) * (bx - ax) + (by - ay) * (by - ay)));
+        }
+    } else if (d.outer_kind == WOS_OUTER_BOX && d.dim == 2) {
+        ne = 4;
+    }
+    int32_t off = 0;
+    for (int e = 0; e < ne; ++e) {
+        g.edge_m[e] = p.edge_m[e];
+        g.edge_off[e] = off;
+        off += p.edge_m[e];
+    }
+    off = outer_elements(d, p);
+    for (int h = 0; h < d.n_holes; ++h) {
+        for (int a = 0; a < 3; ++a)
+            g.hc[h][a] = Real(d.hole_center[h][a]);
+        g.hr[h] = Real(d.hole_radius[h]);
+        g.hole_m[h] = p.hole_m[h];
+        g.hole_t0[h] = Real(p.hole_theta0[h] * inv2pi);
+        g.hole_nb[h] = p.hole_nb[h];
+        g.hole_ns[h] = p.hole_ns[h];
+        g.hole_off[h] = off;
+        off += hole_elements(d, p, h);
+    }
+}
+
+template void fill_geom<float>(const wos_domain &, const wos_partition &, Geom<float> &);
+template void fill_geom<double>(const wos_domain &, const wos_partition &, Geom<double> &);
+
+// Symmetric eigen-decomposition of a d x d matrix (d <= 3) by cyclic Jacobi
+// rotations: A = Q diag(w) Q^T.
+static void sym_eig(int d, const double *A, double *w, double *Q)
+{
+    double a[9];
+    std::memcpy(a, A, sizeof(double) * d * d);
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j)
+            Q[i * d + j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < d; ++i)
+            for (int j = i + 1; j < d; ++j)
+                off += a[i * d + j] * a[i * d + j];
+        if (off == 0.0)
+            break;
+        for (int pp = 0; pp < d; ++pp)
+            for (int q = pp + 1; q < d; ++q) {
+                double apq = a[pp * d + q];
+                if (apq == 0.0)
+                    continue;
+                double theta = (a[q * d + q] - a[pp * d + pp]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) /
+                           (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < d; ++k) {  // A <- A J
+                    double akp = a[k * d + pp], akq = a[k * d + q];
+                    a[k * d + pp] = c * akp - s * akq;
+                    a[k * d + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < d; ++k) {  // A <- J^T A
+                    double apk = a[pp * d + k], aqk = a[q * d + k];
+                    a[pp * d + k] = c * apk - s * aqk;
+                    a[q * d + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < d; ++k) {  // Q <- Q J
+                    double qkp = Q[k * d + pp], qkq = Q[k * d + q];
+                    Q[k * d + pp] = c * qkp - s * qkq;
+                    Q[k * d + q] = s * qkp + c * qkq;
+                }
+            }
+    }
+    for (int i = 0; i < d; ++i)
+        w[i] = a[i * d + i];
+}
+
+wos_status setup_S(int d, const double *K, double *S)
+{
+    if (!K)
+        return WOS_INVALID_ARG;
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double x = K[i * d + j], y = K[j * d + i];
+            if (!std::isfinite(x) ||
+                std::fabs(x - y) > 1e-12 * (std::fabs(x) + std::fabs(y) + 1e-300))
+                return WOS_K_NOT_SPD;
+        }
+    double w[3], Q[9];
+    sym_eig(d, K, w, Q);
+    double lmax = w[0];
+    for (int i = 1; i < d; ++i)
+        lmax = std::max(lmax, w[i]);
+    for (int i = 0; i < d; ++i)
+        if (!(w[i] > 1e-12 * lmax))
+            return WOS_K_NOT_SPD;
+    for (int i = 0; i < d; ++i)
+        for (int j = 0; j < d; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k < d; ++k)
+                acc += Q[i * d + k] * std::sqrt(w[k] / lmax) * Q[j * d + k];
+            S[i * d + j] = acc;
+        }
+    return WOS_OK;
+}
+
+double fp32_floor(const wos_domain &d)
+{
+    double m = 0.0;
+    auto upd = [&](double v) { m = std::max(m, std::fabs(v)); };
+    if (d.outer_kind == WOS_OUTER_SPHERE)
+        for (int a = 0; a < d.dim; ++a) {
+            upd(d.center[a] - d.radius);
+            upd(d.center[a] + d.radius);
+        }
+    else if (d.outer_kind == WOS_OUTER_BOX)
+        for (int a = 0; a < d.dim; ++a) {
+            upd(d.center[a] - d.half[a]);
+            upd(d.center[a] + d.half[a]);
+        }
+    else
+        for (int e = 0; e < 2 * d.n_vertices; ++e)
+            upd(d.vertices[e]);
+    return 128.0 * std::ldexp(1.0, -24) * m;
+}
+
+}  // namespace wos
+
+extern "C" wos_status wos_conductivity_sqrt(int32_t dim, const double *K, double *S)
+{
+    if ((dim != 2 && dim != 3) || !K || !S)
+        return WOS_INVALID_ARG;
+    return setup_S(dim, K, S);
+}
+
+extern "C" int32_t wos_num_elements(const wos_domain *d, const wos_partition *p)
+{
+    if (validate(d, p) != WOS_OK)
+        return -1;
+    return num_elements(*d, *p);
+}
+
+extern "C" double wos_fp32_eps_floor(const wos_domain *d)
+{
+    return d ? fp32_floor(*d) : 0.0;
+}
+
+extern "C" wos_status wos_element_measures(const wos_domain *dp,
+                                           const wos_partition *pp, double *out)
+{
+    wos_status st = validate(dp, pp);
+    if (st != WOS_OK)
+        return st;
+    if (!out || pp->voronoi_n > 0)
+        return WOS_INVALID_ARG;
+    const wos_domain &d = *dp;
+    const wos_partition &p = *pp;
+    const double pi = 3.14159265358979323846;
+    int32_t q = 0;
+    if (d.outer_kind == WOS_OUTER_SPHERE) {
+        if (d.dim == 2)
+            for (int j = 0; j < p.outer_m; ++j)
+                out[q++] = 2 * pi * d.radius / p.outer_m;
+        else
+            for (int j = 0; j < p.outer_nb * p.outer_ns; ++j)
+                out[q++] = 4 * pi * d.radius * d.radius / (p.outer_nb * p.outer_ns);
+    } else if (d.outer_kind == WOS_OUTER_BOX && d.dim == 3) {
+        for (int f = 0; f < 6; ++f) {
+            int ax = f % 3, b0 = ax == 0 ? 1 : 0, b1 = ax == 2 ? 1 : 2;
+            double a = (2 * d.half[b0] / p.face_n1) * (2 * d.half[b1] / p.face_n2);
+            for (int j = 0; j < p.face_n1 * p.face_n2; ++j)
+                out[q++] = a;
+        }
+    } else {
+        double len[WOS_MAX_VERTICES];
+        int ne;
+        if (d.outer_kind == WOS_OUTER_BOX) {
+            ne = 4;
+            len[0] = len[2] = 2 * d.half[0];
+            len[1] = len[3] = 2 * d.half[1];
+        } else {
+            ne = d.n_vertices;
+            for (int e = 0; e < ne; ++e) {
+                int e1 = (e + 1) % ne;
+                len[e] = std::hypot(d.vertices[2 * e1] - d.vertices[2 * e],
+                                    d.vertices[2 * e1 + 1] - d.vertices[2 * e + 1]);
+            }
+        }
+        for (int e = 0; e < ne; ++e)
+            for (int j = 0; j < p.edge_m[e]; ++j)
+                out[q++] = len[e] / p.edge_m[e];
+    }
+    for (int h = 0; h < d.n_holes; ++h) {
+        double r = d.hole_radius[h];
+        if (d.dim == 2)
+            for (int j = 0; j < p.hole_m[h]; ++j)
+                out[q++] = 2 * pi * r / p.hole_m[h];
+        else {
+            int n = p.hole_nb[h] * p.hole_ns[h];
+            for (int j = 0; j < n; ++j)
+                out[q++] = 4 * pi * r * r / n;
+        }
+    }
+    return WOS_OK;
+}
+
+extern "C" wos_status wos_check_points(const wos_domain *dp, const double *pts,
+                                       int32_t M_D, int32_t *bad)
+{
+    wos_partition dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    dummy.voronoi_n = 1;
+    double site[3] = {0, 0, 0};
+    dummy.voronoi_sites = site;
+    wos_status st = validate(dp, &dummy);
+    if (st != WOS_OK || (M_D > 0 && !pts) || M_D < 0)
+        return WOS_INVALID_ARG;
+    Geom<double> g;
+    fill_geom(*dp, dummy, g);
+    for (int32_t i = 0; i < M_D; ++i) {
+        double r = dp->dim == 2 ? domain_dist<double, 2>(g, pts + 2 * i)
+                                : domain_dist<double, 3>(g, pts + 3 * i);
+        bool inside = r > 0.0;
+        if (inside && dp->outer_kind == WOS_OUTER_POLYGON) {
+            // the polygon distance is unsigned: add a crossing-number test
+            double x = pts[2 * i], y = pts[2 * i + 1];
+            bool in = false;
+            int n = dp->n_vertices;
+            for (int e = 0; e < n; ++e) {
+                int e1 = (e + 1) % n;
+                double ax = dp->vertices[2 * e], ay = dp->vertices[2 * e + 1];
+                double bx = dp->vertices[2 * e1], by = dp->vertices[2 * e1 + 1];
+                if ((ay > y) != (by > y) && x < ax + (y - ay) * (bx - ax) / (by - ay))
+                    in = !in;
+            }
+            inside = in;
+        }
+        if (!inside) {
+            if (bad)
+                *bad = i;
+            return WOS_POINT_OUTSIDE;
+        }
+    }
+    return WOS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the walk launch
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename Real, int DIM, int KIND>
+const void *kernel_ptr()
+{
+    return reinterpret_cast<const void *>(&walk_kernel<Real, DIM, KIND>);
+}
+
+template <typename Real>
+const void *pick_kernel(int dim, int kind)
+{
+    if (dim == 2) {
+        if (kind == kSphereOnly) return kernel_ptr<Real, 2, kSphereOnly>();
+        if (kind == kBoxOnly) return kernel_ptr<Real, 2, kBoxOnly>();
+        return kernel_ptr<Real, 2, kGeneric>();
+    }
+    if (kind == kSphereOnly) return kernel_ptr<Real, 3, kSphereOnly>();
+    if (kind == kBoxOnly) return kernel_ptr<Real, 3, kBoxOnly>();
+    return kernel_ptr<Real, 3, kGeneric>();
+}
+
+template <typename Real>
+wos_status build_impl(wos_context *ctx, const wos_domain &d,
+                      const wos_partition &part, const double *S,
+                      const double *points, int32_t M_D, uint32_t N, double eps,
+                      uint64_t seed, const wos_opts &o, uint32_t *counts,
+                      uint32_t *unterm, wos_stats *stats, cudaStream_t stream)
+{
+    WalkParams<Real> *pp = new (std::nothrow) WalkParams<Real>();
+    if (!pp)
+        return WOS_OOM;
+    WalkParams<Real> &p = *pp;
+    fill_geom(d, part, p.g);
+    const int dim = d.dim;
+    for (int i = 0; i < dim * dim; ++i)
+        p.S[i] = Real(S[i]);
+    p.eps = Real(eps);
+    philox_round_keys(seed, p.rk);
+    p.stream_id = o.stream_id;
+    p.N = N;
+    p.k0 = o.k0;
+    p.k1 = o.k1 ? o.k1 : N;
+    p.step_cap = o.step_cap ? o.step_cap : 1000000u;
+    p.M_D = M_D;
+    p.points = points;
+    p.counts = counts;
+    p.unterm = unterm;
+    p.trace_elem = o.trace_elem;
+    p.trace_steps = o.trace_steps;
+    p.trace_x = o.trace_x;
+    const int32_t M = p.g.M_tot;
+    p.hist_words = (M + 1) / 2;
+
+    int kind = kGeneric;
+    if (d.n_holes == 0 && part.voronoi_n <= 0) {
+        if (d.outer_kind == WOS_OUTER_SPHERE) kind = kSphereOnly;
+        else if (d.outer_kind == WOS_OUTER_BOX) kind = kBoxOnly;
+    }
+    const void *kfn = pick_kernel<Real>(dim, kind);
+    int block = o.block_size > 0 ? o.block_size : 256;
+    int warps = block / 32;
+    int nslot = o.hist_slots;
+    size_t slot_bytes = size_t(warps) * p.hist_words * 4;
+    if (nslot == 0) {
+        if (2 * slot_bytes <= 48 * 1024) nslot = 2;
+        else if (slot_bytes <= 96 * 1024) nslot = 1;
+        else nslot = -1;
+    }
+    if (nslot < 0) nslot = 0;
+    size_t smem = size_t(nslot) * slot_bytes;
+    if (smem > size_t(ctx->max_smem_optin)) {
+        delete pp;
+        return WOS_INVALID_ARG;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem));
+    if (e != cudaSuccess) { delete pp; return cuda_status(e); }
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, block, smem);
+    if (e != cudaSuccess || bps < 1) { delete pp; return e != cudaSuccess ? cuda_status(e) : WOS_INVALID_ARG; }
+    if (o.blocks_per_sm > 0) bps = std::min(bps, o.blocks_per_sm);
+    int grid = ctx->sm_count * bps;
+    p.nslot = nslot;
+
+    uint64_t per_point = uint64_t(p.k1 - p.k0);
+    uint64_t total = per_point * uint64_t(M_D);
+    uint64_t tw = o.tile_walks > 0 ? uint64_t(o.tile_walks)
+                                   : total / (16ull * uint64_t(grid) * warps);
+    tw = std::max<uint64_t>(tw, 64);
+    tw = std::min<uint64_t>(tw, 16384);
+    tw = (tw + 31) / 32 * 32;
+    tw = std::min<uint64_t>(tw, per_point);
+    if (tw == 0) tw = 1;
+    p.tile_w = uint32_t(tw);
+    p.tiles_per_point = uint32_t((per_point + tw - 1) / tw);
+    p.n_tiles = uint64_t(p.tiles_per_point) * uint64_t(M_D);
+
+    // per-call scratch: work counters, statistics, Voronoi sites
+    size_t site_bytes = part.voronoi_n > 0 ? size_t(part.voronoi_n) * dim * sizeof(Real) : 0;
+    size_t scratch_bytes = 64 + site_bytes;
+    void *scratch = nullptr;
+    e = cudaMallocAsync(&scratch, scratch_bytes, stream);
+    if (e != cudaSuccess) { delete pp; return cuda_status(e); }
+    p.work = reinterpret_cast<unsigned long long *>(scratch);
+    if (site_bytes) {
+        std::vector<Real> sites(size_t(part.voronoi_n) * dim);
+        for (size_t q = 0; q < sites.size(); ++q)
+            sites[q] = Real(part.voronoi_sites[q]);
+        Real *dsites = reinterpret_cast<Real *>(static_cast<char *>(scratch) + 64);
+        cudaMemcpyAsync(dsites, sites.data(), site_bytes, cudaMemcpyHostToDevice, stream);
+        p.g.vsites = dsites;
+    }
+    cudaMemsetAsync(scratch, 0, 64, stream);
+    if (!o.accumulate) {
+        cudaMemsetAsync(counts, 0, size_t(M_D) * M * 4, stream);
+        if (unterm)
+            cudaMemsetAsync(unterm, 0, size_t(M_D) * 4, stream);
+    }
+    if (stats)
+        cudaEventRecord(ctx->ev0, stream);
+    if (o.kernel_events[0])
+        cudaEventRecord(static_cast<cudaEvent_t>(o.kernel_events[0]), stream);
+    void *args[] = {pp};
+    e = cudaLaunchKernel(kfn, dim3(grid), dim3(block), args, smem, stream);
+    count_launches(ctx, 1);
+    if (o.kernel_events[1])
+        cudaEventRecord(static_cast<cudaEvent_t>(o.kernel_events[1]), stream);
+    if (stats)
+        cudaEventRecord(ctx->ev1, stream);
+    wos_status st = cuda_status(e);
+    if (st == WOS_OK && stats) {
+        unsigned long long w[5] = {0, 0, 0, 0, 0};
+        cudaMemcpyAsync(w, scratch, sizeof(w), cudaMemcpyDeviceToHost, stream);
+        e = cudaStreamSynchronize(stream);
+        st = cuda_status(e);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        stats->steps = w[1];
+        stats->walks = w[2];
+        stats->unterminated = w[3];
+        stats->max_steps = uint32_t(w[4]);
+        stats->grid = grid;
+        stats->block = block;
+        stats->tile_walks = int32_t(tw);
+        stats->hist_slots = nslot;
+        stats->kernel_ms = ms;
+        if (st == WOS_OK && w[3] > 0)
+            st = WOS_STEP_CAP_HIT;
+    }
+    cudaFreeAsync(scratch, stream);
+    delete pp;
+    return st;
+}
+
+}  // namespace
+
+extern "C" wos_status wos_build_operator(wos_context *ctx, const wos_domain *domain,
+                                         const double *K, const double *points,
+                                         int32_t M_D, const wos_partition *partition,
+                                         uint32_t N, double eps, uint64_t seed,
+                                         const wos_opts *opts, uint32_t *counts,
+                                         uint32_t *unterminated, wos_stats *stats,
+                                         void *stream)
+{
+    if (!ctx)
+        return WOS_INVALID_ARG;
+    wos_status st = validate(domain, partition);
+    if (st != WOS_OK)
+        return st;
+    wos_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts)
+        o = *opts;
+    uint32_t k1 = o.k1 ? o.k1 : N;
+    if (M_D < 1 || N < 1 || !points || !counts || !(eps > 0.0) || o.k0 >= k1 || k1 > N)
+        return WOS_INVALID_ARG;
+    if (o.precision != WOS_FP32 && o.precision != WOS_FP64)
+        return WOS_INVALID_ARG;
+    if (o.block_size && (o.block_size % 32 != 0 || o.block_size > 256))
+        return WOS_INVALID_ARG;
+    if (o.hist_slots < -1 || o.hist_slots > 2)
+        return WOS_INVALID_ARG;
+    if (num_elements(*domain, *partition) < 1)
+        return WOS_INVALID_ARG;
+    // walk ids i * N + k must fit 64 bits (always true for int32 M_D)
+    if (uint64_t(M_D) * uint64_t(N) > (1ull << 63))
+        return WOS_COUNT_OVERFLOW;
+    double S[9];
+    st = setup_S(domain->dim, K, S);
+    if (st != WOS_OK)
+        return st;
+    if (o.precision == WOS_FP32 && eps < fp32_floor(*domain))
+        return WOS_EPS_BELOW_FP32_FLOOR;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (o.precision == WOS_FP64)
+        return build_impl<double>(ctx, *domain, *partition, S, points, M_D, N, eps,
+                                  seed, o, counts, unterminated, stats, s);
+    return build_impl<float>(ctx, *domain, *partition, S, points, M_D, N, eps, seed,
+                             o, counts, unterminated, stats, s);
+}
+
+extern "C" wos_status wos_truncation_gap(const double *S, int32_t k, int32_t r)
+{
+    if (!S || k < 1 || r < 1 || r > k)
+        return WOS_INVALID_ARG;
+    if (r == k)
+        return WOS_OK;
+    if (!(S[r] > 0.0))
+        return WOS_OK;
+    return S[r - 1] / S[r] >= 1.5 ? WOS_OK : WOS_TRUNCATION_IN_CLUSTER;
+}

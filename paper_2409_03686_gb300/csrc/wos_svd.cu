@@ -1,0 +1,452 @@
+// wos_svd.cu -- FP64 one-sided Jacobi SVD of the scaled operator and the
+// r-TSVD reconstruction (paper Sec. 2, Eq. (SVD), (u1r); Sec. 4.3,
+// Eq. (A_r_MC), (u_omega_M1_r_MC A); Sec. 5.1, Eq. (tsvd solution
+// simulations)).
+//
+// B = diag(nu) (C[:, Gamma_1] / N) diag(sigma_{Gamma_1})^{-1/2} is formed in
+// FP64, oriented so that the worked matrix W has m >= n columns-of-length-m,
+// and its columns are orthogonalised by one-sided (Hestenes) Jacobi rotations
+// in the parallel round-robin order: each round pairs the n columns into n/2
+// disjoint pairs, one warp per pair; n - 1 rounds make a sweep that touches
+// every pair once.  Rounds are separated by a grid barrier of a cooperative
+// launch (every wait is bounded and reports WOS_DEVICE_TIMEOUT).  A pair is
+// rotated when |w_p . w_q| > tol sqrt(|w_p|^2 |w_q|^2), tol = 1e-15, the
+// relative test of Demmel & Veselic (1992); the build stops after a sweep
+// without rotations.  FP64 is used for everything here: the operator is
+// severely ill-conditioned (its singular values decay exponentially).
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "wos.h"
+#include "wos_internal.h"
+
+namespace {
+
+constexpr unsigned FULL = 0xFFFFFFFFu;
+constexpr double kTol = 1e-15;
+constexpr int kMaxSweeps = 80;
+constexpr int kSvdBlock = 256;
+
+struct SvdWork {
+    double *W;        // m x n, column-major (column j contiguous)
+    double *Vw;       // n x n, column-major
+    int m, n;         // worked orientation, m >= n
+    int n_pad;        // n rounded up to even (a dummy column when odd)
+    unsigned *bar;    // [0] arrive count, [1] generation, [2..4] rotation
+                      // counters of sweeps mod 3, [5] status, [6] sweeps
+};
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(FULL, v, o);
+    return __shfl_sync(FULL, v, 0);  // one value for every lane
+}
+
+// Grid barrier for a cooperative launch; bounded wait (about 2 s) that
+// records WOS_DEVICE_TIMEOUT in bar[5] instead of hanging.
+__device__ bool grid_barrier(unsigned *bar, unsigned nblocks)
+{
+    __syncthreads();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *gen = bar + 1;
+        unsigned g = *gen;
+        __threadfence();
+        unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long t0 = clock64();
+            while (*gen == g) {
+                __nanosleep(32);
+                if (clock64() - t0 > 4000000000LL) {
+                    atomicExch(bar + 5, unsigned(WOS_DEVICE_TIMEOUT));
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        if (*(volatile unsigned *)(bar + 5) != 0u)
+            ok = 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Column index of round-robin position `pos` in round `r` (circle method:
+// position 0 fixed, the other n_pad - 1 positions rotate).
+__device__ __forceinline__ int rr_player(int pos, int r, int n_pad)
+{
+    if (pos == 0)
+        return 0;
+    return 1 + (pos - 1 + r) % (n_pad - 1);
+}
+
+__global__ void __launch_bounds__(kSvdBlock)
+jacobi_kernel(SvdWork w)
+{
+    const int lane = threadIdx.x & 31;
+    const int warps_per_block = blockDim.x >> 5;
+    const int gwarp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
+    const int nwarps = gridDim.x * warps_per_block;
+    const int half = w.n_pad / 2;
+    const int m = w.m, n = w.n;
+    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+        unsigned *rot = w.bar + 2 + (sweep % 3);
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            w.bar[2 + ((sweep + 1) % 3)] = 0u;
+        for (int r = 0; r < w.n_pad - 1; ++r) {
+            for (int pr = gwarp; pr < half; pr += nwarps) {
+                int a = rr_player(pr, r, w.n_pad);
+                int b = rr_player(w.n_pad - 1 - pr, r, w.n_pad);
+                int p = min(a, b), q = max(a, b);
+                if (q >= n)
+                    continue;  // the dummy column of odd n
+                double *wp = w.W + size_t(p) * m, *wq = w.W + size_t(q) * m;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = lane; i < m; i += 32) {
+                    double x = wp[i], y = wq[i];
+                    al = fma(x, x, al);
+                    be = fma(y, y, be);
+                    ga = fma(x, y, ga);
+                }
+                al = warp_sum(al);
+                be = warp_sum(be);
+                ga = warp_sum(ga);
+                if (al == 0.0 || be == 0.0)
+                    continue;
+                if (fabs(ga) <= kTol * sqrt(al) * sqrt(be))
+                    continue;
+                double zeta = (be - al) / (2.0 * ga);
+                double t = (zeta >= 0.0 ? 1.0 : -1.0) /
+                           (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / sqrt(1.0 + t * t);
+                double s = c * t;
+                for (int i = lane; i < m; i += 32) {
+                    double x = wp[i], y = wq[i];
+                    wp[i] = c * x - s * y;
+                    wq[i] = s * x + c * y;
+                }
+                double *vp = w.Vw + size_t(p) * n, *vq = w.Vw + size_t(q) * n;
+                for (int i = lane; i < n; i += 32) {
+                    double x = vp[i], y = vq[i];
+                    vp[i] = c * x - s * y;
+                    vq[i] = s * x + c * y;
+                }
+                if (lane == 0)
+                    atomicAdd(rot, 1u);
+            }
+            if (!grid_barrier(w.bar, gridDim.x))
+                return;
+        }
+        bool done = *(volatile unsigned *)rot == 0u;
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            w.bar[6] = unsigned(sweep + 1);
+        if (done)
+            return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        atomicExch(w.bar + 5, unsigned(WOS_NO_CONVERGENCE));
+}
+
+// B (worked orientation): W[:, col] with col over Gamma_1 elements (or
+// over points when transposed); V_w = I.
+__global__ void form_B_kernel(SvdWork w, const uint32_t *counts, int M_D, int M_tot,
+                              double invN, const int *g1_idx, int M_1,
+                              const double *nu, const double *sigma, int transposed)
+{
+    size_t total = size_t(M_D) * M_1;
+    double nu_def = 1.0 / sqrt(double(M_D));
+    for (size_t q = blockIdx.x * size_t(blockDim.x) + threadIdx.x; q < total;
+         q += size_t(gridDim.x) * blockDim.x) {
+        int i = int(q / M_1), l = int(q % M_1);
+        int j = g1_idx[l];
+        double v = (nu ? nu[i] : nu_def) * double(counts[size_t(i) * M_tot + j]) * invN /
+                   sqrt(sigma[j]);
+        if (!transposed)
+            w.W[size_t(l) * M_D + i] = v;  // column l, row i
+        else
+            w.W[size_t(i) * M_1 + l] = v;  // column i, row l
+    }
+    size_t nn = size_t(w.n) * w.n;
+    for (size_t q = blockIdx.x * size_t(blockDim.x) + threadIdx.x; q < nn;
+         q += size_t(gridDim.x) * blockDim.x)
+        w.Vw[q] = (q / w.n == q % w.n) ? 1.0 : 0.0;
+}
+
+__global__ void column_norms_kernel(SvdWork w, double *sv)
+{
+    int lane = threadIdx.x & 31;
+    int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int j = gw; j < w.n; j += nw) {
+        const double *c = w.W + size_t(j) * w.m;
+        double s = 0.0;
+        for (int i = lane; i < w.m; i += 32)
+            s = fma(c[i], c[i], s);
+        s = warp_sum(s);
+        if (lane == 0)
+            sv[j] = sqrt(s);
+    }
+}
+
+// Rank of every column by descending norm (ties by index), sign from the
+// largest-magnitude entry of the B-side right vector, then the outputs
+// U (M_D x k), S (k), V (M_1 x k), row-major.
+__global__ void finalize_kernel(SvdWork w, const double *sv, int transposed,
+                                double *U, double *S, double *V)
+{
+    int lane = threadIdx.x & 31;
+    int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nw = (gridDim.x * blockDim.x) >> 5;
+    const int k = w.n;
+    for (int j = gw; j < k; j += nw) {
+        double sj = sv[j];
+        int rank = 0;
+        for (int i = lane; i < k; i += 32) {
+            double si = sv[i];
+            rank += (si > sj || (si == sj && i < j)) ? 1 : 0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            rank += __shfl_xor_sync(FULL, rank, o);
+        // B-side right vector: V_w column (not transposed) or W column / s
+        const double *rv = transposed ? (w.W + size_t(j) * w.m) : (w.Vw + size_t(j) * w.n);
+        int rn = transposed ? w.m : w.n;
+        double big = -1.0;
+        int arg = 0;
+        for (int i = lane; i < rn; i += 32) {
+            double a = fabs(rv[i]);
+            if (a > big) { big = a; arg = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            double ob = __shfl_xor_sync(FULL, big, o);
+            int oa = __shfl_xor_sync(FULL, arg, o);
+            if (ob > big || (ob == big && oa < arg)) { big = ob; arg = oa; }
+        }
+        double sign = rv[arg] >= 0.0 ? 1.0 : -1.0;
+        double inv = sj > 0.0 ? 1.0 / sj : 0.0;
+        if (lane == 0)
+            S[rank] = sj;
+        const double *wc = w.W + size_t(j) * w.m;
+        const double *vc = w.Vw + size_t(j) * w.n;
+        if (!transposed) {
+            for (int i = lane; i < w.m; i += 32)   // U: M_D = m rows
+                U[size_t(i) * k + rank] = sign * wc[i] * inv;
+            for (int i = lane; i < w.n; i += 32)   // V: M_1 = n rows
+                V[size_t(i) * k + rank] = sign * vc[i];
+        } else {
+            for (int i = lane; i < w.m; i += 32)   // V: M_1 = m rows
+                V[size_t(i) * k + rank] = sign * wc[i] * inv;
+            for (int i = lane; i < w.n; i += 32)   // U: M_D = n rows
+                U[size_t(i) * k + rank] = sign * vc[i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// TSVD pieces
+// ---------------------------------------------------------------------------
+// y_i = x_i + alpha * sum_j (C[i][j] / N) f_j  over all M_tot elements.
+__global__ void counts_matvec_kernel(const uint32_t *counts, int M_D, int M_tot,
+                                     double invN, const double *f, const double *x,
+                                     double alpha, double *y)
+{
+    int lane = threadIdx.x & 31;
+    int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = gw; i < M_D; i += nw) {
+        const uint32_t *row = counts + size_t(i) * M_tot;
+        double s = 0.0;
+        for (int j = lane; j < M_tot; j += 32)
+            s = fma(double(row[j]), f[j], s);
+        s = warp_sum(s);
+        if (lane == 0)
+            y[i] = (x ? x[i] : 0.0) + alpha * s * invN;
+    }
+}
+
+// f[j] = u0 on Gamma_0 (in Gamma_0 order), 0 on Gamma_1; or u1 on Gamma_1.
+__global__ void scatter_kernel(const int *idx, int n, const double *vals, double *f)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+        f[idx[q]] = vals ? vals[q] : 0.0;
+}
+
+// t_c = filter(S_c) * sum_i U[i][c] nu_i b_i, c < r (one warp per c).
+__global__ void tsvd_t_kernel(const double *U, const double *S, int M_D, int k, int r,
+                              const double *nu, const double *b, double alpha, double *t)
+{
+    int lane = threadIdx.x & 31;
+    int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nw = (gridDim.x * blockDim.x) >> 5;
+    double nu_def = 1.0 / sqrt(double(M_D));
+    for (int c = gw; c < r; c += nw) {
+        double s = 0.0;
+        for (int i = lane; i < M_D; i += 32)
+            s = fma(U[size_t(i) * k + c], (nu ? nu[i] : nu_def) * b[i], s);
+        s = warp_sum(s);
+        if (lane == 0) {
+            double sc = S[c];
+            double filt = alpha > 0.0 ? sc / (sc * sc + alpha) : (sc > 0.0 ? 1.0 / sc : 0.0);
+            t[c] = filt * s;
+        }
+    }
+}
+
+// u1[l] = sigma_{g1[l]}^{-1/2} sum_{c<r} V[l][c] t_c
+__global__ void tsvd_u_kernel(const double *V, int M_1, int k, int r, const double *t,
+                              const int *g1_idx, const double *sigma, double *u1)
+{
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < M_1; l += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < r; ++c)
+            s = fma(V[size_t(l) * k + c], t[c], s);
+        u1[l] = s / sqrt(sigma[g1_idx[l]]);
+    }
+}
+
+struct Lists {
+    std::vector<int> g1, g0;
+};
+
+Lists split(const uint8_t *gamma1, int M_tot)
+{
+    Lists L;
+    for (int j = 0; j < M_tot; ++j)
+        (gamma1[j] ? L.g1 : L.g0).push_back(j);
+    return L;
+}
+
+}  // namespace
+
+extern "C" wos_status wos_op_svd(wos_context *ctx, const uint32_t *counts, int32_t M_D,
+                                 int32_t M_tot, uint32_t N, const uint8_t *gamma1,
+                                 const double *nu, const double *sigma, double *U,
+                                 double *S, double *V, int32_t *sweeps, void *stream)
+{
+    if (!ctx || !counts || !gamma1 || !sigma || !U || !S || !V || M_D < 1 ||
+        M_tot < 1 || N < 1)
+        return WOS_INVALID_ARG;
+    cudaSetDevice(wos::ctx_device(ctx));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Lists L = split(gamma1, M_tot);
+    const int M_1 = int(L.g1.size());
+    if (M_1 < 1)
+        return WOS_INVALID_ARG;
+    const int transposed = M_D < M_1;
+    SvdWork w;
+    w.m = transposed ? M_1 : M_D;
+    w.n = transposed ? M_D : M_1;
+    w.n_pad = w.n + (w.n & 1);
+    if (w.n_pad < 2) w.n_pad = 2;
+    size_t bytes_W = size_t(w.m) * w.n * 8, bytes_V = size_t(w.n) * w.n * 8;
+    size_t bytes = bytes_W + bytes_V + size_t(w.n) * 8 + 64 + size_t(M_1) * 4;
+    char *base = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&base), bytes, st);
+    if (e != cudaSuccess)
+        return wos::cuda_status(e);
+    w.W = reinterpret_cast<double *>(base);
+    w.Vw = reinterpret_cast<double *>(base + bytes_W);
+    double *sv = reinterpret_cast<double *>(base + bytes_W + bytes_V);
+    w.bar = reinterpret_cast<unsigned *>(base + bytes_W + bytes_V + size_t(w.n) * 8);
+    int *g1 = reinterpret_cast<int *>(base + bytes_W + bytes_V + size_t(w.n) * 8 + 64);
+    cudaMemsetAsync(w.bar, 0, 64, st);
+    cudaMemcpyAsync(g1, L.g1.data(), size_t(M_1) * 4, cudaMemcpyHostToDevice, st);
+    int sms = wos::ctx_sm_count(ctx);
+    form_B_kernel<<<sms * 4, 256, 0, st>>>(w, counts, M_D, M_tot, 1.0 / double(N), g1, M_1,
+                                          nu, sigma, transposed);
+    // cooperative Jacobi: one warp per pair, all blocks co-resident
+    int bps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, jacobi_kernel, kSvdBlock, 0);
+    int pairs = w.n_pad / 2;
+    int want = (pairs + kSvdBlock / 32 - 1) / (kSvdBlock / 32);
+    int grid = std::max(1, std::min(want, std::max(1, bps) * sms));
+    void *args[] = {&w};
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<void *>(jacobi_kernel), dim3(grid),
+                                    dim3(kSvdBlock), args, 0, st);
+    if (e == cudaSuccess) {
+        column_norms_kernel<<<sms, 256, 0, st>>>(w, sv);
+        finalize_kernel<<<sms, 256, 0, st>>>(w, sv, transposed, U, S, V);
+        e = cudaGetLastError();
+    }
+    wos::count_launches(ctx, e == cudaSuccess ? 4 : 1);
+    wos_status status = wos::cuda_status(e);
+    if (status == WOS_OK && sweeps) {
+        unsigned hb[7];
+        cudaMemcpyAsync(hb, w.bar, sizeof(hb), cudaMemcpyDeviceToHost, st);
+        e = cudaStreamSynchronize(st);
+        status = wos::cuda_status(e);
+        *sweeps = int32_t(hb[6]);
+        if (status == WOS_OK && hb[5] != 0u)
+            status = wos_status(hb[5]);
+    }
+    cudaFreeAsync(base, st);
+    return status;
+}
+
+extern "C" wos_status wos_reconstruct(wos_context *ctx, const double *U, const double *S,
+                                      const double *V, int32_t M_D, int32_t k,
+                                      const uint32_t *counts, int32_t M_tot, uint32_t N,
+                                      const uint8_t *gamma1, const double *nu,
+                                      const double *sigma, const double *uD,
+                                      const double *u0, int32_t r, double tikhonov_alpha,
+                                      double *u_gamma1, double *uD_hat, void *stream)
+{
+    if (!ctx || !U || !S || !V || !counts || !gamma1 || !sigma || !uD || !u_gamma1 ||
+        M_D < 1 || M_tot < 1 || N < 1 || k < 1 || r < 1 || r > k || tikhonov_alpha < 0)
+        return WOS_INVALID_ARG;
+    cudaSetDevice(wos::ctx_device(ctx));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Lists L = split(gamma1, M_tot);
+    const int M_1 = int(L.g1.size()), M_0 = int(L.g0.size());
+    if (M_1 < 1 || k > std::min(M_D, M_1))
+        return WOS_INVALID_ARG;
+    // scratch: f (M_tot), b (M_D), t (k), index lists
+    size_t bytes = size_t(M_tot) * 8 + size_t(M_D) * 8 + size_t(k) * 8 +
+                   size_t(M_tot) * 4 + 64;
+    char *base = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&base), bytes, st);
+    if (e != cudaSuccess)
+        return wos::cuda_status(e);
+    double *f = reinterpret_cast<double *>(base);
+    double *b = f + M_tot;
+    double *t = b + M_D;
+    int *g1 = reinterpret_cast<int *>(t + k);
+    int *g0 = g1 + M_1;
+    cudaMemcpyAsync(g1, L.g1.data(), size_t(M_1) * 4, cudaMemcpyHostToDevice, st);
+    if (M_0)
+        cudaMemcpyAsync(g0, L.g0.data(), size_t(M_0) * 4, cudaMemcpyHostToDevice, st);
+    int sms = wos::ctx_sm_count(ctx);
+    const double invN = 1.0 / double(N);
+    // b = uD - A u0full (u0full: u0 on Gamma_0, 0 on Gamma_1)
+    cudaMemsetAsync(f, 0, size_t(M_tot) * 8, st);
+    if (u0 && M_0)
+        scatter_kernel<<<sms, 256, 0, st>>>(g0, M_0, u0, f);
+    counts_matvec_kernel<<<sms * 2, 256, 0, st>>>(counts, M_D, M_tot, invN, f, uD, -1.0, b);
+    tsvd_t_kernel<<<std::max(1, (r + 7) / 8), 256, 0, st>>>(U, S, M_D, k, r, nu, b,
+                                                            tikhonov_alpha, t);
+    tsvd_u_kernel<<<std::max(1, (M_1 + 255) / 256), 256, 0, st>>>(V, M_1, k, r, t, g1,
+                                                                  sigma, u_gamma1);
+    if (uD_hat) {
+        scatter_kernel<<<sms, 256, 0, st>>>(g1, M_1, u_gamma1, f);
+        counts_matvec_kernel<<<sms * 2, 256, 0, st>>>(counts, M_D, M_tot, invN, f, nullptr,
+                                                      1.0, uD_hat);
+    }
+    wos::count_launches(ctx, 3 + ((u0 && M_0) ? 1 : 0) + (uD_hat ? 2 : 0));
+    e = cudaGetLastError();
+    cudaFreeAsync(base, st);
+    return wos::cuda_status(e);
+}

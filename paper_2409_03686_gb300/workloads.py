@@ -554,3 +554,20 @@ def mixed_batch(n_instances: int = 64, seed: int = 7, m_lo: int = 64,
         out.append(Instance(f"b{q}-{kind}", dom, part, K, pts, N=N, eps=eps,
                             seed=seed, stream=q))
     return out
+
+
+def synthetic_counts(M_D: int, M_tot: int, N: int, seed: int = 0,
+                     width: float = 0.05) -> np.ndarray:
+    """Seeded multinomial count matrix shaped like an operator: row i draws N
+    samples from a smooth periodic bump centred at i / M_D (for SVD tests at
+    sizes the oracle walker would take too long to build)."""
+    rng = np.random.default_rng(seed)
+    t = np.arange(M_tot) / M_tot
+    C = np.empty((M_D, M_tot), np.uint32)
+    for i in range(M_D):
+        dc = np.abs(t - (i + 0.5) / M_D)
+        dc = np.minimum(dc, 1 - dc)
+        p = 1.0 / (dc ** 2 + width ** 2)
+        p /= p.sum()
+        C[i] = rng.multinomial(N, p)
+    return C

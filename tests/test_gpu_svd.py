@@ -1,0 +1,106 @@
+"""Parity of the CUDA FP64 Jacobi SVD (wos_op_svd) and the TSVD
+reconstruction (wos_reconstruct) with the oracle, on the same counts.
+
+Singular values: |s - s_ref| <= 1e-10 s_ref for s_ref >= 1e-6 s_1, else
+<= 1e-10 s_1 (two different FP64 Jacobi orders cannot agree relatively on
+the tiny singular values of a severely ill-posed operator).  Singular
+vectors are compared through the projector U_r U_r^T at spectral gaps (they
+are defined only up to sign / rotation inside clusters).  Reconstructions
+agree to 1e-8 relative in the 2-norm for r at a gap."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import ctx
+from oracle import oracle as O
+from paper_2409_03686_gb300 import workloads as W
+from paper_2409_03686_gb300 import wos
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def _svd_pair(C, N, gamma1, sigma, nu):
+    Ct = torch.as_tensor(C.astype(np.int32), device=DEV)
+    sg = torch.as_tensor(sigma, device=DEV)
+    nut = torch.as_tensor(nu, device=DEV)
+    U, S, V, sweeps = wos.wos_op_svd(ctx(), Ct, N, gamma1, sg, nu=nut)
+    B = O.operator_B(C, N, gamma1, nu, sigma)
+    Uo, so, Vo, sw_o, ok = O.jacobi_svd(B)
+    return (U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy(), sweeps), (Uo, so, Vo), (Ct, sg, nut)
+
+
+def _check_sv(s, so):
+    big = so >= 1e-6 * so[0]
+    assert np.all(np.abs(s - so)[big] <= 1e-10 * so[big]), np.max(np.abs(s - so)[big] / so[big])
+    assert np.all(np.abs(s - so)[~big] <= 1e-10 * so[0])
+
+
+def _gaps(so, max_r):
+    return [r for r in range(1, min(max_r, len(so) - 1) + 1)
+            if so[r] > 0 and so[r - 1] / so[r] >= 1.5 and so[r - 1] > 1e-6 * so[0]]
+
+
+@pytest.mark.parametrize("make", [
+    lambda: W.disc_config(N=4000, fp64=True),
+    lambda: W.annulus_config(N=1000, grid=6, m_each=32),
+    lambda: W.perforated_disc_config(N=1000, eps=1e-6, n_points=20, m_outer=20, m_hole=8),
+])
+def test_svd_matches_oracle_on_oracle_counts(make):
+    inst = make()
+    C, _, _ = O.build_counts(inst)
+    sigma = O.element_measures(inst.domain, inst.partition)
+    g1 = inst.partition.gamma1
+    (U, s, V, sweeps), (Uo, so, Vo), _ = _svd_pair(C, inst.N, g1, sigma, inst.nu_vec())
+    _check_sv(s, so)
+    k = len(so)
+    np.testing.assert_allclose(U.T @ U, np.eye(k), atol=1e-12)
+    np.testing.assert_allclose(V.T @ V, np.eye(k), atol=1e-12)
+    B = O.operator_B(C, inst.N, g1, inst.nu_vec(), sigma)
+    np.testing.assert_allclose(U @ np.diag(s) @ V.T, B, atol=1e-13 * so[0])
+    for r in _gaps(so, 12):
+        np.testing.assert_allclose(U[:, :r] @ U[:, :r].T, Uo[:, :r] @ Uo[:, :r].T, atol=1e-8)
+    # spectral identity eig(Lambda^nu) = s^2 (Prop. coro:B-Lambda)
+    ev = np.sort(np.linalg.eigvalsh(B @ B.T))[::-1][:k]
+    np.testing.assert_allclose(s ** 2, ev, rtol=1e-9, atol=1e-14 * ev[0])
+
+
+@pytest.mark.parametrize("shape", [(256, 256, 128), (96, 300, 200), (1024, 1536, 768)])
+def test_svd_matches_oracle_at_benchmark_shapes(shape):
+    M_D, M_tot, M_1 = shape
+    N = 100_000
+    C = W.synthetic_counts(M_D, M_tot, N, seed=M_D)
+    g1 = np.zeros(M_tot, np.uint8)
+    g1[:M_1] = 1
+    sigma = np.full(M_tot, 2 * np.pi / M_tot)
+    nu = np.full(M_D, 1 / np.sqrt(M_D))
+    (U, s, V, sweeps), (Uo, so, Vo), _ = _svd_pair(C, N, g1, sigma, nu)
+    _check_sv(s, so)
+    assert sweeps < 40
+
+
+def test_reconstruction_matches_oracle():
+    inst = W.annulus_config(N=2000, grid=6, m_each=32)
+    C, _, _ = O.build_counts(inst)
+    sigma = O.element_measures(inst.domain, inst.partition)
+    g1 = inst.partition.gamma1
+    nu = inst.nu_vec()
+    meas = W.measurements(inst, noise=0.01)
+    (U, s, V, _), (Uo, so, Vo), (Ct, sg, nut) = _svd_pair(C, inst.N, g1, sigma, nu)
+    Ut, St, Vt = (torch.as_tensor(x, device=DEV) for x in (U, s, V))
+    uD = torch.as_tensor(meas.uD, device=DEV)
+    u0 = torch.as_tensor(meas.u0, device=DEV)
+    gaps = _gaps(so, 20)
+    assert gaps
+    for r in gaps:
+        u1, uhat = wos.wos_reconstruct(ctx(), Ut, St, Vt, Ct, inst.N, g1, sg, uD, r,
+                                       u0=u0, nu=nut)
+        ro, rhat = O.reconstruct(Uo, so, Vo, r, C, inst.N, g1, nu, sigma, meas.uD, meas.u0)
+        u1 = u1.cpu().numpy()
+        assert np.linalg.norm(u1 - ro) <= 1e-8 * np.linalg.norm(ro), r
+        assert np.linalg.norm(uhat.cpu().numpy() - rhat) <= 1e-8 * np.linalg.norm(rhat)
+    u1, _ = wos.wos_reconstruct(ctx(), Ut, St, Vt, Ct, inst.N, g1, sg, uD, len(s), u0=u0,
+                                nu=nut, tikhonov_alpha=1e-6)
+    ro, _ = O.reconstruct(Uo, so, Vo, len(so), C, inst.N, g1, nu, sigma, meas.uD, meas.u0,
+                          tikhonov=1e-6)
+    assert np.linalg.norm(u1.cpu().numpy() - ro) <= 1e-8 * np.linalg.norm(ro)

@@ -1,0 +1,190 @@
+"""Parity of the CUDA walk kernel (wos_build_operator) with the FP64 oracle.
+
+With the same Philox counters the GPU and the oracle run the same chain, so
+exit elements are compared walk by walk: at least 99.9 % must agree (the
+rest are knife-edge walks where FP32 rounding differs from FP64), integer
+counts must equal the histogram of the GPU's own per-walk trace bit for bit,
+and every row must sum to N exactly.  FP64 walks agree with the oracle to
+rounding, so their agreement is essentially total."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import ctx, gpu_build, oracle_walks
+from oracle import closed_forms as CF
+from paper_2409_03686_gb300 import workloads as W
+from paper_2409_03686_gb300 import wos
+from stats_util import beta_eps, check_band
+
+pytestmark = pytest.mark.gpu
+
+
+def _hist(trace, M):
+    out = np.zeros((trace.shape[0], M), np.int64)
+    for i in range(trace.shape[0]):
+        t = trace[i]
+        out[i] = np.bincount(t[t >= 0], minlength=M)
+    return out
+
+
+def _check_consistent(inst, r):
+    tr = r["trace"]
+    assert (tr >= -1).all(), "every walk must be traced"
+    np.testing.assert_array_equal(r["counts"], _hist(tr, inst.M_tot))
+    np.testing.assert_array_equal(r["unterm"], (tr == -1).sum(1))
+    assert (r["counts"].sum(1) + r["unterm"] == tr.shape[1]).all()
+
+
+def test_fp64_walks_match_oracle_walk_by_walk():
+    inst = W.disc_config(N=2000, fp64=True)
+    r = gpu_build(inst, trace_steps=True)
+    _check_consistent(inst, r)
+    el, ns, _ = oracle_walks(inst)
+    agree = (r["trace"] == el).mean()
+    assert agree >= 0.9999, agree
+    assert (r["steps"] == ns).mean() >= 0.9999
+    assert r["stats"]["walks"] == inst.M_D * inst.N
+    assert r["stats"]["steps"] == int(r["steps"].sum())
+
+
+GEOMS = {
+    "disc32": lambda: W.disc_config(N=1000, fp64=False),
+    "square": lambda: W.square_config(N=600, grid=8),
+    "annulus": lambda: W.annulus_config(N=600, grid=8),
+    "lshape": lambda: W.lshape_config(N=600, n_points=40),
+    "perforated": lambda: W.perforated_disc_config(N=600, eps=1e-5, fp64=False,
+                                                   n_points=40, m_outer=100, m_hole=20),
+    "ball": lambda: W.ball_config(N=500, n_points=40),
+    "ball_rand_K": lambda: W.config3_instances(N=500, n_points=40)[1],
+    "cube": lambda: W.cube_config(N=500, n_points=40),
+    "shell": lambda: W.shell_config(N=500, shift=0.3, n_points=40),
+    "ball64": lambda: W.ball_config(N=300, n_points=20).replace(fp64=True),
+    "lshape64": lambda: W.lshape_config(N=300, n_points=20).replace(fp64=True, eps=1e-8),
+}
+
+
+@pytest.mark.parametrize("name", list(GEOMS))
+def test_walks_match_oracle(name):
+    inst = GEOMS[name]()
+    r = gpu_build(inst, trace_steps=True)
+    _check_consistent(inst, r)
+    el, ns, _ = oracle_walks(inst)
+    agree = (r["trace"] == el).mean()
+    assert agree >= 0.999, (name, agree)
+    # counts differ from the oracle's by at most the disagreeing walks
+    Co = _hist(el, inst.M_tot)
+    bad = (r["trace"] != el).sum(1)
+    assert (np.abs(r["counts"] - Co).sum(1) <= 2 * bad).all()
+
+
+def test_schedule_does_not_change_results():
+    inst = W.square_config(N=1000, grid=6)
+    ref = gpu_build(inst, trace=False)["counts"]
+    for kw in [dict(tile_walks=64), dict(tile_walks=96, hist_slots=1),
+               dict(tile_walks=1000, hist_slots=-1), dict(block_size=64, blocks_per_sm=1),
+               dict(block_size=128, tile_walks=32, hist_slots=2)]:
+        np.testing.assert_array_equal(gpu_build(inst, trace=False, **kw)["counts"], ref)
+
+
+def test_resume_is_bit_identical():
+    inst = W.annulus_config(N=1500, grid=4)
+    full = gpu_build(inst, trace=False)
+    a = gpu_build(inst, trace=False, k0=0, k1=700)
+    b = gpu_build(inst, trace=False, k0=700, k1=1500, counts=a["counts_t"],
+                  unterminated=a["unterm_t"], accumulate=True)
+    np.testing.assert_array_equal(b["counts"], full["counts"])
+    np.testing.assert_array_equal(b["unterm"], full["unterm"])
+
+
+def test_step_cap_leaves_walks_unterminated():
+    inst = W.square_config(N=800, grid=4).replace(step_cap=4)
+    r = gpu_build(inst, trace_steps=True)
+    _check_consistent(inst, r)
+    assert r["unterm"].sum() > 0
+    assert r["stats"]["unterminated"] == r["unterm"].sum()
+    assert r["steps"].max() == 4
+    el, ns, _ = oracle_walks(inst)
+    assert (r["trace"] == el).mean() >= 0.999
+
+
+def test_edge_cases():
+    # one point, one walk; a ragged tail of tiles
+    inst = W.disc_config(N=1, fp64=False).replace(points=np.array([[0.3, -0.2]]))
+    r = gpu_build(inst)
+    _check_consistent(inst, r)
+    inst = W.disc_config(N=33, fp64=False)
+    r = gpu_build(inst, tile_walks=32)
+    _check_consistent(inst, r)
+    el, _, _ = oracle_walks(inst)
+    assert (r["trace"] == el).mean() >= 0.99
+    # a point already inside the eps-shell stops with N_eps = 0
+    inst = W.disc_config(N=64, fp64=False, eps=1e-4).replace(
+        points=np.array([[0.99995, 0.0], [0.0, -0.5]]))
+    r = gpu_build(inst, trace_steps=True)
+    assert (r["steps"][0] == 0).all() and (r["trace"][0] == 0).all()
+    # many elements: the shared-memory histogram is replaced by HBM atomics
+    inst = W.disc_config(N=400, fp64=False).replace(
+        partition=W.Partition(outer_m=60000, gamma1=np.ones(60000, np.uint8)))
+    r = gpu_build(inst)
+    assert r["stats"]["hist_slots"] == 0
+    _check_consistent(inst, r)
+    el, _, _ = oracle_walks(inst)
+    assert (r["trace"] == el).mean() >= 0.999
+
+
+def test_closed_form_disc_fp32():
+    inst = W.disc_config(N=100_000, fp64=False)
+    r = gpu_build(inst, trace=False)
+    A = r["counts"] / inst.N
+    P = np.array([CF.disc_row(x, 32) for x in inst.points])
+    ok, info = check_band(A, P, inst.N, beta_eps(inst.eps, 0.75 / (2 * math.pi * 0.25)))
+    assert ok, info
+
+
+def test_closed_form_ball_fp32():
+    inst = W.ball_config(N=100_000, n_points=16, nb=4, ns=6, K=np.eye(3))
+    r = gpu_build(inst, trace=False)
+    A = r["counts"] / inst.N
+    P = np.array([CF.ball_patch_row(x, 4, 6) for x in inst.points])
+    rmax = np.linalg.norm(inst.points, axis=1).max()
+    ok, info = check_band(A, P, inst.N,
+                          beta_eps(inst.eps, (1 - rmax ** 2) / (4 * math.pi * (1 - rmax) ** 3)))
+    assert ok, info
+
+
+def test_harmonic_martingale_on_gpu_exit_points():
+    # E[u(X_exit)] = u(x) for the K-harmonic cubic (no eps bias)
+    inst = W.annulus_config(N=20_000, grid=2)
+    r = gpu_build(inst, trace_x=True)
+    u = W.k_harmonic_cubic(inst.K)
+    vals = u(r["x"])
+    z = (vals.mean(1) - u(inst.points)) / (vals.std(1) / math.sqrt(inst.N))
+    assert np.abs(z).max() < 4.5, z
+
+
+def test_full_size_sampled_parity():
+    """The benchmark workload (square, 256 points, N = 1e5, FP32) in its own
+    launch configuration; sampled rows are replayed walk by walk by the
+    oracle, every row is checked for exact sums."""
+    inst = W.square_config()
+    r = gpu_build(inst)
+    _check_consistent(inst, r)
+    rows = [0, 137, 255]
+    el, _, _ = oracle_walks(inst, rows=rows)
+    agree = (r["trace"][rows] == el).mean()
+    assert agree >= 0.999, agree
+
+
+def test_errors_are_reported():
+    inst = W.square_config(N=10, grid=2)
+    with pytest.raises(wos.WosError) as e:
+        gpu_build(inst.replace(K=np.array([[1.0, 2.0], [2.0, 1.0]])), trace=False)
+    assert e.value.code == 2
+    with pytest.raises(wos.WosError) as e:
+        gpu_build(inst.replace(eps=1e-7), trace=False)
+    assert e.value.code == 4
+    with pytest.raises(wos.WosError) as e:
+        gpu_build(inst, trace=False, k0=5, k1=3)
+    assert e.value.code == 1
