@@ -279,6 +279,10 @@ def run_gpu(args, rank: int, world: int, dist):
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     kev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             for _ in prep] for _ in range(args.steps)]
+    for row in kev:  # create the events; the library re-records them around the kernel
+        for pair in row:
+            for e in pair:
+                e.record(stream)
     clocks = ClockSampler(local)
     if dist is not None:
         dist.barrier()

@@ -125,7 +125,8 @@ def test_edge_cases():
     r = gpu_build(inst, trace_steps=True)
     assert (r["steps"][0] == 0).all() and (r["trace"][0] == 0).all()
     # many elements: the shared-memory histogram is replaced by HBM atomics
-    inst = W.disc_config(N=400, fp64=False).replace(
+    # (cells 1e-4 rad wide are below FP32 position resolution: FP64 walks)
+    inst = W.disc_config(N=400, fp64=True).replace(
         partition=W.Partition(outer_m=60000, gamma1=np.ones(60000, np.uint8)))
     r = gpu_build(inst)
     assert r["stats"]["hist_slots"] == 0
