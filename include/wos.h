@@ -44,7 +44,9 @@ typedef enum {
     WOS_CUDA_ERROR = 9,         /* a CUDA runtime call failed */
     WOS_NO_CONVERGENCE = 10,    /* Jacobi SVD did not converge in max sweeps */
     WOS_TRUNCATION_IN_CLUSTER = 11, /* warning: sigma_r / sigma_{r+1} < 1.5 */
-    WOS_NOT_READY = 12          /* a queued request is not finished yet */
+    WOS_NOT_READY = 12,         /* a queued request is not finished yet */
+    WOS_NOALLOC_LIMIT = 13      /* the problem needs more than the fixed scratch
+                                   of wos_build_operator_noalloc */
 } wos_status;
 
 #define WOS_MAX_VERTICES 64
@@ -200,6 +202,36 @@ wos_status wos_build_operator(wos_context *ctx, const wos_domain *domain,
                               const wos_opts *opts, uint32_t *counts,
                               uint32_t *unterminated, wos_stats *stats,
                               void *stream);
+
+/* The operator build of wos_build_operator for callers that cannot allocate
+ * device memory.  The paper has no counterpart: this is an interface for
+ * callers that run under a device-memory budget reserved up front (work is
+ * admitted by its footprint) or inside a host framework that owns every
+ * device allocation, so that neither cudaMalloc nor cudaMallocAsync may be
+ * called on their behalf.
+ *
+ * Arguments, results and errors are those of wos_build_operator, plus
+ * WOS_NOALLOC_LIMIT.  The call allocates nothing: its scratch (the work-queue
+ * and statistics counters, and the site table of an extrinsic Voronoi
+ * partition) lives in one 64 KiB array of device memory defined by the
+ * library, which every GPU that loads the library holds until the process
+ * exits.  Limits: at most 2048 Voronoi sites (more returns WOS_NOALLOC_LIMIT);
+ * everything else as in wos_build_operator.  stats->kernel_ms is left 0 (use
+ * opts->kernel_events to time the kernel).
+ *
+ * The first call on each device looks up that array's device address (with
+ * the context's device current); make that first call before any stream
+ * capture.  All calls on a device share the array and it keeps the last
+ * call's contents: each call clears the counters it needs at zero, but calls
+ * whose device work may overlap (other streams, no event ordering) race on
+ * it and must be serialised by the caller. */
+wos_status wos_build_operator_noalloc(wos_context *ctx, const wos_domain *domain,
+                                      const double *K, const double *points,
+                                      int32_t M_D, const wos_partition *partition,
+                                      uint32_t N, double eps, uint64_t seed,
+                                      const wos_opts *opts, uint32_t *counts,
+                                      uint32_t *unterminated, wos_stats *stats,
+                                      void *stream);
 
 /* Check that every point (host, M_D x dim) lies strictly inside D.  Returns
  * WOS_OK or WOS_POINT_OUTSIDE (first offending index in *bad if non-NULL). */

@@ -43,6 +43,7 @@ wos_status cuda_status(cudaError_t e)
 int ctx_device(const wos_context *c) { return c->device; }
 void count_launches(wos_context *c, int n) { c->launches += uint64_t(n); }
 int ctx_sm_count(const wos_context *c) { return c->sm_count; }
+int ctx_max_smem(const wos_context *c) { return c->max_smem_optin; }
 
 }  // namespace wos
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "wos.h"
+#include "wos_device.cuh"
 
 namespace wos {
 
@@ -11,5 +12,14 @@ wos_status cuda_status(cudaError_t e);
 int ctx_device(const wos_context *c);
 int ctx_sm_count(const wos_context *c);
 void count_launches(wos_context *c, int n);
+int ctx_max_smem(const wos_context *c);
+
+// descriptor handling shared by the entry points (wos_api.cu)
+wos_status validate(const wos_domain *d, const wos_partition *p);
+int32_t num_elements(const wos_domain &d, const wos_partition &p);
+template <typename Real>
+void fill_geom(const wos_domain &d, const wos_partition &p, Geom<Real> &g);
+wos_status setup_S(int d, const double *K, double *S);
+double fp32_floor(const wos_domain &d);
 
 }  // namespace wos

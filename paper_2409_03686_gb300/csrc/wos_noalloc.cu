@@ -1,0 +1,265 @@
+// wos_noalloc.cu -- wos_build_operator_noalloc: the operator build for callers
+// that must not allocate device memory.
+//
+// Some callers cannot call cudaMalloc (or cudaMallocAsync) at all: a process
+// that runs under a device-memory budget reserved up front and admits work
+// only by its footprint, or code hosted inside a framework that owns every
+// device allocation (its own pool, its own accounting) and forbids others'.
+// For them this entry point does the same build as wos_build_operator but
+// takes its scratch -- the work-queue counter, the statistics counters and,
+// for extrinsic Voronoi partitions, the site table -- from one fixed array in
+// device memory that the library defines at file scope.  The caller still
+// passes (and owns) every input and output array.
+//
+// The array is kNoAllocScratchBytes = 64 KiB: 256 bytes of counters, then at
+// most kNoAllocMaxSites = 2048 Voronoi sites.  Every GPU that loads the library
+// holds those 64 KiB until the process exits.  All calls on a device share the
+// array and it keeps the last call's contents; each call clears the counters
+// that must start at zero before its kernel runs.  Calls whose device work
+// overlaps on the GPU (different streams, or no ordering between them) race
+// on the array: order them on one stream or with events.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "walk_kernel.cuh"
+#include "wos.h"
+#include "wos_internal.h"
+
+using namespace wos;
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 64 * 1024;
+constexpr size_t kCounterBytes = 256;
+constexpr int32_t kNoAllocMaxSites = 2048;
+constexpr int kMaxDevices = 64;
+static_assert(kCounterBytes + size_t(kNoAllocMaxSites) * 3 * sizeof(double) <=
+                  kNoAllocScratchBytes,
+              "the site table must fit the scratch array");
+
+// The scratch array.  In host code this name is only a stand-in for the
+// symbol: its device address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_addr_mu;
+void *g_addr[kMaxDevices];
+bool g_addr_ready[kMaxDevices];
+
+// Device address of g_noalloc_scratch on `device` (which must be current).
+// The first call on a device looks it up; later calls reuse it.
+wos_status scratch_address(int device, unsigned char **out)
+{
+    if (device < 0 || device >= kMaxDevices)
+        return WOS_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_addr_mu);
+    if (!g_addr_ready[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr)
+            return e == cudaSuccess ? WOS_CUDA_ERROR : cuda_status(e);
+        g_addr[device] = p;
+        g_addr_ready[device] = true;
+    }
+    *out = static_cast<unsigned char *>(g_addr[device]);
+    return WOS_OK;
+}
+
+template <typename Real, int DIM, int KIND>
+const void *kernel_ptr()
+{
+    return reinterpret_cast<const void *>(&walk_kernel<Real, DIM, KIND>);
+}
+
+template <typename Real>
+const void *pick_kernel(int dim, int kind)
+{
+    if (dim == 2) {
+        if (kind == kSphereOnly) return kernel_ptr<Real, 2, kSphereOnly>();
+        if (kind == kBoxOnly) return kernel_ptr<Real, 2, kBoxOnly>();
+        return kernel_ptr<Real, 2, kGeneric>();
+    }
+    if (kind == kSphereOnly) return kernel_ptr<Real, 3, kSphereOnly>();
+    if (kind == kBoxOnly) return kernel_ptr<Real, 3, kBoxOnly>();
+    return kernel_ptr<Real, 3, kGeneric>();
+}
+
+template <typename Real>
+wos_status build_noalloc(wos_context *ctx, unsigned char *scratch, const wos_domain &d,
+                         const wos_partition &part, const double *S, const double *points,
+                         int32_t M_D, uint32_t N, double eps, uint64_t seed,
+                         const wos_opts &o, uint32_t *counts, uint32_t *unterm,
+                         wos_stats *stats, cudaStream_t stream)
+{
+    WalkParams<Real> p;  // host stack, passed by value to the kernel
+    fill_geom(d, part, p.g);
+    const int dim = d.dim;
+    for (int i = 0; i < 9; ++i)
+        p.S[i] = i < dim * dim ? Real(S[i]) : Real(0);
+    p.eps = Real(eps);
+    philox_round_keys(seed, p.rk);
+    p.stream_id = o.stream_id;
+    p.N = N;
+    p.k0 = o.k0;
+    p.k1 = o.k1 ? o.k1 : N;
+    p.step_cap = o.step_cap ? o.step_cap : 1000000u;
+    p.M_D = M_D;
+    p.points = points;
+    p.counts = counts;
+    p.unterm = unterm;
+    p.trace_elem = o.trace_elem;
+    p.trace_steps = o.trace_steps;
+    p.trace_x = o.trace_x;
+    const int32_t M = p.g.M_tot;
+    p.hist_words = (M + 1) / 2;
+
+    int kind = kGeneric;
+    if (d.n_holes == 0 && part.voronoi_n <= 0) {
+        if (d.outer_kind == WOS_OUTER_SPHERE) kind = kSphereOnly;
+        else if (d.outer_kind == WOS_OUTER_BOX) kind = kBoxOnly;
+    }
+    const void *kfn = pick_kernel<Real>(dim, kind);
+    const int block = o.block_size > 0 ? o.block_size : 256;
+    const int warps = block / 32;
+    int nslot = o.hist_slots;
+    const size_t slot_bytes = size_t(warps) * p.hist_words * 4;
+    if (nslot == 0) {
+        if (2 * slot_bytes <= 48 * 1024) nslot = 2;
+        else if (slot_bytes <= 96 * 1024) nslot = 1;
+        else nslot = -1;
+    }
+    if (nslot < 0) nslot = 0;
+    const size_t smem = size_t(nslot) * slot_bytes;
+    if (smem > size_t(ctx_max_smem(ctx)))
+        return WOS_INVALID_ARG;
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(smem));
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, block, smem);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    if (bps < 1)
+        return WOS_INVALID_ARG;
+    if (o.blocks_per_sm > 0) bps = std::min(bps, o.blocks_per_sm);
+    const int grid = ctx_sm_count(ctx) * bps;
+    p.nslot = nslot;
+
+    const uint64_t per_point = uint64_t(p.k1 - p.k0);
+    const uint64_t total = per_point * uint64_t(M_D);
+    uint64_t tw = o.tile_walks > 0 ? uint64_t(o.tile_walks)
+                                   : total / (16ull * uint64_t(grid) * warps);
+    tw = std::max<uint64_t>(tw, 64);
+    tw = std::min<uint64_t>(tw, 16384);
+    tw = (tw + 31) / 32 * 32;
+    tw = std::min<uint64_t>(tw, per_point);
+    if (tw == 0) tw = 1;
+    p.tile_w = uint32_t(tw);
+    p.tiles_per_point = uint32_t((per_point + tw - 1) / tw);
+    p.n_tiles = uint64_t(p.tiles_per_point) * uint64_t(M_D);
+
+    // scratch: counters at offset 0 (cleared every call), sites after them
+    p.work = reinterpret_cast<unsigned long long *>(scratch);
+    if (part.voronoi_n > 0) {
+        Real staging[size_t(kNoAllocMaxSites) * 3];  // host stack, no allocation
+        const size_t n = size_t(part.voronoi_n) * dim;
+        for (size_t q = 0; q < n; ++q)
+            staging[q] = Real(part.voronoi_sites[q]);
+        Real *dsites = reinterpret_cast<Real *>(scratch + kCounterBytes);
+        // pageable source: returns once the staging buffer has been read
+        e = cudaMemcpyAsync(dsites, staging, n * sizeof(Real), cudaMemcpyHostToDevice,
+                            stream);
+        if (e != cudaSuccess)
+            return cuda_status(e);
+        p.g.vsites = dsites;
+    }
+    e = cudaMemsetAsync(scratch, 0, kCounterBytes, stream);
+    if (e != cudaSuccess)
+        return cuda_status(e);
+    if (!o.accumulate) {
+        cudaMemsetAsync(counts, 0, size_t(M_D) * M * 4, stream);
+        if (unterm)
+            cudaMemsetAsync(unterm, 0, size_t(M_D) * 4, stream);
+    }
+    if (o.kernel_events[0])
+        cudaEventRecord(static_cast<cudaEvent_t>(o.kernel_events[0]), stream);
+    void *args[] = {&p};
+    e = cudaLaunchKernel(kfn, dim3(grid), dim3(block), args, smem, stream);
+    count_launches(ctx, 1);
+    if (o.kernel_events[1])
+        cudaEventRecord(static_cast<cudaEvent_t>(o.kernel_events[1]), stream);
+    wos_status st = cuda_status(e);
+    if (st == WOS_OK && stats) {
+        unsigned long long w[5] = {0, 0, 0, 0, 0};
+        cudaMemcpyAsync(w, scratch, sizeof(w), cudaMemcpyDeviceToHost, stream);
+        st = cuda_status(cudaStreamSynchronize(stream));
+        std::memset(stats, 0, sizeof(*stats));
+        stats->steps = w[1];
+        stats->walks = w[2];
+        stats->unterminated = w[3];
+        stats->max_steps = uint32_t(w[4]);
+        stats->grid = grid;
+        stats->block = block;
+        stats->tile_walks = int32_t(tw);
+        stats->hist_slots = nslot;
+        if (st == WOS_OK && w[3] > 0)
+            st = WOS_STEP_CAP_HIT;
+    }
+    return st;
+}
+
+}  // namespace
+
+extern "C" wos_status wos_build_operator_noalloc(
+    wos_context *ctx, const wos_domain *domain, const double *K, const double *points,
+    int32_t M_D, const wos_partition *partition, uint32_t N, double eps, uint64_t seed,
+    const wos_opts *opts, uint32_t *counts, uint32_t *unterminated, wos_stats *stats,
+    void *stream)
+{
+    if (!ctx)
+        return WOS_INVALID_ARG;
+    wos_status st = validate(domain, partition);
+    if (st != WOS_OK)
+        return st;
+    wos_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts)
+        o = *opts;
+    const uint32_t k1 = o.k1 ? o.k1 : N;
+    if (M_D < 1 || N < 1 || !points || !counts || !(eps > 0.0) || o.k0 >= k1 || k1 > N)
+        return WOS_INVALID_ARG;
+    if (o.precision != WOS_FP32 && o.precision != WOS_FP64)
+        return WOS_INVALID_ARG;
+    if (o.block_size && (o.block_size % 32 != 0 || o.block_size > 256))
+        return WOS_INVALID_ARG;
+    if (o.hist_slots < -1 || o.hist_slots > 2)
+        return WOS_INVALID_ARG;
+    if (num_elements(*domain, *partition) < 1)
+        return WOS_INVALID_ARG;
+    if (partition->voronoi_n > kNoAllocMaxSites)
+        return WOS_NOALLOC_LIMIT;
+    if (uint64_t(M_D) * uint64_t(N) > (1ull << 63))
+        return WOS_COUNT_OVERFLOW;
+    double S[9];
+    st = setup_S(domain->dim, K, S);
+    if (st != WOS_OK)
+        return st;
+    if (o.precision == WOS_FP32 && eps < fp32_floor(*domain))
+        return WOS_EPS_BELOW_FP32_FLOOR;
+    const int dev = ctx_device(ctx);
+    if (cudaSetDevice(dev) != cudaSuccess)
+        return WOS_CUDA_ERROR;
+    unsigned char *scratch = nullptr;
+    st = scratch_address(dev, &scratch);
+    if (st != WOS_OK)
+        return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (o.precision == WOS_FP64)
+        return build_noalloc<double>(ctx, scratch, *domain, *partition, S, points, M_D, N,
+                                     eps, seed, o, counts, unterminated, stats, s);
+    return build_noalloc<float>(ctx, scratch, *domain, *partition, S, points, M_D, N, eps,
+                                seed, o, counts, unterminated, stats, s);
+}

@@ -28,6 +28,7 @@ STATUS = {
     4: "WOS_EPS_BELOW_FP32_FLOOR", 5: "WOS_COUNT_OVERFLOW", 6: "WOS_STEP_CAP_HIT",
     7: "WOS_DEVICE_TIMEOUT", 8: "WOS_OOM", 9: "WOS_CUDA_ERROR",
     10: "WOS_NO_CONVERGENCE", 11: "WOS_TRUNCATION_IN_CLUSTER", 12: "WOS_NOT_READY",
+    13: "WOS_NOALLOC_LIMIT",
 }
 WARNINGS = {6, 11}
 
@@ -140,6 +141,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.wos_check_points.argtypes = [vp, vp, i32, vp]
     L.wos_build_operator.argtypes = [vp, vp, vp, vp, i32, vp, u32, dbl, u64, vp, vp, vp,
                                      vp, vp]
+    L.wos_build_operator_noalloc.argtypes = [vp, vp, vp, vp, i32, vp, u32, dbl, u64, vp,
+                                             vp, vp, vp, vp]
     L.wos_op_svd.argtypes = [vp, vp, i32, i32, u32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.wos_reconstruct.argtypes = [vp, vp, vp, vp, i32, i32, vp, i32, u32, vp, vp, vp, vp,
                                   vp, i32, dbl, vp, vp, vp]
@@ -337,6 +340,29 @@ def wos_build_operator(ctx: Context, domain, K, points, partition, N: int, eps: 
                                 ctypes.byref(st) if st is not None else None,
                                 _stream(stream))
     _check(code, "wos_build_operator")
+    return counts, unterminated, (st.as_dict() if st is not None else None)
+
+
+def wos_build_operator_noalloc(ctx: Context, domain, K, points, partition, N: int,
+                               eps: float, seed: int, counts, unterminated=None,
+                               opts: WosOpts | None = None, stats: bool = True,
+                               stream=None):
+    """The same build as wos_build_operator for callers that cannot allocate
+    device memory: the library takes its scratch from a fixed device array
+    instead of allocating, and this wrapper allocates nothing either -- the
+    caller passes the counts (and optional unterminated) tensors.  Calls on
+    one device must not overlap on the GPU."""
+    L = load()
+    D = make_domain(domain)
+    P, keep = make_partition(domain, partition)
+    Kc = np.ascontiguousarray(K, dtype=np.float64)
+    st = WosStats() if stats else None
+    code = L.wos_build_operator_noalloc(
+        ctx.h, ctypes.byref(D), Kc.ctypes.data, points.data_ptr(), int(points.shape[0]),
+        ctypes.byref(P), int(N), float(eps), int(seed),
+        ctypes.byref(opts) if opts is not None else None, counts.data_ptr(),
+        _ptr(unterminated), ctypes.byref(st) if st is not None else None, _stream(stream))
+    _check(code, "wos_build_operator_noalloc")
     return counts, unterminated, (st.as_dict() if st is not None else None)
 
 
