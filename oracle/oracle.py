@@ -137,6 +137,8 @@ def make_domain(dom, part):
     D.outer_nb, D.outer_ns = part.outer_nb, part.outer_ns
     D.face_n1, D.face_n2 = part.face_n1, part.face_n2
     for h in range(len(dom.holes)):
+        if part.voronoi_sites is not None:
+            break  # Voronoi sites replace the per-component cells
         if dom.dim == 2:
             D.hole_m[h] = part.hole_m[h]
             D.hole_theta0[h] = part.hole_theta0[h]

@@ -195,6 +195,8 @@ def make_partition(dom, part):
     P.outer_nb, P.outer_ns = part.outer_nb, part.outer_ns
     P.face_n1, P.face_n2 = part.face_n1, part.face_n2
     for h in range(len(dom.holes)):
+        if part.voronoi_sites is not None:
+            break  # Voronoi sites replace the per-component cells
         if dom.dim == 2:
             P.hole_m[h] = part.hole_m[h]
             P.hole_theta0[h] = part.hole_theta0[h]

@@ -145,3 +145,14 @@ def test_no_gpu_means_loud_failure(lib):
         pytest.skip("a GPU is present")
     with pytest.raises(wos.WosError):
         wos.Context(0)
+
+
+def test_voronoi_partition_with_holes_marshals(lib):
+    inst = W.annulus_config(m_each=8)
+    sites = W.element_centres(inst.domain, inst.partition)
+    part = W.Partition(voronoi_sites=sites, gamma1=inst.partition.gamma1)
+    assert wos.wos_num_elements(inst.domain, part) == 16
+    assert O.num_elements(inst.domain, part) == 16
+    x = np.array([[0.0, 0.99], [0.51, 0.0]])
+    np.testing.assert_array_equal(O.classify(inst.domain, part, x),
+                                  np.argmin(((sites[None] - x[:, None]) ** 2).sum(-1), 1))
