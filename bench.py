@@ -238,7 +238,9 @@ def run_gpu(args, rank: int, world: int, dist):
         prep.append(p)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def one(p, timing_events=None, host_io=False):
+    streams = [torch.cuda.Stream(device=dev) for _ in prep]
+
+    def one(p, timing_events=None, host_io=False, stream=None):
         inst = p["inst"]
         opts = wos.make_opts(precision=0, stream_id=inst.stream,
                              kernel_events=timing_events)
@@ -249,7 +251,7 @@ def run_gpu(args, rank: int, world: int, dist):
         else:
             pts, uD, u0 = p["points"], p["uD"], p["u0"]
         sol = wos.solve_instance(ctx, inst, uD, u0, p["r"], points=pts, sigma=p["sigma"],
-                                 opts=opts)
+                                 opts=opts, stream=stream)
         if host_io:
             c = sol.counts.to("cpu", non_blocking=True)
             u1 = sol.u_gamma1.to("cpu", non_blocking=True)
@@ -269,9 +271,30 @@ def run_gpu(args, rank: int, world: int, dist):
         p["steps"] = st["steps"]
         p["kind"] = "box" if inst.domain.outer == "box" else "annulus"
         steps_per_inst.append(st["steps"])
+    def step(timing=None, host_io=False, start_ev=None):
+        """One step: every instance's pipeline on its own stream, joined on
+        the current stream (instances overlap on the GPU)."""
+        main = torch.cuda.current_stream()
+        outs = []
+        done = []
+        for q, p in enumerate(prep):
+            s = streams[q]
+            if start_ev is not None:
+                s.wait_event(start_ev)
+            else:
+                s.wait_stream(main)
+            with torch.cuda.stream(s):
+                outs.append(one(p, timing_events=timing[q] if timing else None,
+                                host_io=host_io, stream=s))
+                ev = torch.cuda.Event()
+                ev.record(s)
+                done.append(ev)
+        for ev in done:
+            main.wait_event(ev)
+        return outs
+
     for _ in range(args.warmup):
-        for p in prep:
-            one(p)
+        step()
     torch.cuda.synchronize()
 
     # ---- device-timed steps --------------------------------------------------
@@ -293,8 +316,7 @@ def run_gpu(args, rank: int, world: int, dist):
     for it in range(args.steps):
         flush.zero_()
         starts[it].record(stream)
-        for q, p in enumerate(prep):
-            one(p, timing_events=kev[it][q])
+        step(timing=kev[it], start_ev=starts[it])
         ends[it].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
@@ -313,10 +335,26 @@ def run_gpu(args, rank: int, world: int, dist):
     value = world * walks_per_step * args.steps / (total_ms / 1e3)
     steps_per_s = world * steps_per_step * args.steps / (total_ms / 1e3)
 
-    # roofline of the walk kernel: algorithmic lane-operations / kernel time
-    k_ms = [[a.elapsed_time(b) for (a, b) in row] for row in kev]
+    # roofline of the walk kernel: algorithmic lane-operations / kernel time.
+    # The instances overlap on the GPU, so the kernel time of a step is the
+    # union of its walk-kernel intervals (CUDA events on the launching
+    # streams, placed relative to the step's start event).
     ops = sum(OPS_PER_STEP[p["kind"]] * p["steps"] for p in prep)
-    kernel_ms_step = float(np.mean([sum(row) for row in k_ms]))
+    unions = []
+    for it in range(args.steps):
+        iv = sorted((starts[it].elapsed_time(a), starts[it].elapsed_time(b))
+                    for (a, b) in kev[it])
+        tot, cur0, cur1 = 0.0, None, None
+        for a, b in iv:
+            if cur1 is None or a > cur1:
+                if cur1 is not None:
+                    tot += cur1 - cur0
+                cur0, cur1 = a, b
+            else:
+                cur1 = max(cur1, b)
+        tot += cur1 - cur0
+        unions.append(tot)
+    kernel_ms_step = float(np.mean(unions))
     achieved = ops / (kernel_ms_step / 1e3) / 1e9
     traffic = _traffic_from_profile()
 
@@ -328,7 +366,7 @@ def run_gpu(args, rank: int, world: int, dist):
     torch.cuda.synchronize()
     e2e_s.record(stream)
     for it in range(args.steps):
-        outs = [one(p, host_io=True) for p in prep]
+        outs = step(host_io=True)
         d2h = sum(o[1][0].numel() * 4 + o[1][1].numel() * 8 for o in outs)
     e2e_e.record(stream)
     torch.cuda.synchronize()

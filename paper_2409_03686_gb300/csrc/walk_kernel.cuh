@@ -17,6 +17,9 @@
 //    ballot + popc ranks), so warps stay full despite geometric walk lengths.
 //  * The Philox counter of step n of walk w is (n / G, w lo, w hi, stream):
 //    results do not depend on scheduling.
+//  * A finished lane only pushes its stopped point into a per-warp queue in
+//    shared memory; once 32 are queued the whole warp classifies them (pi of
+//    App. A) and tallies them at full lane efficiency.
 //  * Tally: each warp owns NSLOT shared-memory histograms (one per tile in
 //    flight), two uint16 counts per 32-bit word (a tile has < 65536 walks).
 //    A slot is flushed to HBM with coalesced integer atomics when its tile is
@@ -30,7 +33,7 @@
 
 namespace wos {
 
-enum KernelKind : int { kGeneric = 0, kSphereOnly = 1, kBoxOnly = 2 };
+enum KernelKind : int { kGeneric = 0, kSphereOnly = 1, kBoxOnly = 2, kSphereHoles = 3 };
 
 template <typename Real> struct WalkParams {
     Geom<Real> g;
@@ -43,6 +46,7 @@ template <typename Real> struct WalkParams {
     uint32_t step_cap;
     int32_t M_D;
     const double *points; // device, M_D x DIM
+    const Real *points_r; // the same in walk precision, or null (convert here)
     uint32_t *counts;     // device, M_D x M_tot
     uint32_t *unterm;     // device, M_D (may be null)
     int32_t *trace_elem;  // optional traces (tests)
@@ -71,7 +75,22 @@ __device__ __forceinline__ Real walk_dist(const Geom<Real> &g, const Real *x)
         return sphere_dist<Real, DIM>(g, x);
     if (KIND == kBoxOnly)
         return box_dist_value<Real, DIM>(g, x);
+    if (KIND == kSphereHoles) {
+        Real r = sphere_dist<Real, DIM>(g, x);
+        for (int h = 0; h < g.n_holes; ++h)
+            r = w_min(r, hole_dist<Real, DIM>(g, h, x));
+        return r;
+    }
     return domain_dist<Real, DIM>(g, x);
+}
+
+constexpr int kQueue = 64;  // per-warp exit queue (entries)
+
+// Shared-memory bytes of one warp's exit queue.
+template <typename Real, int DIM>
+__host__ __device__ constexpr size_t queue_bytes()
+{
+    return size_t(kQueue) * (DIM * sizeof(Real) + 4 * sizeof(uint32_t));
 }
 
 // Flush one warp-private slot into the counts row of point `pt`.
@@ -100,13 +119,9 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
     extern __shared__ uint32_t smem[];
 
     const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int32_t M = p.g.M_tot;
-    uint32_t *hist = smem + (threadIdx.x >> 5) * (p.nslot > 0 ? p.nslot : 1) * p.hist_words;
-    for (int32_t w = lane; w < p.nslot * p.hist_words; w += 32)
-        hist[w] = 0u;
-    __syncwarp();
-
     // warp-uniform tile / slot state
     int32_t tile_i = 0;
     uint32_t tile_k = 0, tile_kend = 0;
@@ -114,6 +129,54 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
     int32_t slot_cur = 0;
     uint32_t gen0 = 0, gen1 = 0;
     int32_t pt0 = -1, pt1 = -1;
+    // shared memory: [exit queues of all warps][histogram slots of all warps]
+    unsigned char *qbase = reinterpret_cast<unsigned char *>(smem) +
+                           size_t(warp) * queue_bytes<Real, DIM>();
+    Real *qx = reinterpret_cast<Real *>(qbase);             // [DIM][kQueue]
+    uint32_t *qi = reinterpret_cast<uint32_t *>(qx + DIM * kQueue);  // point
+    uint32_t *qk = qi + kQueue;                              // walk k
+    uint32_t *qsg = qk + kQueue;                             // gen << 1 | slot
+    uint32_t *qn_steps = qsg + kQueue;                       // N_eps
+    uint32_t *hist = reinterpret_cast<uint32_t *>(
+                         reinterpret_cast<unsigned char *>(smem) +
+                         size_t(blockDim.x >> 5) * queue_bytes<Real, DIM>()) +
+                     warp * (p.nslot > 0 ? p.nslot : 1) * p.hist_words;
+    for (int32_t w = lane; w < p.nslot * p.hist_words; w += 32)
+        hist[w] = 0u;
+    int32_t qn = 0;  // queued exits (warp-uniform)
+    __syncwarp();
+
+    // classify and tally queue entries [q0, q0 + cnt) (cnt <= 32), one per lane
+    auto drain = [&](int32_t q0, int32_t cnt) {
+        if (lane < cnt) {
+            int32_t e = q0 + lane;
+            Real Xe[DIM];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a)
+                Xe[a] = qx[a * kQueue + e];
+            int32_t ei = int32_t(qi[e]);
+            uint32_t sg = qsg[e];
+            int32_t j = classify<Real, DIM>(p.g, Xe);
+            if (p.trace_elem) {
+                size_t q = size_t(ei) * (p.k1 - p.k0) + (qk[e] - p.k0);
+                p.trace_elem[q] = j;
+                if (p.trace_steps) p.trace_steps[q] = qn_steps[e];
+                if (p.trace_x) {
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a)
+                        p.trace_x[q * DIM + a] = double(Xe[a]);
+                }
+            }
+            uint32_t es = sg & 1u, eg = sg >> 1;
+            uint32_t g_now = es ? gen1 : gen0;
+            if (p.nslot > 0 && eg == g_now)
+                atomicAdd(hist + es * p.hist_words + (j >> 1), 1u << ((j & 1) * 16));
+            else
+                atomicAdd(p.counts + size_t(ei) * M + j, 1u);
+        }
+        __syncwarp();
+    };
+
 
     // lane state
     Real X[DIM];
@@ -168,7 +231,8 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
                 whi = uint32_t(wid >> 32);
 #pragma unroll
                 for (int a = 0; a < DIM; ++a)
-                    X[a] = Real(p.points[size_t(li) * DIM + a]);
+                    X[a] = p.points_r ? p.points_r[size_t(li) * DIM + a]
+                                      : Real(p.points[size_t(li) * DIM + a]);
                 nstep = 0;
                 active = true;
                 lslot = slot_cur;
@@ -181,33 +245,31 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
             break;
 
         // ---- one group of G steps of the chain (Eq. (wos chain)) -----------
+        // Branch-free: every step is evaluated and a stopped walk keeps X.
         bool stop = false, capped = false;
         if (active) {
             uint32_t w[4];
             philox4x32_10(nstep / G, wlo, whi, p.stream_id, p.rk, w);
 #pragma unroll
             for (int s = 0; s < G; ++s) {
-                if (!stop) {
-                    Real r = walk_dist<Real, DIM, KIND>(p.g, X);
-                    if (r <= p.eps) {
-                        stop = true;
-                    } else if (nstep >= p.step_cap) {
-                        stop = true;
-                        capped = true;
-                    } else {
-                        Real U[DIM];
-                        direction<Real, DIM>(w + s * WPS, U);
+                Real r = walk_dist<Real, DIM, KIND>(p.g, X);
+                bool at_eps = r <= p.eps;
+                bool at_cap = nstep >= p.step_cap;
+                bool go = !stop && !at_eps && !at_cap;
+                capped = capped || (!stop && !at_eps && at_cap);
+                stop = stop || !go;
+                Real U[DIM];
+                direction<Real, DIM>(w + s * WPS, U);
 #pragma unroll
-                        for (int a = 0; a < DIM; ++a) {
-                            Real su = Real(0);
+                for (int a = 0; a < DIM; ++a) {
+                    Real su = Real(0);
 #pragma unroll
-                            for (int b = 0; b < DIM; ++b)
-                                su += p.S[a * DIM + b] * U[b];
-                            X[a] += r * su;
-                        }
-                        ++nstep;
-                    }
+                    for (int b = 0; b < DIM; ++b)
+                        su += p.S[a * DIM + b] * U[b];
+                    Real xn = X[a] + r * su;
+                    X[a] = go ? xn : X[a];
                 }
+                nstep += go ? 1u : 0u;
             }
         }
         bool fin = active && stop;
@@ -215,40 +277,54 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
         if (!__any_sync(FULL, fin))
             continue;
 
-        // ---- tally the finished walks (Eq. (WoE_matrix_MC)) ----------------
-        if (fin) {
-            int32_t j = capped ? -1 : classify<Real, DIM>(p.g, X);
-            if (p.trace_elem) {
-                size_t q = size_t(li) * (p.k1 - p.k0) + (lk - p.k0);
-                p.trace_elem[q] = j;
-                if (p.trace_steps) p.trace_steps[q] = nstep;
-                if (p.trace_x) {
-#pragma unroll
-                    for (int a = 0; a < DIM; ++a)
-                        p.trace_x[q * DIM + a] = double(X[a]);
-                }
-            }
-            if (j >= 0) {
-                uint32_t g_now = lslot ? gen1 : gen0;
-                if (p.nslot > 0 && lgen == g_now)
-                    atomicAdd(hist + lslot * p.hist_words + (j >> 1),
-                              1u << ((j & 1) * 16));
-                else
-                    atomicAdd(p.counts + size_t(li) * M + j, 1u);
-            } else {
+        // ---- queue the finished walks; tally 32 at a time (Eq. (WoE_matrix_MC))
+        {
+            bool cap_fin = fin && capped;
+            if (cap_fin) {
                 ++my_unterm;
                 if (p.unterm)
                     atomicAdd(p.unterm + li, 1u);
+                if (p.trace_elem) {
+                    size_t q = size_t(li) * (p.k1 - p.k0) + (lk - p.k0);
+                    p.trace_elem[q] = -1;
+                    if (p.trace_steps) p.trace_steps[q] = nstep;
+                    if (p.trace_x) {
+#pragma unroll
+                        for (int a = 0; a < DIM; ++a)
+                            p.trace_x[q * DIM + a] = double(X[a]);
+                    }
+                }
             }
-            my_steps += nstep;
-            ++my_walks;
-            my_max = nstep > my_max ? nstep : my_max;
-            active = false;
+            bool push = fin && !capped;
+            unsigned pm = __ballot_sync(FULL, push);
+            if (push) {
+                int32_t e = qn + int32_t(__popc(pm & lt_mask));
+#pragma unroll
+                for (int a = 0; a < DIM; ++a)
+                    qx[a * kQueue + e] = X[a];
+                qi[e] = uint32_t(li);
+                qk[e] = lk;
+                qsg[e] = (lgen << 1) | uint32_t(lslot);
+                qn_steps[e] = nstep;
+            }
+            qn += int32_t(__popc(pm));
+            if (fin) {
+                my_steps += nstep;
+                ++my_walks;
+                my_max = nstep > my_max ? nstep : my_max;
+                active = false;
+            }
+            __syncwarp();
+            if (qn >= 32) {
+                drain(qn - 32, 32);
+                qn -= 32;
+            }
         }
-        __syncwarp();
     }
 
-    // ---- retire: flush the slots, add the warp's statistics ----------------
+    // ---- retire: drain the queue, flush the slots, add the statistics -------
+    if (qn > 0)
+        drain(0, qn);
     if (p.nslot > 0) {
         if (pt0 >= 0)
             flush_slot(hist, p.hist_words, p.counts + size_t(pt0) * M, lane);

@@ -14,7 +14,7 @@
 
 #include "wos.h"
 #include "wos_internal.h"
-#include "walk_kernel.cuh"
+#include "walk_launch.cuh"
 
 using namespace wos;
 
@@ -487,23 +487,12 @@ extern "C" wos_status wos_check_points(const wos_domain *dp, const double *pts,
 // ---------------------------------------------------------------------------
 namespace {
 
-template <typename Real, int DIM, int KIND>
-const void *kernel_ptr()
-{
-    return reinterpret_cast<const void *>(&walk_kernel<Real, DIM, KIND>);
-}
-
 template <typename Real>
-const void *pick_kernel(int dim, int kind)
+__global__ void convert_points_kernel(const double *in, int n, Real *out)
 {
-    if (dim == 2) {
-        if (kind == kSphereOnly) return kernel_ptr<Real, 2, kSphereOnly>();
-        if (kind == kBoxOnly) return kernel_ptr<Real, 2, kBoxOnly>();
-        return kernel_ptr<Real, 2, kGeneric>();
-    }
-    if (kind == kSphereOnly) return kernel_ptr<Real, 3, kSphereOnly>();
-    if (kind == kBoxOnly) return kernel_ptr<Real, 3, kBoxOnly>();
-    return kernel_ptr<Real, 3, kGeneric>();
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n)
+        out[q] = Real(in[q]);
 }
 
 template <typename Real>
@@ -530,6 +519,7 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
     p.step_cap = o.step_cap ? o.step_cap : 1000000u;
     p.M_D = M_D;
     p.points = points;
+    p.points_r = nullptr;
     p.counts = counts;
     p.unterm = unterm;
     p.trace_elem = o.trace_elem;
@@ -538,66 +528,50 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
     const int32_t M = p.g.M_tot;
     p.hist_words = (M + 1) / 2;
 
-    int kind = kGeneric;
-    if (d.n_holes == 0 && part.voronoi_n <= 0) {
-        if (d.outer_kind == WOS_OUTER_SPHERE) kind = kSphereOnly;
-        else if (d.outer_kind == WOS_OUTER_BOX) kind = kBoxOnly;
-    }
-    const void *kfn = pick_kernel<Real>(dim, kind);
-    int block = o.block_size > 0 ? o.block_size : 256;
-    int warps = block / 32;
-    int nslot = o.hist_slots;
-    size_t slot_bytes = size_t(warps) * p.hist_words * 4;
-    if (nslot == 0) {
-        if (2 * slot_bytes <= 48 * 1024) nslot = 2;
-        else if (slot_bytes <= 96 * 1024) nslot = 1;
-        else nslot = -1;
-    }
-    if (nslot < 0) nslot = 0;
-    size_t smem = size_t(nslot) * slot_bytes;
-    if (smem > size_t(ctx->max_smem_optin)) {
+    const uint64_t per_point = uint64_t(p.k1 - p.k0);
+    WalkPlan plan;
+    wos_status pst = plan_walk_any<Real>(dim, walk_kind(d, part), M, o, ctx->sm_count,
+                                         ctx->max_smem_optin, per_point, M_D, &plan);
+    if (pst != WOS_OK) {
         delete pp;
-        return WOS_INVALID_ARG;
+        return pst;
     }
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem));
-    if (e != cudaSuccess) { delete pp; return cuda_status(e); }
-    int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, block, smem);
-    if (e != cudaSuccess || bps < 1) { delete pp; return e != cudaSuccess ? cuda_status(e) : WOS_INVALID_ARG; }
-    if (o.blocks_per_sm > 0) bps = std::min(bps, o.blocks_per_sm);
-    int grid = ctx->sm_count * bps;
+    const void *kfn = plan.kfn;
+    const int grid = plan.grid, block = plan.block, nslot = plan.nslot;
+    const size_t smem = plan.smem;
+    const uint64_t tw = plan.tile_w;
     p.nslot = nslot;
+    p.tile_w = plan.tile_w;
+    p.tiles_per_point = plan.tiles_per_point;
+    p.n_tiles = plan.n_tiles;
 
-    uint64_t per_point = uint64_t(p.k1 - p.k0);
-    uint64_t total = per_point * uint64_t(M_D);
-    uint64_t tw = o.tile_walks > 0 ? uint64_t(o.tile_walks)
-                                   : total / (16ull * uint64_t(grid) * warps);
-    tw = std::max<uint64_t>(tw, 64);
-    tw = std::min<uint64_t>(tw, 16384);
-    tw = (tw + 31) / 32 * 32;
-    tw = std::min<uint64_t>(tw, per_point);
-    if (tw == 0) tw = 1;
-    p.tile_w = uint32_t(tw);
-    p.tiles_per_point = uint32_t((per_point + tw - 1) / tw);
-    p.n_tiles = uint64_t(p.tiles_per_point) * uint64_t(M_D);
-
-    // per-call scratch: work counters, statistics, Voronoi sites
+    // per-call scratch: work counters, statistics, Voronoi sites and (FP32
+    // walks) the points in walk precision, so that no walk converts FP64
     size_t site_bytes = part.voronoi_n > 0 ? size_t(part.voronoi_n) * dim * sizeof(Real) : 0;
-    size_t scratch_bytes = 64 + site_bytes;
+    site_bytes = (site_bytes + 255) / 256 * 256;
+    const bool convert = sizeof(Real) != sizeof(double);
+    size_t pts_bytes = convert ? size_t(M_D) * dim * sizeof(Real) : 0;
+    size_t scratch_bytes = 256 + site_bytes + pts_bytes;
     void *scratch = nullptr;
-    e = cudaMallocAsync(&scratch, scratch_bytes, stream);
+    cudaError_t e = cudaMallocAsync(&scratch, scratch_bytes, stream);
     if (e != cudaSuccess) { delete pp; return cuda_status(e); }
     p.work = reinterpret_cast<unsigned long long *>(scratch);
     if (site_bytes) {
         std::vector<Real> sites(size_t(part.voronoi_n) * dim);
         for (size_t q = 0; q < sites.size(); ++q)
             sites[q] = Real(part.voronoi_sites[q]);
-        Real *dsites = reinterpret_cast<Real *>(static_cast<char *>(scratch) + 64);
+        Real *dsites = reinterpret_cast<Real *>(static_cast<char *>(scratch) + 256);
         cudaMemcpyAsync(dsites, sites.data(), site_bytes, cudaMemcpyHostToDevice, stream);
         p.g.vsites = dsites;
     }
     cudaMemsetAsync(scratch, 0, 64, stream);
+    if (convert) {
+        Real *dpts = reinterpret_cast<Real *>(static_cast<char *>(scratch) + 256 + site_bytes);
+        int n = M_D * dim;
+        convert_points_kernel<Real><<<(n + 255) / 256, 256, 0, stream>>>(points, n, dpts);
+        count_launches(ctx, 1);
+        p.points_r = dpts;
+    }
     if (!o.accumulate) {
         cudaMemsetAsync(counts, 0, size_t(M_D) * M * 4, stream);
         if (unterm)

@@ -24,7 +24,7 @@
 #include <cstring>
 #include <mutex>
 
-#include "walk_kernel.cuh"
+#include "walk_launch.cuh"
 #include "wos.h"
 #include "wos_internal.h"
 
@@ -67,25 +67,6 @@ wos_status scratch_address(int device, unsigned char **out)
     return WOS_OK;
 }
 
-template <typename Real, int DIM, int KIND>
-const void *kernel_ptr()
-{
-    return reinterpret_cast<const void *>(&walk_kernel<Real, DIM, KIND>);
-}
-
-template <typename Real>
-const void *pick_kernel(int dim, int kind)
-{
-    if (dim == 2) {
-        if (kind == kSphereOnly) return kernel_ptr<Real, 2, kSphereOnly>();
-        if (kind == kBoxOnly) return kernel_ptr<Real, 2, kBoxOnly>();
-        return kernel_ptr<Real, 2, kGeneric>();
-    }
-    if (kind == kSphereOnly) return kernel_ptr<Real, 3, kSphereOnly>();
-    if (kind == kBoxOnly) return kernel_ptr<Real, 3, kBoxOnly>();
-    return kernel_ptr<Real, 3, kGeneric>();
-}
-
 template <typename Real>
 wos_status build_noalloc(wos_context *ctx, unsigned char *scratch, const wos_domain &d,
                          const wos_partition &part, const double *S, const double *points,
@@ -107,6 +88,7 @@ wos_status build_noalloc(wos_context *ctx, unsigned char *scratch, const wos_dom
     p.step_cap = o.step_cap ? o.step_cap : 1000000u;
     p.M_D = M_D;
     p.points = points;
+    p.points_r = nullptr;  // converted per walk: no scratch for a copy
     p.counts = counts;
     p.unterm = unterm;
     p.trace_elem = o.trace_elem;
@@ -115,51 +97,21 @@ wos_status build_noalloc(wos_context *ctx, unsigned char *scratch, const wos_dom
     const int32_t M = p.g.M_tot;
     p.hist_words = (M + 1) / 2;
 
-    int kind = kGeneric;
-    if (d.n_holes == 0 && part.voronoi_n <= 0) {
-        if (d.outer_kind == WOS_OUTER_SPHERE) kind = kSphereOnly;
-        else if (d.outer_kind == WOS_OUTER_BOX) kind = kBoxOnly;
-    }
-    const void *kfn = pick_kernel<Real>(dim, kind);
-    const int block = o.block_size > 0 ? o.block_size : 256;
-    const int warps = block / 32;
-    int nslot = o.hist_slots;
-    const size_t slot_bytes = size_t(warps) * p.hist_words * 4;
-    if (nslot == 0) {
-        if (2 * slot_bytes <= 48 * 1024) nslot = 2;
-        else if (slot_bytes <= 96 * 1024) nslot = 1;
-        else nslot = -1;
-    }
-    if (nslot < 0) nslot = 0;
-    const size_t smem = size_t(nslot) * slot_bytes;
-    if (smem > size_t(ctx_max_smem(ctx)))
-        return WOS_INVALID_ARG;
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem));
-    if (e != cudaSuccess)
-        return cuda_status(e);
-    int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, block, smem);
-    if (e != cudaSuccess)
-        return cuda_status(e);
-    if (bps < 1)
-        return WOS_INVALID_ARG;
-    if (o.blocks_per_sm > 0) bps = std::min(bps, o.blocks_per_sm);
-    const int grid = ctx_sm_count(ctx) * bps;
+    WalkPlan plan;
+    wos_status pst = plan_walk_any<Real>(dim, walk_kind(d, part), M, o, ctx_sm_count(ctx),
+                                         ctx_max_smem(ctx), uint64_t(p.k1 - p.k0), M_D,
+                                         &plan);
+    if (pst != WOS_OK)
+        return pst;
+    const void *kfn = plan.kfn;
+    const int grid = plan.grid, block = plan.block, nslot = plan.nslot;
+    const size_t smem = plan.smem;
+    const uint64_t tw = plan.tile_w;
     p.nslot = nslot;
-
-    const uint64_t per_point = uint64_t(p.k1 - p.k0);
-    const uint64_t total = per_point * uint64_t(M_D);
-    uint64_t tw = o.tile_walks > 0 ? uint64_t(o.tile_walks)
-                                   : total / (16ull * uint64_t(grid) * warps);
-    tw = std::max<uint64_t>(tw, 64);
-    tw = std::min<uint64_t>(tw, 16384);
-    tw = (tw + 31) / 32 * 32;
-    tw = std::min<uint64_t>(tw, per_point);
-    if (tw == 0) tw = 1;
-    p.tile_w = uint32_t(tw);
-    p.tiles_per_point = uint32_t((per_point + tw - 1) / tw);
-    p.n_tiles = uint64_t(p.tiles_per_point) * uint64_t(M_D);
+    p.tile_w = plan.tile_w;
+    p.tiles_per_point = plan.tiles_per_point;
+    p.n_tiles = plan.n_tiles;
+    cudaError_t e = cudaSuccess;
 
     // scratch: counters at offset 0 (cleared every call), sites after them
     p.work = reinterpret_cast<unsigned long long *>(scratch);

@@ -31,6 +31,8 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr double kTol = 1e-15;
 constexpr int kMaxSweeps = 80;
 constexpr int kSvdBlock = 256;
+constexpr int kPairThreads = 128;
+constexpr int kRowsPerThread = 4;  // rows kept in registers per thread
 
 struct SvdWork {
     double *W;        // m x n, column-major (column j contiguous)
@@ -39,6 +41,7 @@ struct SvdWork {
     int n_pad;        // n rounded up to even (a dummy column when odd)
     unsigned *bar;    // [0] arrive count, [1] generation, [2..4] rotation
                       // counters of sweeps mod 3, [5] status, [6] sweeps
+    unsigned *ver;    // n_pad column versions (rounds finished per column)
 };
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -93,70 +96,178 @@ __device__ __forceinline__ int rr_player(int pos, int r, int n_pad)
     return 1 + (pos - 1 + r) % (n_pad - 1);
 }
 
-__global__ void __launch_bounds__(kSvdBlock)
+// Wait (bounded, about 2 s) until column version ver[c] >= want.
+__device__ bool wait_version(const unsigned *ver, int c, unsigned want, unsigned *status)
+{
+    const volatile unsigned *v = ver + c;
+    if (*v >= want)
+        return true;
+    long long t0 = clock64();
+    while (*v < want) {
+        __nanosleep(20);
+        if (clock64() - t0 > 4000000000LL) {
+            atomicExch(status, unsigned(WOS_DEVICE_TIMEOUT));
+            return false;
+        }
+        if (*(volatile unsigned *)status != 0u)
+            return false;
+    }
+    return true;
+}
+
+// One pair per CTA of kPairThreads threads; the m rows are split over the
+// CTA so a pair uses a whole SM's FP64 pipe.  Rounds are ordered by column
+// versions: ver[c] counts the rounds that have finished with column c, so the
+// pair (p, q) of global round R starts once ver[p] >= R and ver[q] >= R (the
+// previous round's writers of p and q are done).  Only one grid barrier per
+// sweep remains, for the convergence test.  Columns are read and written
+// through L2 (ld.cg / st.cg): other SMs update them between rounds.
+__global__ void __launch_bounds__(kPairThreads)
 jacobi_kernel(SvdWork w)
 {
-    const int lane = threadIdx.x & 31;
-    const int warps_per_block = blockDim.x >> 5;
-    const int gwarp = blockIdx.x * warps_per_block + (threadIdx.x >> 5);
-    const int nwarps = gridDim.x * warps_per_block;
+    __shared__ double part[3][kPairThreads / 32];
+    __shared__ double cs[2];
+    __shared__ int go, flag;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int half = w.n_pad / 2;
     const int m = w.m, n = w.n;
+    unsigned *status = w.bar + 5;
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
         unsigned *rot = w.bar + 2 + (sweep % 3);
-        if (blockIdx.x == 0 && threadIdx.x == 0)
+        if (blockIdx.x == 0 && tid == 0)
             w.bar[2 + ((sweep + 1) % 3)] = 0u;
         for (int r = 0; r < w.n_pad - 1; ++r) {
-            for (int pr = gwarp; pr < half; pr += nwarps) {
+            const unsigned R = unsigned(sweep) * unsigned(w.n_pad - 1) + unsigned(r);
+            for (int pr = blockIdx.x; pr < half; pr += gridDim.x) {
                 int a = rr_player(pr, r, w.n_pad);
                 int b = rr_player(w.n_pad - 1 - pr, r, w.n_pad);
                 int p = min(a, b), q = max(a, b);
-                if (q >= n)
-                    continue;  // the dummy column of odd n
-                double *wp = w.W + size_t(p) * m, *wq = w.W + size_t(q) * m;
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int i = lane; i < m; i += 32) {
-                    double x = wp[i], y = wq[i];
-                    al = fma(x, x, al);
-                    be = fma(y, y, be);
-                    ga = fma(x, y, ga);
+                if (tid == 0) {
+                    bool ok = wait_version(w.ver, p, R, status);
+                    if (ok && q < n)
+                        ok = wait_version(w.ver, q, R, status);
+                    __threadfence();
+                    go = ok;
                 }
-                al = warp_sum(al);
-                be = warp_sum(be);
-                ga = warp_sum(ga);
-                if (al == 0.0 || be == 0.0)
-                    continue;
-                if (fabs(ga) <= kTol * sqrt(al) * sqrt(be))
-                    continue;
-                double zeta = (be - al) / (2.0 * ga);
-                double t = (zeta >= 0.0 ? 1.0 : -1.0) /
-                           (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                double c = 1.0 / sqrt(1.0 + t * t);
-                double s = c * t;
-                for (int i = lane; i < m; i += 32) {
-                    double x = wp[i], y = wq[i];
-                    wp[i] = c * x - s * y;
-                    wq[i] = s * x + c * y;
+                __syncthreads();
+                if (!go)
+                    return;
+                bool rotated = false;
+                if (q < n) {
+                    double *wp = w.W + size_t(p) * m, *wq = w.W + size_t(q) * m;
+                    double *vp = w.Vw + size_t(p) * n, *vq = w.Vw + size_t(q) * n;
+                    // this thread's rows stay in registers between the dot
+                    // products and the rotation (m <= kRowsPerThread * CTA)
+                    double xr[kRowsPerThread], yr[kRowsPerThread];
+                    double vx[kRowsPerThread], vy[kRowsPerThread];
+                    double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+                    for (int k = 0; k < kRowsPerThread; ++k) {
+                        int i = tid + k * kPairThreads;
+                        xr[k] = i < m ? __ldcg(wp + i) : 0.0;
+                        yr[k] = i < m ? __ldcg(wq + i) : 0.0;
+                        vx[k] = i < n ? __ldcg(vp + i) : 0.0;
+                        vy[k] = i < n ? __ldcg(vq + i) : 0.0;
+                    }
+#pragma unroll
+                    for (int k = 0; k < kRowsPerThread; ++k) {
+                        al = fma(xr[k], xr[k], al);
+                        be = fma(yr[k], yr[k], be);
+                        ga = fma(xr[k], yr[k], ga);
+                    }
+                    for (int i = tid + kRowsPerThread * kPairThreads; i < m; i += kPairThreads) {
+                        double x = __ldcg(wp + i), y = __ldcg(wq + i);
+                        al = fma(x, x, al);
+                        be = fma(y, y, be);
+                        ga = fma(x, y, ga);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        al += __shfl_xor_sync(FULL, al, o);
+                        be += __shfl_xor_sync(FULL, be, o);
+                        ga += __shfl_xor_sync(FULL, ga, o);
+                    }
+                    if (lane == 0) {
+                        part[0][wid] = al;
+                        part[1][wid] = be;
+                        part[2][wid] = ga;
+                    }
+                    __syncthreads();
+                    // one thread combines the partial sums and computes the
+                    // rotation (FP64 is scarce on this part: 2 FMA/clk/SM)
+                    if (tid == 0) {
+                        al = be = ga = 0.0;
+#pragma unroll
+                        for (int k = 0; k < kPairThreads / 32; ++k) {
+                            al += part[0][k];
+                            be += part[1][k];
+                            ga += part[2][k];
+                        }
+                        double c = 1.0, sn = 0.0;
+                        int rot_flag = 0;
+                        // rotate when |ga| > tol sqrt(al be), tested squared
+                        if (al != 0.0 && be != 0.0 && ga * ga > (kTol * kTol) * (al * be)) {
+                            // t = ga / (h + sign(h) sqrt(h^2 + ga^2)), h = (be - al) / 2:
+                            // the smaller root of t^2 + 2 zeta t - 1, zeta = h / ga
+                            double h = 0.5 * (be - al);
+                            double rt = sqrt(fma(h, h, ga * ga));
+                            double t = ga / (h >= 0.0 ? h + rt : h - rt);
+                            c = rsqrt(fma(t, t, 1.0));
+                            sn = c * t;
+                            rot_flag = 1;
+                        }
+                        cs[0] = c;
+                        cs[1] = sn;
+                        flag = rot_flag;
+                    }
+                    __syncthreads();
+                    if (flag) {
+                        rotated = true;
+                        const double c = cs[0], s = cs[1];
+#pragma unroll
+                        for (int k = 0; k < kRowsPerThread; ++k) {
+                            int i = tid + k * kPairThreads;
+                            if (i < m) {
+                                __stcg(wp + i, c * xr[k] - s * yr[k]);
+                                __stcg(wq + i, s * xr[k] + c * yr[k]);
+                            }
+                            if (i < n) {
+                                __stcg(vp + i, c * vx[k] - s * vy[k]);
+                                __stcg(vq + i, s * vx[k] + c * vy[k]);
+                            }
+                        }
+                        for (int i = tid + kRowsPerThread * kPairThreads; i < m; i += kPairThreads) {
+                            double x = __ldcg(wp + i), y = __ldcg(wq + i);
+                            __stcg(wp + i, c * x - s * y);
+                            __stcg(wq + i, s * x + c * y);
+                        }
+                        for (int i = tid + kRowsPerThread * kPairThreads; i < n; i += kPairThreads) {
+                            double x = __ldcg(vp + i), y = __ldcg(vq + i);
+                            __stcg(vp + i, c * x - s * y);
+                            __stcg(vq + i, s * x + c * y);
+                        }
+                    }
                 }
-                double *vp = w.Vw + size_t(p) * n, *vq = w.Vw + size_t(q) * n;
-                for (int i = lane; i < n; i += 32) {
-                    double x = vp[i], y = vq[i];
-                    vp[i] = c * x - s * y;
-                    vq[i] = s * x + c * y;
+                __syncthreads();
+                if (tid == 0) {
+                    __threadfence();
+                    atomicExch(w.ver + p, R + 1u);
+                    if (q < n)
+                        atomicExch(w.ver + q, R + 1u);
+                    if (rotated)
+                        atomicAdd(rot, 1u);
                 }
-                if (lane == 0)
-                    atomicAdd(rot, 1u);
             }
-            if (!grid_barrier(w.bar, gridDim.x))
-                return;
         }
+        if (!grid_barrier(w.bar, gridDim.x))
+            return;
         bool done = *(volatile unsigned *)rot == 0u;
-        if (blockIdx.x == 0 && threadIdx.x == 0)
+        if (blockIdx.x == 0 && tid == 0)
             w.bar[6] = unsigned(sweep + 1);
         if (done)
             return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0)
+    if (blockIdx.x == 0 && tid == 0)
         atomicExch(w.bar + 5, unsigned(WOS_NO_CONVERGENCE));
 }
 
@@ -353,7 +464,8 @@ extern "C" wos_status wos_op_svd(wos_context *ctx, const uint32_t *counts, int32
     w.n_pad = w.n + (w.n & 1);
     if (w.n_pad < 2) w.n_pad = 2;
     size_t bytes_W = size_t(w.m) * w.n * 8, bytes_V = size_t(w.n) * w.n * 8;
-    size_t bytes = bytes_W + bytes_V + size_t(w.n) * 8 + 64 + size_t(M_1) * 4;
+    size_t bytes_ver = (size_t(w.n_pad) * 4 + 255) / 256 * 256;
+    size_t bytes = bytes_W + bytes_V + size_t(w.n) * 8 + 64 + bytes_ver + size_t(M_1) * 4;
     char *base = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&base), bytes, st);
     if (e != cudaSuccess)
@@ -362,21 +474,22 @@ extern "C" wos_status wos_op_svd(wos_context *ctx, const uint32_t *counts, int32
     w.Vw = reinterpret_cast<double *>(base + bytes_W);
     double *sv = reinterpret_cast<double *>(base + bytes_W + bytes_V);
     w.bar = reinterpret_cast<unsigned *>(base + bytes_W + bytes_V + size_t(w.n) * 8);
-    int *g1 = reinterpret_cast<int *>(base + bytes_W + bytes_V + size_t(w.n) * 8 + 64);
-    cudaMemsetAsync(w.bar, 0, 64, st);
+    w.ver = reinterpret_cast<unsigned *>(base + bytes_W + bytes_V + size_t(w.n) * 8 + 64);
+    int *g1 = reinterpret_cast<int *>(base + bytes_W + bytes_V + size_t(w.n) * 8 + 64 +
+                                      bytes_ver);
+    cudaMemsetAsync(w.bar, 0, 64 + bytes_ver, st);
     cudaMemcpyAsync(g1, L.g1.data(), size_t(M_1) * 4, cudaMemcpyHostToDevice, st);
     int sms = wos::ctx_sm_count(ctx);
     form_B_kernel<<<sms * 4, 256, 0, st>>>(w, counts, M_D, M_tot, 1.0 / double(N), g1, M_1,
                                           nu, sigma, transposed);
-    // cooperative Jacobi: one warp per pair, all blocks co-resident
+    // cooperative Jacobi: one pair per CTA at a time, all CTAs co-resident
     int bps = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, jacobi_kernel, kSvdBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, jacobi_kernel, kPairThreads, 0);
     int pairs = w.n_pad / 2;
-    int want = (pairs + kSvdBlock / 32 - 1) / (kSvdBlock / 32);
-    int grid = std::max(1, std::min(want, std::max(1, bps) * sms));
+    int grid = std::max(1, std::min({pairs, 2 * sms, std::max(1, bps) * sms}));
     void *args[] = {&w};
     e = cudaLaunchCooperativeKernel(reinterpret_cast<void *>(jacobi_kernel), dim3(grid),
-                                    dim3(kSvdBlock), args, 0, st);
+                                    dim3(kPairThreads), args, 0, st);
     if (e == cudaSuccess) {
         column_norms_kernel<<<sms, 256, 0, st>>>(w, sv);
         finalize_kernel<<<sms, 256, 0, st>>>(w, sv, transposed, U, S, V);
