@@ -84,6 +84,19 @@ __device__ __forceinline__ Real walk_dist(const Geom<Real> &g, const Real *x)
     return domain_dist<Real, DIM>(g, x);
 }
 
+// The element of a stopped point, with only the code the kernel kind needs.
+template <typename Real, int DIM, int KIND>
+__device__ __forceinline__ int32_t walk_classify(const Geom<Real> &g, const Real *x)
+{
+    if (KIND == kSphereOnly)
+        return outer_sphere_cell<Real, DIM>(g, x);
+    if (KIND == kBoxOnly)
+        return outer_box_cell<Real, DIM>(g, x);
+    if (KIND == kSphereHoles)
+        return sphere_holes_cell<Real, DIM>(g, x);
+    return classify<Real, DIM>(g, x);
+}
+
 constexpr int kQueue = 64;  // per-warp exit queue (entries)
 
 // Shared-memory bytes of one warp's exit queue.
@@ -156,7 +169,7 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
                 Xe[a] = qx[a * kQueue + e];
             int32_t ei = int32_t(qi[e]);
             uint32_t sg = qsg[e];
-            int32_t j = classify<Real, DIM>(p.g, Xe);
+            int32_t j = walk_classify<Real, DIM, KIND>(p.g, Xe);
             if (p.trace_elem) {
                 size_t q = size_t(ei) * (p.k1 - p.k0) + (qk[e] - p.k0);
                 p.trace_elem[q] = j;

@@ -35,7 +35,19 @@ enum OuterKind : int32_t { kSphere = 1, kBox = 2, kPolygon = 3 };
 // ---------------------------------------------------------------------------
 // scalar helpers that resolve to the device intrinsics or the host libm
 // ---------------------------------------------------------------------------
-WOS_HD float w_sqrt(float x) { return sqrtf(x); }
+// FP32 square root: on the device the SFU approximation (sqrt.approx.f32,
+// no slow path; exact at 0 and inf): the distances it feeds only need to sit
+// far inside the eps-shell, which FP32 rounding already limits.
+WOS_HD float w_sqrt(float x)
+{
+#ifdef __CUDA_ARCH__
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+#else
+    return sqrtf(x);
+#endif
+}
 WOS_HD double w_sqrt(double x) { return sqrt(x); }
 WOS_HD float w_floor(float x) { return floorf(x); }
 WOS_HD double w_floor(double x) { return floor(x); }
@@ -248,41 +260,81 @@ WOS_HD Real domain_dist(const Geom<Real> &g, const Real *x)
     return r;
 }
 
-// Element of the outer component holding pi(x).
+// Cell of pi(x) on an outer sphere (circle arcs / z-band x sector patches).
 template <typename Real, int DIM>
-WOS_HD int32_t outer_cell(const Geom<Real> &g, const Real *x)
+WOS_HD int32_t outer_sphere_cell(const Geom<Real> &g, const Real *x)
+{
+    Real v0 = x[0] - g.c[0], v1 = x[1] - g.c[1];
+    if (DIM == 2)
+        return circle_cell(v0, v1, g.outer_m, g.outer_t0);
+    return sphere_cell(v0, v1, x[DIM - 1] - g.c[DIM - 1], g.nb, g.ns);
+}
+
+// Cell of pi(x) on a box: nearest side / face, then its cell.
+template <typename Real, int DIM>
+WOS_HD int32_t outer_box_cell(const Geom<Real> &g, const Real *x)
 {
     Real v[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
         v[a] = x[a] - g.c[a];
-    if (g.outer_kind == kSphere) {
-        if (DIM == 2)
-            return circle_cell(v[0], v[1], g.outer_m, g.outer_t0);
-        return sphere_cell(v[0], v[1], v[2], g.nb, g.ns);
+    int32_t f;
+    box_dist<Real, DIM>(g, x, &f);
+    if (DIM == 2) {
+        Real t;
+        if (f == 0) t = (v[0] + g.h[0]) / (Real(2) * g.h[0]);
+        else if (f == 1) t = (v[1] + g.h[1]) / (Real(2) * g.h[1]);
+        else if (f == 2) t = (g.h[0] - v[0]) / (Real(2) * g.h[0]);
+        else t = (g.h[1] - v[1]) / (Real(2) * g.h[1]);
+        return g.edge_off[f] + cell_of(t, g.edge_m[f]);
     }
-    if (g.outer_kind == kBox) {
-        int32_t f;
-        box_dist<Real, DIM>(g, x, &f);
-        if (DIM == 2) {
-            Real t;
-            if (f == 0) t = (v[0] + g.h[0]) / (Real(2) * g.h[0]);
-            else if (f == 1) t = (v[1] + g.h[1]) / (Real(2) * g.h[1]);
-            else if (f == 2) t = (g.h[0] - v[0]) / (Real(2) * g.h[0]);
-            else t = (g.h[1] - v[1]) / (Real(2) * g.h[1]);
-            return g.edge_off[f] + cell_of(t, g.edge_m[f]);
-        }
-        int ax = f % 3;
-        int b0 = ax == 0 ? 1 : 0;
-        int b1 = ax == 2 ? 1 : 2;
-        Real t0 = (v[b0] + g.h[b0]) / (Real(2) * g.h[b0]);
-        Real t1 = (v[b1] + g.h[b1]) / (Real(2) * g.h[b1]);
-        return f * g.n1 * g.n2 + cell_of(t0, g.n1) * g.n2 + cell_of(t1, g.n2);
-    }
+    int ax = f % 3;
+    int b0 = ax == 0 ? 1 : 0;
+    int b1 = ax == 2 ? 1 : 2;
+    Real t0 = (v[b0] + g.h[b0]) / (Real(2) * g.h[b0]);
+    Real t1 = (v[b1] + g.h[b1]) / (Real(2) * g.h[b1]);
+    return f * g.n1 * g.n2 + cell_of(t0, g.n1) * g.n2 + cell_of(t1, g.n2);
+}
+
+// Element of the outer component holding pi(x).
+template <typename Real, int DIM>
+WOS_HD int32_t outer_cell(const Geom<Real> &g, const Real *x)
+{
+    if (g.outer_kind == kSphere)
+        return outer_sphere_cell<Real, DIM>(g, x);
+    if (g.outer_kind == kBox)
+        return outer_box_cell<Real, DIM>(g, x);
     int32_t e;
     Real t;
     polygon_dist<Real>(g, x, &e, &t);
     return g.edge_off[e] + cell_of(t, g.edge_m[e]);
+}
+
+// Cell of pi(x) on hole `comp`.
+template <typename Real, int DIM>
+WOS_HD int32_t hole_cell(const Geom<Real> &g, int comp, const Real *x)
+{
+    Real vx = x[0] - g.hc[comp][0], vy = x[1] - g.hc[comp][1];
+    if (DIM == 2)
+        return g.hole_off[comp] + circle_cell(vx, vy, g.hole_m[comp], g.hole_t0[comp]);
+    Real vz = x[DIM - 1] - g.hc[comp][DIM - 1];
+    return g.hole_off[comp] + sphere_cell(vx, vy, vz, g.hole_nb[comp], g.hole_ns[comp]);
+}
+
+// Sphere with holes: nearest component (outer first, lowest hole on ties).
+template <typename Real, int DIM>
+WOS_HD int32_t sphere_holes_cell(const Geom<Real> &g, const Real *x)
+{
+    Real best = sphere_dist<Real, DIM>(g, x);
+    int32_t comp = -1;
+    for (int hidx = 0; hidx < g.n_holes; ++hidx) {
+        Real rh = hole_dist<Real, DIM>(g, hidx, x);
+        if (rh < best) {
+            best = rh;
+            comp = hidx;
+        }
+    }
+    return comp < 0 ? outer_sphere_cell<Real, DIM>(g, x) : hole_cell<Real, DIM>(g, comp, x);
 }
 
 // The element j of a stopped point: extrinsic Voronoi site, or the cell of
@@ -318,13 +370,7 @@ WOS_HD int32_t classify(const Geom<Real> &g, const Real *x)
             comp = hidx;
         }
     }
-    if (comp < 0)
-        return outer_cell<Real, DIM>(g, x);
-    Real vx = x[0] - g.hc[comp][0], vy = x[1] - g.hc[comp][1];
-    if (DIM == 2)
-        return g.hole_off[comp] + circle_cell(vx, vy, g.hole_m[comp], g.hole_t0[comp]);
-    Real vz = x[DIM - 1] - g.hc[comp][DIM - 1];
-    return g.hole_off[comp] + sphere_cell(vx, vy, vz, g.hole_nb[comp], g.hole_ns[comp]);
+    return comp < 0 ? outer_cell<Real, DIM>(g, x) : hole_cell<Real, DIM>(g, comp, x);
 }
 
 // ---------------------------------------------------------------------------
@@ -379,7 +425,16 @@ template <> struct Uniform<double> {
     }
 };
 
-__device__ __forceinline__ void w_sincospi(float x, float *s, float *c) { sincospif(x, s, c); }
+// sin(pi x), cos(pi x) for x = 2u in [0, 2): FP32 walks use the SFU sine and
+// cosine on the angle pi (x - 1) in [-pi, pi) -- the range of their
+// documented absolute error bound (2^-21.41) -- and flip both signs.
+__device__ __forceinline__ void w_sincospi(float x, float *s, float *c)
+{
+    float ss, cc;
+    __sincosf(3.14159265358979f * (x - 1.0f), &ss, &cc);
+    *s = -ss;
+    *c = -cc;
+}
 __device__ __forceinline__ void w_sincospi(double x, double *s, double *c) { sincospi(x, s, c); }
 
 // U uniform on S^{d-1}: d = 2 (cos 2 pi u, sin 2 pi u); d = 3 Archimedes:

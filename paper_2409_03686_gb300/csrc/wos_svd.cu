@@ -33,6 +33,7 @@ constexpr int kMaxSweeps = 80;
 constexpr int kSvdBlock = 256;
 constexpr int kPairThreads = 128;
 constexpr int kRowsPerThread = 4;  // rows kept in registers per thread
+static_assert(kPairThreads == 128, "the partial sums below assume four warps");
 
 struct SvdWork {
     double *W;        // m x n, column-major (column j contiguous)
@@ -96,23 +97,36 @@ __device__ __forceinline__ int rr_player(int pos, int r, int n_pad)
     return 1 + (pos - 1 + r) % (n_pad - 1);
 }
 
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *a)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *a, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
 // Wait (bounded, about 2 s) until column version ver[c] >= want.
 __device__ bool wait_version(const unsigned *ver, int c, unsigned want, unsigned *status)
 {
-    const volatile unsigned *v = ver + c;
-    if (*v >= want)
+    if (ld_acquire(ver + c) >= want)
         return true;
     long long t0 = clock64();
-    while (*v < want) {
-        __nanosleep(20);
-        if (clock64() - t0 > 4000000000LL) {
-            atomicExch(status, unsigned(WOS_DEVICE_TIMEOUT));
-            return false;
+    for (unsigned it = 1;; ++it) {
+        if (ld_acquire(ver + c) >= want)
+            return true;
+        if ((it & 63u) == 0u) {
+            if (clock64() - t0 > 4000000000LL) {
+                atomicExch(status, unsigned(WOS_DEVICE_TIMEOUT));
+                return false;
+            }
+            if (*(volatile unsigned *)status != 0u)
+                return false;
         }
-        if (*(volatile unsigned *)status != 0u)
-            return false;
     }
-    return true;
 }
 
 // One pair per CTA of kPairThreads threads; the m rows are split over the
@@ -146,7 +160,6 @@ jacobi_kernel(SvdWork w)
                     bool ok = wait_version(w.ver, p, R, status);
                     if (ok && q < n)
                         ok = wait_version(w.ver, q, R, status);
-                    __threadfence();
                     go = ok;
                 }
                 __syncthreads();
@@ -196,13 +209,10 @@ jacobi_kernel(SvdWork w)
                     // one thread combines the partial sums and computes the
                     // rotation (FP64 is scarce on this part: 2 FMA/clk/SM)
                     if (tid == 0) {
-                        al = be = ga = 0.0;
-#pragma unroll
-                        for (int k = 0; k < kPairThreads / 32; ++k) {
-                            al += part[0][k];
-                            be += part[1][k];
-                            ga += part[2][k];
-                        }
+                        // pairwise sums of the four warp partials
+                        al = (part[0][0] + part[0][1]) + (part[0][2] + part[0][3]);
+                        be = (part[1][0] + part[1][1]) + (part[1][2] + part[1][3]);
+                        ga = (part[2][0] + part[2][1]) + (part[2][2] + part[2][3]);
                         double c = 1.0, sn = 0.0;
                         int rot_flag = 0;
                         // rotate when |ga| > tol sqrt(al be), tested squared
@@ -250,10 +260,12 @@ jacobi_kernel(SvdWork w)
                 }
                 __syncthreads();
                 if (tid == 0) {
+                    // the CTA's stores are ordered before the flags by the
+                    // barrier above and the release fence here
                     __threadfence();
-                    atomicExch(w.ver + p, R + 1u);
+                    st_release(w.ver + p, R + 1u);
                     if (q < n)
-                        atomicExch(w.ver + q, R + 1u);
+                        st_release(w.ver + q, R + 1u);
                     if (rotated)
                         atomicAdd(rot, 1u);
                 }
