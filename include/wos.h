@@ -233,6 +233,39 @@ wos_status wos_build_operator_noalloc(wos_context *ctx, const wos_domain *domain
                                       uint32_t *unterminated, wos_stats *stats,
                                       void *stream);
 
+/* One operator build of a batch (see wos_build_operators_batched).  Host
+ * descriptors are read during the call; device arrays as in
+ * wos_build_operator. */
+typedef struct {
+    const wos_domain *domain;
+    const wos_partition *partition;
+    const double *K;          /* host, dim x dim */
+    const double *points;     /* device, M_D x dim */
+    int32_t M_D;
+    uint32_t N;               /* walks per point */
+    double eps;
+    uint32_t stream_id;       /* fourth Philox counter word of this problem */
+    uint32_t step_cap;        /* 0 = 1,000,000 */
+    uint32_t *counts;         /* device, M_D x M_tot */
+    uint32_t *unterminated;   /* device, M_D, or NULL */
+} wos_problem;
+
+/* Many MC-REM builds (paper Sec. 5.1, Algorithm MC-REM, applied to each
+ * problem) in one persistent launch per dimension: the walks of all the
+ * problems of one dimension share a global tile queue, so problems of very
+ * different sizes and walk lengths keep the whole GPU busy.  All problems
+ * share `seed` and opts->precision; each problem's walks use counter
+ * (block, walk lo, walk hi, stream_id), so its counts are bit-identical to
+ * the same problem built alone with wos_build_operator (same stream_id).
+ * opts may set precision, accumulate and the launch fields (block_size,
+ * blocks_per_sm, tile_walks, hist_slots, kernel_events); k0 / k1 and traces
+ * must be zero.  stats (host or NULL): totals over the batch; non-NULL waits.
+ * Errors: those of wos_build_operator, for the first failing problem. */
+wos_status wos_build_operators_batched(wos_context *ctx, int32_t n,
+                                       const wos_problem *problems, uint64_t seed,
+                                       const wos_opts *opts, wos_stats *stats,
+                                       void *stream);
+
 /* Check that every point (host, M_D x dim) lies strictly inside D.  Returns
  * WOS_OK or WOS_POINT_OUTSIDE (first offending index in *bad if non-NULL). */
 wos_status wos_check_points(const wos_domain *domain, const double *points,

@@ -7,20 +7,23 @@
 // Design (one GB300, no tensor cores: the chain is scalar ALU/SFU work):
 //  * Persistent grid: blocks_per_SM x SMs; every warp loops until the tile
 //    queue is empty and its lanes are idle.
-//  * Work = walks (i, k).  A tile is a run of walks k0..k1 of one point i;
-//    warps take tiles from a global counter (one atomic per tile).
+//  * Work = walks (instance, point i, walk k).  A tile is a run of walks of
+//    one point; warps take tiles from a global counter (one atomic per tile).
+//    One launch serves one instance (its record in the constant bank) or a
+//    batch of instances of one precision and dimension (records in global
+//    memory, each lane reading its own walk's record through L1).
 //  * Every lane owns one walk at a time.  Walks advance in groups of G steps
 //    that share one Philox4x32-10 block (G = 4 words / words per step), so all
 //    lanes call Philox together; a lane whose walk stops mid-group idles to
-//    the group's end.  At a group boundary the finished lanes tally their
-//    exit element and are refilled from the warp's tile (warp-level refill:
-//    ballot + popc ranks), so warps stay full despite geometric walk lengths.
+//    the group's end.  At a group boundary the finished lanes are refilled
+//    from the warp's tile (warp-level refill: ballot + popc ranks), so warps
+//    stay full despite geometric walk lengths.
 //  * The Philox counter of step n of walk w is (n / G, w lo, w hi, stream):
-//    results do not depend on scheduling.
+//    results do not depend on scheduling or on the batch a walk runs in.
 //  * A finished lane only pushes its stopped point into a per-warp queue in
 //    shared memory; once 32 are queued the whole warp classifies them (pi of
 //    App. A) and tallies them at full lane efficiency.
-//  * Tally: each warp owns NSLOT shared-memory histograms (one per tile in
+//  * Tally: each warp owns up to two shared-memory histograms (one per tile in
 //    flight), two uint16 counts per 32-bit word (a tile has < 65536 walks).
 //    A slot is flushed to HBM with coalesced integer atomics when its tile is
 //    retired; a walk that outlives its slot (generation mismatch) adds to HBM
@@ -35,12 +38,12 @@ namespace wos {
 
 enum KernelKind : int { kGeneric = 0, kSphereOnly = 1, kBoxOnly = 2, kSphereHoles = 3 };
 
-template <typename Real> struct WalkParams {
+// One instance of the operator build.
+template <typename Real> struct WalkInst {
     Geom<Real> g;
     Real S[9];            // (K / lambda_max)^{1/2}, row-major DIM x DIM
     Real eps;
-    uint32_t rk[20];      // Philox key schedule
-    uint32_t stream_id;   // fourth counter word
+    uint32_t stream_id;   // fourth Philox counter word
     uint32_t N;           // walks per point: walk id = i * N + k
     uint32_t k0, k1;      // walk range of every point
     uint32_t step_cap;
@@ -49,17 +52,24 @@ template <typename Real> struct WalkParams {
     const Real *points_r; // the same in walk precision, or null (convert here)
     uint32_t *counts;     // device, M_D x M_tot
     uint32_t *unterm;     // device, M_D (may be null)
-    int32_t *trace_elem;  // optional traces (tests)
+    uint32_t tile_w;      // walks per tile
+    uint32_t tiles_per_point;
+    uint64_t tile_begin;  // first global tile of this instance (batches)
+};
+
+template <typename Real> struct WalkParams {
+    WalkInst<Real> one;          // the instance of a single-instance launch
+    const WalkInst<Real> *insts; // batch: instance records (device)
+    int32_t n_inst;
+    uint32_t rk[20];             // Philox key schedule (shared by a batch)
+    int32_t *trace_elem;         // optional traces (single instance; tests)
     uint32_t *trace_steps;
     double *trace_x;
-    // scheduling
-    uint32_t tile_w;           // walks per tile
-    uint32_t tiles_per_point;
     uint64_t n_tiles;
-    unsigned long long *work;  // [0] tile counter, [1] steps, [2] walks,
-                               // [3] unterminated, [4] max steps
-    int32_t nslot;             // 0 (global tally), 1 or 2
-    int32_t hist_words;        // ceil(M_tot / 2)
+    unsigned long long *work;    // [0] tile counter, [1] steps, [2] walks,
+                                 // [3] unterminated, [4] max steps
+    int32_t nslot;               // 0 (global tally), 1 or 2
+    int32_t hist_words;          // ceil(M_tot / 2), max over a batch
 };
 
 template <typename Real, int DIM> struct Steps {
@@ -99,14 +109,15 @@ __device__ __forceinline__ int32_t walk_classify(const Geom<Real> &g, const Real
 
 constexpr int kQueue = 64;  // per-warp exit queue (entries)
 
-// Shared-memory bytes of one warp's exit queue.
+// Shared-memory bytes of one warp's exit queue: DIM coordinates and five
+// words (point, instance, walk k, slot generation, N_eps) per entry.
 template <typename Real, int DIM>
 __host__ __device__ constexpr size_t queue_bytes()
 {
-    return size_t(kQueue) * (DIM * sizeof(Real) + 4 * sizeof(uint32_t));
+    return size_t(kQueue) * (DIM * sizeof(Real) + 5 * sizeof(uint32_t));
 }
 
-// Flush one warp-private slot into the counts row of point `pt`.
+// Flush one warp-private slot into a counts row.
 __device__ __forceinline__ void flush_slot(uint32_t *slot, int32_t words,
                                            uint32_t *counts_row, int lane)
 {
@@ -122,7 +133,7 @@ __device__ __forceinline__ void flush_slot(uint32_t *slot, int32_t words,
     __syncwarp();
 }
 
-template <typename Real, int DIM, int KIND>
+template <typename Real, int DIM, int KIND, bool MULTI>
 __global__ void __launch_bounds__(256, 4)
 walk_kernel(const __grid_constant__ WalkParams<Real> p)
 {
@@ -130,26 +141,30 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
     constexpr int WPS = Steps<Real, DIM>::kWordsPerStep;
     constexpr unsigned FULL = 0xFFFFFFFFu;
     extern __shared__ uint32_t smem[];
+    const WalkInst<Real> *__restrict__ insts = p.insts;
+    auto inst = [&](int32_t q) -> const WalkInst<Real> & {
+        return MULTI ? insts[q] : p.one;
+    };
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int32_t M = p.g.M_tot;
     // warp-uniform tile / slot state
-    int32_t tile_i = 0;
+    int32_t tile_inst = 0, tile_i = 0;
     uint32_t tile_k = 0, tile_kend = 0;
     bool no_more = false;
     int32_t slot_cur = 0;
     uint32_t gen0 = 0, gen1 = 0;
-    int32_t pt0 = -1, pt1 = -1;
+    int32_t pt0 = -1, pt1 = -1, in0 = 0, in1 = 0;
     // shared memory: [exit queues of all warps][histogram slots of all warps]
     unsigned char *qbase = reinterpret_cast<unsigned char *>(smem) +
                            size_t(warp) * queue_bytes<Real, DIM>();
-    Real *qx = reinterpret_cast<Real *>(qbase);             // [DIM][kQueue]
+    Real *qx = reinterpret_cast<Real *>(qbase);                      // [DIM][kQueue]
     uint32_t *qi = reinterpret_cast<uint32_t *>(qx + DIM * kQueue);  // point
-    uint32_t *qk = qi + kQueue;                              // walk k
-    uint32_t *qsg = qk + kQueue;                             // gen << 1 | slot
-    uint32_t *qn_steps = qsg + kQueue;                       // N_eps
+    uint32_t *qinst = qi + kQueue;                                   // instance
+    uint32_t *qk = qinst + kQueue;                                   // walk k
+    uint32_t *qsg = qk + kQueue;                                     // gen << 1 | slot
+    uint32_t *qn_steps = qsg + kQueue;                               // N_eps
     uint32_t *hist = reinterpret_cast<uint32_t *>(
                          reinterpret_cast<unsigned char *>(smem) +
                          size_t(blockDim.x >> 5) * queue_bytes<Real, DIM>()) +
@@ -167,11 +182,12 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
 #pragma unroll
             for (int a = 0; a < DIM; ++a)
                 Xe[a] = qx[a * kQueue + e];
-            int32_t ei = int32_t(qi[e]);
-            uint32_t sg = qsg[e];
-            int32_t j = walk_classify<Real, DIM, KIND>(p.g, Xe);
-            if (p.trace_elem) {
-                size_t q = size_t(ei) * (p.k1 - p.k0) + (qk[e] - p.k0);
+            const int32_t ei = int32_t(qi[e]);
+            const WalkInst<Real> &I = inst(int32_t(qinst[e]));
+            const uint32_t sg = qsg[e];
+            const int32_t j = walk_classify<Real, DIM, KIND>(I.g, Xe);
+            if (!MULTI && p.trace_elem) {
+                size_t q = size_t(ei) * (I.k1 - I.k0) + (qk[e] - I.k0);
                 p.trace_elem[q] = j;
                 if (p.trace_steps) p.trace_steps[q] = qn_steps[e];
                 if (p.trace_x) {
@@ -180,20 +196,19 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
                         p.trace_x[q * DIM + a] = double(Xe[a]);
                 }
             }
-            uint32_t es = sg & 1u, eg = sg >> 1;
-            uint32_t g_now = es ? gen1 : gen0;
+            const uint32_t es = sg & 1u, eg = sg >> 1;
+            const uint32_t g_now = es ? gen1 : gen0;
             if (p.nslot > 0 && eg == g_now)
                 atomicAdd(hist + es * p.hist_words + (j >> 1), 1u << ((j & 1) * 16));
             else
-                atomicAdd(p.counts + size_t(ei) * M + j, 1u);
+                atomicAdd(I.counts + size_t(ei) * I.g.M_tot + j, 1u);
         }
         __syncwarp();
     };
 
-
     // lane state
     Real X[DIM];
-    int32_t li = 0;
+    int32_t li = 0, linst = 0;
     uint32_t lk = 0, wlo = 0, whi = 0, nstep = 0;
     int32_t lslot = 0;
     uint32_t lgen = 0;
@@ -216,18 +231,34 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
                     no_more = true;
                     break;
                 }
-                uint32_t ti = uint32_t(t / p.tiles_per_point);
-                uint32_t tr = uint32_t(t - uint64_t(ti) * p.tiles_per_point);
+                int32_t q = 0;
+                if (MULTI) {  // last instance whose first tile is <= t
+                    int32_t lo = 0, hi = p.n_inst - 1;
+                    while (lo < hi) {
+                        int32_t mid = (lo + hi + 1) >> 1;
+                        if (insts[mid].tile_begin <= t) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    q = lo;
+                }
+                const WalkInst<Real> &T = inst(q);
+                const uint64_t tl = t - T.tile_begin;
+                const uint32_t ti = uint32_t(tl / T.tiles_per_point);
+                const uint32_t tr = uint32_t(tl - uint64_t(ti) * T.tiles_per_point);
+                tile_inst = q;
                 tile_i = int32_t(ti);
-                tile_k = p.k0 + tr * p.tile_w;
-                tile_kend = min(tile_k + p.tile_w, p.k1);
+                tile_k = T.k0 + tr * T.tile_w;
+                tile_kend = min(tile_k + T.tile_w, T.k1);
                 if (p.nslot > 0) {
                     int32_t s = (p.nslot == 2) ? (slot_cur ^ 1) : 0;
                     int32_t old_pt = s ? pt1 : pt0;
-                    if (old_pt >= 0)
+                    if (old_pt >= 0) {
+                        const WalkInst<Real> &O = inst(s ? in1 : in0);
                         flush_slot(hist + s * p.hist_words, p.hist_words,
-                                   p.counts + size_t(old_pt) * M, lane);
-                    if (s) { ++gen1; pt1 = tile_i; } else { ++gen0; pt0 = tile_i; }
+                                   O.counts + size_t(old_pt) * O.g.M_tot, lane);
+                    }
+                    if (s) { ++gen1; pt1 = tile_i; in1 = tile_inst; }
+                    else { ++gen0; pt0 = tile_i; in0 = tile_inst; }
                     slot_cur = s;
                 }
                 continue;
@@ -237,15 +268,17 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
             uint32_t n = __popc(need_mask);
             uint32_t take = n < avail ? n : avail;
             if (mine && rank < take) {
+                const WalkInst<Real> &T = inst(tile_inst);
+                linst = tile_inst;
                 li = tile_i;
                 lk = tile_k + rank;
-                uint64_t wid = uint64_t(li) * p.N + lk;
+                uint64_t wid = uint64_t(li) * T.N + lk;
                 wlo = uint32_t(wid);
                 whi = uint32_t(wid >> 32);
 #pragma unroll
                 for (int a = 0; a < DIM; ++a)
-                    X[a] = p.points_r ? p.points_r[size_t(li) * DIM + a]
-                                      : Real(p.points[size_t(li) * DIM + a]);
+                    X[a] = T.points_r ? T.points_r[size_t(li) * DIM + a]
+                                      : Real(T.points[size_t(li) * DIM + a]);
                 nstep = 0;
                 active = true;
                 lslot = slot_cur;
@@ -261,13 +294,14 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
         // Branch-free: every step is evaluated and a stopped walk keeps X.
         bool stop = false, capped = false;
         if (active) {
+            const WalkInst<Real> &I = inst(linst);
             uint32_t w[4];
-            philox4x32_10(nstep / G, wlo, whi, p.stream_id, p.rk, w);
+            philox4x32_10(nstep / G, wlo, whi, I.stream_id, p.rk, w);
 #pragma unroll
             for (int s = 0; s < G; ++s) {
-                Real r = walk_dist<Real, DIM, KIND>(p.g, X);
-                bool at_eps = r <= p.eps;
-                bool at_cap = nstep >= p.step_cap;
+                Real r = walk_dist<Real, DIM, KIND>(I.g, X);
+                bool at_eps = r <= I.eps;
+                bool at_cap = nstep >= I.step_cap;
                 bool go = !stop && !at_eps && !at_cap;
                 capped = capped || (!stop && !at_eps && at_cap);
                 stop = stop || !go;
@@ -278,7 +312,7 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
                     Real su = Real(0);
 #pragma unroll
                     for (int b = 0; b < DIM; ++b)
-                        su += p.S[a * DIM + b] * U[b];
+                        su += I.S[a * DIM + b] * U[b];
                     Real xn = X[a] + r * su;
                     X[a] = go ? xn : X[a];
                 }
@@ -294,11 +328,12 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
         {
             bool cap_fin = fin && capped;
             if (cap_fin) {
+                const WalkInst<Real> &I = inst(linst);
                 ++my_unterm;
-                if (p.unterm)
-                    atomicAdd(p.unterm + li, 1u);
-                if (p.trace_elem) {
-                    size_t q = size_t(li) * (p.k1 - p.k0) + (lk - p.k0);
+                if (I.unterm)
+                    atomicAdd(I.unterm + li, 1u);
+                if (!MULTI && p.trace_elem) {
+                    size_t q = size_t(li) * (I.k1 - I.k0) + (lk - I.k0);
                     p.trace_elem[q] = -1;
                     if (p.trace_steps) p.trace_steps[q] = nstep;
                     if (p.trace_x) {
@@ -316,6 +351,7 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
                 for (int a = 0; a < DIM; ++a)
                     qx[a * kQueue + e] = X[a];
                 qi[e] = uint32_t(li);
+                qinst[e] = uint32_t(linst);
                 qk[e] = lk;
                 qsg[e] = (lgen << 1) | uint32_t(lslot);
                 qn_steps[e] = nstep;
@@ -339,11 +375,15 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
     if (qn > 0)
         drain(0, qn);
     if (p.nslot > 0) {
-        if (pt0 >= 0)
-            flush_slot(hist, p.hist_words, p.counts + size_t(pt0) * M, lane);
-        if (p.nslot == 2 && pt1 >= 0)
+        if (pt0 >= 0) {
+            const WalkInst<Real> &O = inst(in0);
+            flush_slot(hist, p.hist_words, O.counts + size_t(pt0) * O.g.M_tot, lane);
+        }
+        if (p.nslot == 2 && pt1 >= 0) {
+            const WalkInst<Real> &O = inst(in1);
             flush_slot(hist + p.hist_words, p.hist_words,
-                       p.counts + size_t(pt1) * M, lane);
+                       O.counts + size_t(pt1) * O.g.M_tot, lane);
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {

@@ -1,14 +1,17 @@
-// walk_launch.cuh -- launch planning of the persistent walk kernel, shared by
-// every entry point that launches it (grid, block, shared memory, tiles).
+// walk_launch.cuh -- host-side set-up and launch planning of the persistent
+// walk kernel, shared by every entry point that launches it: the instance
+// record, the kernel variant, block / grid / shared memory and tile sizes.
 #pragma once
 
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 
 #include "walk_kernel.cuh"
 #include "wos.h"
+#include "wos_internal.h"
 
 namespace wos {
 
@@ -16,26 +19,28 @@ struct WalkPlan {
     const void *kfn;   // kernel entry
     int block, grid, nslot;
     size_t smem;       // dynamic shared memory per block
-    uint32_t tile_w, tiles_per_point;
+    uint32_t tile_w;   // walks per tile (single instance)
+    uint32_t tiles_per_point;
     uint64_t n_tiles;
 };
 
-template <typename Real, int DIM, int KIND>
+template <typename Real, int DIM, int KIND, bool MULTI>
 const void *walk_kernel_ptr()
 {
-    return reinterpret_cast<const void *>(&walk_kernel<Real, DIM, KIND>);
+    return reinterpret_cast<const void *>(&walk_kernel<Real, DIM, KIND, MULTI>);
 }
 
-template <typename Real, int DIM>
+template <typename Real, int DIM, bool MULTI>
 const void *pick_walk_kernel(int kind)
 {
-    if (kind == kSphereOnly) return walk_kernel_ptr<Real, DIM, kSphereOnly>();
-    if (kind == kBoxOnly) return walk_kernel_ptr<Real, DIM, kBoxOnly>();
-    if (kind == kSphereHoles) return walk_kernel_ptr<Real, DIM, kSphereHoles>();
-    return walk_kernel_ptr<Real, DIM, kGeneric>();
+    if (kind == kSphereOnly) return walk_kernel_ptr<Real, DIM, kSphereOnly, MULTI>();
+    if (kind == kBoxOnly) return walk_kernel_ptr<Real, DIM, kBoxOnly, MULTI>();
+    if (kind == kSphereHoles) return walk_kernel_ptr<Real, DIM, kSphereHoles, MULTI>();
+    return walk_kernel_ptr<Real, DIM, kGeneric, MULTI>();
 }
 
-// Kernel kind: specialised distance for a plain disc / ball or box.
+// Kernel kind: specialised distance for a plain disc / ball, a box, or a
+// disc / ball with holes.
 inline int walk_kind(const wos_domain &d, const wos_partition &part)
 {
     if (part.voronoi_n <= 0 && d.outer_kind == WOS_OUTER_SPHERE)
@@ -45,20 +50,43 @@ inline int walk_kind(const wos_domain &d, const wos_partition &part)
     return kGeneric;
 }
 
-// Plans a launch: block size, shared-memory histogram slots per warp (2 when
-// they fit next to the exit queues in ~56 KiB per block, so that four blocks
-// share an SM; else 1; else none), grid = SMs x resident blocks, and the tile
-// size (about 16 tiles per warp, 64..16384 walks, a multiple of 32, at most
-// the walks of one point).
-template <typename Real, int DIM>
-wos_status plan_walk(int kind, int32_t M_tot, const wos_opts &o, int sm_count,
-                     int max_smem_optin, uint64_t per_point, int32_t M_D, WalkPlan *P)
+// Fills an instance record (points_r, tiles and counts pointers are left to
+// the caller).
+template <typename Real>
+void fill_inst(const wos_domain &d, const wos_partition &part, const double *S,
+               const double *points, int32_t M_D, uint32_t N, double eps,
+               uint32_t stream_id, uint32_t k0, uint32_t k1, uint32_t step_cap,
+               uint32_t *counts, uint32_t *unterm, WalkInst<Real> *I)
 {
-    P->kfn = pick_walk_kernel<Real, DIM>(kind);
+    std::memset(I, 0, sizeof(*I));
+    fill_geom(d, part, I->g);
+    for (int i = 0; i < 9; ++i)
+        I->S[i] = i < d.dim * d.dim ? Real(S[i]) : Real(0);
+    I->eps = Real(eps);
+    I->stream_id = stream_id;
+    I->N = N;
+    I->k0 = k0;
+    I->k1 = k1 ? k1 : N;
+    I->step_cap = step_cap ? step_cap : 1000000u;
+    I->M_D = M_D;
+    I->points = points;
+    I->points_r = nullptr;
+    I->counts = counts;
+    I->unterm = unterm;
+}
+
+// Block size, shared-memory histogram slots per warp (2 when they fit next
+// to the exit queues in ~56 KiB per block, so that four blocks share an SM;
+// else 1; else none), grid = SMs x resident blocks.
+template <typename Real, int DIM, bool MULTI>
+wos_status plan_grid(int kind, int32_t max_M_tot, const wos_opts &o, int sm_count,
+                     int max_smem_optin, WalkPlan *P)
+{
+    P->kfn = pick_walk_kernel<Real, DIM, MULTI>(kind);
     P->block = o.block_size > 0 ? o.block_size : 256;
     const int warps = P->block / 32;
     const size_t qbytes = size_t(warps) * queue_bytes<Real, DIM>();
-    const size_t slot_bytes = size_t(warps) * size_t((M_tot + 1) / 2) * 4;
+    const size_t slot_bytes = size_t(warps) * size_t((max_M_tot + 1) / 2) * 4;
     const size_t budget = 56 * 1024;
     int nslot = o.hist_slots;
     if (nslot == 0) {
@@ -84,27 +112,52 @@ wos_status plan_walk(int kind, int32_t M_tot, const wos_opts &o, int sm_count,
     if (o.blocks_per_sm > 0)
         bps = std::min(bps, o.blocks_per_sm);
     P->grid = sm_count * bps;
-    const uint64_t total = per_point * uint64_t(M_D);
+    return WOS_OK;
+}
+
+// Tile size: about 16 tiles per warp over the whole launch, 64..16384 walks,
+// a multiple of 32, at most the walks of one point.
+inline uint32_t tile_size(const wos_opts &o, uint64_t total_walks, int grid, int block,
+                          uint64_t per_point)
+{
+    const int warps = block / 32;
     uint64_t tw = o.tile_walks > 0 ? uint64_t(o.tile_walks)
-                                   : total / (16ull * uint64_t(P->grid) * warps);
+                                   : total_walks / (16ull * uint64_t(grid) * warps);
     tw = std::max<uint64_t>(tw, 64);
     tw = std::min<uint64_t>(tw, 16384);
     tw = (tw + 31) / 32 * 32;
     tw = std::min<uint64_t>(tw, per_point);
-    if (tw == 0) tw = 1;
-    P->tile_w = uint32_t(tw);
-    P->tiles_per_point = uint32_t((per_point + tw - 1) / tw);
-    P->n_tiles = uint64_t(P->tiles_per_point) * uint64_t(M_D);
-    return WOS_OK;
+    return tw == 0 ? 1u : uint32_t(tw);
 }
 
+// Single-instance plan.
 template <typename Real>
 wos_status plan_walk_any(int dim, int kind, int32_t M_tot, const wos_opts &o, int sm_count,
                          int max_smem_optin, uint64_t per_point, int32_t M_D, WalkPlan *P)
 {
-    if (dim == 2)
-        return plan_walk<Real, 2>(kind, M_tot, o, sm_count, max_smem_optin, per_point, M_D, P);
-    return plan_walk<Real, 3>(kind, M_tot, o, sm_count, max_smem_optin, per_point, M_D, P);
+    wos_status st = dim == 2
+        ? plan_grid<Real, 2, false>(kind, M_tot, o, sm_count, max_smem_optin, P)
+        : plan_grid<Real, 3, false>(kind, M_tot, o, sm_count, max_smem_optin, P);
+    if (st != WOS_OK)
+        return st;
+    P->tile_w = tile_size(o, per_point * uint64_t(M_D), P->grid, P->block, per_point);
+    P->tiles_per_point = uint32_t((per_point + P->tile_w - 1) / P->tile_w);
+    P->n_tiles = uint64_t(P->tiles_per_point) * uint64_t(M_D);
+    return WOS_OK;
+}
+
+// Fills p.one and the plan fields of a single-instance launch.
+template <typename Real>
+void apply_plan(const WalkPlan &P, WalkParams<Real> *p)
+{
+    p->one.tile_w = P.tile_w;
+    p->one.tiles_per_point = P.tiles_per_point;
+    p->one.tile_begin = 0;
+    p->insts = nullptr;
+    p->n_inst = 1;
+    p->n_tiles = P.n_tiles;
+    p->nslot = P.nslot;
+    p->hist_words = (p->one.g.M_tot + 1) / 2;
 }
 
 }  // namespace wos

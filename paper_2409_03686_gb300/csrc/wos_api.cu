@@ -506,29 +506,17 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
     if (!pp)
         return WOS_OOM;
     WalkParams<Real> &p = *pp;
-    fill_geom(d, part, p.g);
+    std::memset(&p, 0, sizeof(p));
     const int dim = d.dim;
-    for (int i = 0; i < dim * dim; ++i)
-        p.S[i] = Real(S[i]);
-    p.eps = Real(eps);
+    fill_inst<Real>(d, part, S, points, M_D, N, eps, o.stream_id, o.k0, o.k1, o.step_cap,
+                    counts, unterm, &p.one);
     philox_round_keys(seed, p.rk);
-    p.stream_id = o.stream_id;
-    p.N = N;
-    p.k0 = o.k0;
-    p.k1 = o.k1 ? o.k1 : N;
-    p.step_cap = o.step_cap ? o.step_cap : 1000000u;
-    p.M_D = M_D;
-    p.points = points;
-    p.points_r = nullptr;
-    p.counts = counts;
-    p.unterm = unterm;
     p.trace_elem = o.trace_elem;
     p.trace_steps = o.trace_steps;
     p.trace_x = o.trace_x;
-    const int32_t M = p.g.M_tot;
-    p.hist_words = (M + 1) / 2;
+    const int32_t M = p.one.g.M_tot;
 
-    const uint64_t per_point = uint64_t(p.k1 - p.k0);
+    const uint64_t per_point = uint64_t(p.one.k1 - p.one.k0);
     WalkPlan plan;
     wos_status pst = plan_walk_any<Real>(dim, walk_kind(d, part), M, o, ctx->sm_count,
                                          ctx->max_smem_optin, per_point, M_D, &plan);
@@ -536,14 +524,11 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
         delete pp;
         return pst;
     }
+    apply_plan(plan, &p);
     const void *kfn = plan.kfn;
     const int grid = plan.grid, block = plan.block, nslot = plan.nslot;
     const size_t smem = plan.smem;
     const uint64_t tw = plan.tile_w;
-    p.nslot = nslot;
-    p.tile_w = plan.tile_w;
-    p.tiles_per_point = plan.tiles_per_point;
-    p.n_tiles = plan.n_tiles;
 
     // per-call scratch: work counters, statistics, Voronoi sites and (FP32
     // walks) the points in walk precision, so that no walk converts FP64
@@ -561,8 +546,9 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
         for (size_t q = 0; q < sites.size(); ++q)
             sites[q] = Real(part.voronoi_sites[q]);
         Real *dsites = reinterpret_cast<Real *>(static_cast<char *>(scratch) + 256);
-        cudaMemcpyAsync(dsites, sites.data(), site_bytes, cudaMemcpyHostToDevice, stream);
-        p.g.vsites = dsites;
+        cudaMemcpyAsync(dsites, sites.data(), sites.size() * sizeof(Real),
+                        cudaMemcpyHostToDevice, stream);
+        p.one.g.vsites = dsites;
     }
     cudaMemsetAsync(scratch, 0, 64, stream);
     if (convert) {
@@ -570,7 +556,7 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
         int n = M_D * dim;
         convert_points_kernel<Real><<<(n + 255) / 256, 256, 0, stream>>>(points, n, dpts);
         count_launches(ctx, 1);
-        p.points_r = dpts;
+        p.one.points_r = dpts;
     }
     if (!o.accumulate) {
         cudaMemsetAsync(counts, 0, size_t(M_D) * M * 4, stream);

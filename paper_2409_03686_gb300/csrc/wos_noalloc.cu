@@ -75,42 +75,27 @@ wos_status build_noalloc(wos_context *ctx, unsigned char *scratch, const wos_dom
                          wos_stats *stats, cudaStream_t stream)
 {
     WalkParams<Real> p;  // host stack, passed by value to the kernel
-    fill_geom(d, part, p.g);
+    std::memset(&p, 0, sizeof(p));
     const int dim = d.dim;
-    for (int i = 0; i < 9; ++i)
-        p.S[i] = i < dim * dim ? Real(S[i]) : Real(0);
-    p.eps = Real(eps);
+    fill_inst<Real>(d, part, S, points, M_D, N, eps, o.stream_id, o.k0, o.k1, o.step_cap,
+                    counts, unterm, &p.one);  // points_r stays null: converted per walk
     philox_round_keys(seed, p.rk);
-    p.stream_id = o.stream_id;
-    p.N = N;
-    p.k0 = o.k0;
-    p.k1 = o.k1 ? o.k1 : N;
-    p.step_cap = o.step_cap ? o.step_cap : 1000000u;
-    p.M_D = M_D;
-    p.points = points;
-    p.points_r = nullptr;  // converted per walk: no scratch for a copy
-    p.counts = counts;
-    p.unterm = unterm;
     p.trace_elem = o.trace_elem;
     p.trace_steps = o.trace_steps;
     p.trace_x = o.trace_x;
-    const int32_t M = p.g.M_tot;
-    p.hist_words = (M + 1) / 2;
+    const int32_t M = p.one.g.M_tot;
 
     WalkPlan plan;
     wos_status pst = plan_walk_any<Real>(dim, walk_kind(d, part), M, o, ctx_sm_count(ctx),
-                                         ctx_max_smem(ctx), uint64_t(p.k1 - p.k0), M_D,
-                                         &plan);
+                                         ctx_max_smem(ctx), uint64_t(p.one.k1 - p.one.k0),
+                                         M_D, &plan);
     if (pst != WOS_OK)
         return pst;
+    apply_plan(plan, &p);
     const void *kfn = plan.kfn;
     const int grid = plan.grid, block = plan.block, nslot = plan.nslot;
     const size_t smem = plan.smem;
     const uint64_t tw = plan.tile_w;
-    p.nslot = nslot;
-    p.tile_w = plan.tile_w;
-    p.tiles_per_point = plan.tiles_per_point;
-    p.n_tiles = plan.n_tiles;
     cudaError_t e = cudaSuccess;
 
     // scratch: counters at offset 0 (cleared every call), sites after them
@@ -126,7 +111,7 @@ wos_status build_noalloc(wos_context *ctx, unsigned char *scratch, const wos_dom
                             stream);
         if (e != cudaSuccess)
             return cuda_status(e);
-        p.g.vsites = dsites;
+        p.one.g.vsites = dsites;
     }
     e = cudaMemsetAsync(scratch, 0, kCounterBytes, stream);
     if (e != cudaSuccess)

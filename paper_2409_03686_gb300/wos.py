@@ -91,6 +91,22 @@ class WosOpts(ctypes.Structure):
     ]
 
 
+class WosProblem(ctypes.Structure):
+    _fields_ = [
+        ("domain", ctypes.c_void_p),
+        ("partition", ctypes.c_void_p),
+        ("K", ctypes.c_void_p),
+        ("points", ctypes.c_void_p),
+        ("M_D", ctypes.c_int32),
+        ("N", ctypes.c_uint32),
+        ("eps", ctypes.c_double),
+        ("stream_id", ctypes.c_uint32),
+        ("step_cap", ctypes.c_uint32),
+        ("counts", ctypes.c_void_p),
+        ("unterminated", ctypes.c_void_p),
+    ]
+
+
 class WosStats(ctypes.Structure):
     _fields_ = [
         ("walks", ctypes.c_uint64),
@@ -143,6 +159,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
                                      vp, vp]
     L.wos_build_operator_noalloc.argtypes = [vp, vp, vp, vp, i32, vp, u32, dbl, u64, vp,
                                              vp, vp, vp, vp]
+    L.wos_build_operators_batched.argtypes = [vp, i32, vp, u64, vp, vp, vp]
     L.wos_op_svd.argtypes = [vp, vp, i32, i32, u32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.wos_reconstruct.argtypes = [vp, vp, vp, vp, i32, i32, vp, i32, u32, vp, vp, vp, vp,
                                   vp, i32, dbl, vp, vp, vp]
@@ -365,6 +382,54 @@ def wos_build_operator_noalloc(ctx: Context, domain, K, points, partition, N: in
         ctypes.byref(opts) if opts is not None else None, counts.data_ptr(),
         _ptr(unterminated), ctypes.byref(st) if st is not None else None, _stream(stream))
     _check(code, "wos_build_operator_noalloc")
+    return counts, unterminated, (st.as_dict() if st is not None else None)
+
+
+def wos_build_operators_batched(ctx: Context, insts, seed: int, points=None,
+                                counts=None, unterminated=None, opts: WosOpts | None = None,
+                                stats: bool = True, stream=None):
+    """Builds the operators of many workloads.Instance objects in one launch
+    per dimension.  Each instance's stream_id (its `stream`) keeps its walks
+    identical to a lone build.  Returns (counts list, unterminated list,
+    stats)."""
+    import torch
+    L = load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    keep = []
+    probs = (WosProblem * len(insts))()
+    counts = list(counts) if counts is not None else []
+    unterminated = list(unterminated) if unterminated is not None else []
+    points = list(points) if points is not None else []
+    for q, inst in enumerate(insts):
+        D = make_domain(inst.domain)
+        P, kp = make_partition(inst.domain, inst.partition)
+        Kc = np.ascontiguousarray(inst.K, dtype=np.float64)
+        keep += [D, P, kp, Kc]
+        if len(points) <= q:
+            points.append(torch.as_tensor(inst.points, dtype=torch.float64, device=dev))
+        M_tot = int(L.wos_num_elements(ctypes.byref(D), ctypes.byref(P)))
+        if len(counts) <= q:
+            counts.append(torch.empty((inst.M_D, M_tot), dtype=torch.int32, device=dev))
+        if len(unterminated) <= q:
+            unterminated.append(torch.empty(inst.M_D, dtype=torch.int32, device=dev))
+        pb = probs[q]
+        pb.domain = ctypes.addressof(D)
+        pb.partition = ctypes.addressof(P)
+        pb.K = Kc.ctypes.data
+        pb.points = points[q].data_ptr()
+        pb.M_D = inst.M_D
+        pb.N = int(inst.N)
+        pb.eps = float(inst.eps)
+        pb.stream_id = int(inst.stream)
+        pb.step_cap = 0 if inst.step_cap == 1_000_000 else int(inst.step_cap)
+        pb.counts = counts[q].data_ptr()
+        pb.unterminated = unterminated[q].data_ptr()
+    st = WosStats() if stats else None
+    code = L.wos_build_operators_batched(ctx.h, len(insts), ctypes.byref(probs), int(seed),
+                                         ctypes.byref(opts) if opts is not None else None,
+                                         ctypes.byref(st) if st is not None else None,
+                                         _stream(stream))
+    _check(code, "wos_build_operators_batched")
     return counts, unterminated, (st.as_dict() if st is not None else None)
 
 
