@@ -409,6 +409,105 @@ def run_gpu(args, rank: int, world: int, dist):
     print(json.dumps(line))
 
 
+def run_batch(args, rank: int, world: int, dist):
+    """Config 4: the 64-instance mixed batch (disc, annulus, square, L-shape,
+    ball, box; log-uniform sizes and walks per point) in one autotuned
+    persistent launch per dimension, against one plain launch per instance
+    (default launch settings) on the same GPU.  Operator builds only."""
+    import torch
+    from paper_2409_03686_gb300 import build as B
+    from paper_2409_03686_gb300 import workloads as W
+    from paper_2409_03686_gb300 import wos
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    ctx = wos.Context(local)
+    insts = W.mixed_batch(64, scale=args.batch_scale)
+    pts = [torch.as_tensor(i.points, dtype=torch.float64, device=dev) for i in insts]
+    walks = sum(i.M_D * i.N for i in insts)
+    # sequential plain launches (no tuning in the context yet)
+    counts_seq = []
+    def sequential():
+        out = []
+        for inst, p in zip(insts, pts):
+            c, u, _ = wos.wos_build_operator(ctx, inst.domain, inst.K, p, inst.partition,
+                                             inst.N, inst.eps, inst.seed,
+                                             opts=wos.make_opts(stream_id=inst.stream),
+                                             stats=False)
+            out.append(c)
+        return out
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    def timed(fn, reps):
+        ms = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            ev0.record()
+            r = fn()
+            ev1.record()
+            torch.cuda.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+        return r, ms
+    sequential()
+    seq_out, seq_ms = timed(sequential, args.steps)
+    # autotune each (dim, kind) class on its largest instance, then batch
+    classes = {}
+    for inst in insts:
+        key = (inst.dim, inst.domain.outer, len(inst.domain.holes) > 0)
+        if key not in classes or inst.M_D * inst.N > classes[key].M_D * classes[key].N:
+            classes[key] = inst
+    tunings = {str(k): wos.wos_autotune(ctx, v) for k, v in classes.items()}
+    def batched():
+        c, u, _ = wos.wos_build_operators_batched(ctx, insts, seed=insts[0].seed, points=pts,
+                                                  stats=False)
+        return c
+    for _ in range(max(1, args.warmup)):
+        batched()
+    bat_out, bat_ms = timed(batched, args.steps)
+    same = all(torch.equal(a, b) for a, b in zip(seq_out, bat_out))
+
+    # small requests: 256 instances of 64..256 points x 1e3..1e4 walks
+    small = W.mixed_batch(256, seed=17, m_lo=64, m_hi=256, n_lo=1e3, n_hi=1e4)
+    spts = [torch.as_tensor(i.points, dtype=torch.float64, device=dev) for i in small]
+    swalks = sum(i.M_D * i.N for i in small)
+    def small_seq():
+        return [wos.wos_build_operator(ctx, i.domain, i.K, p, i.partition, i.N, i.eps, i.seed,
+                                       opts=wos.make_opts(stream_id=i.stream), stats=False)[0]
+                for i, p in zip(small, spts)]
+    def small_bat():
+        return wos.wos_build_operators_batched(ctx, small, seed=small[0].seed, points=spts,
+                                               stats=False)[0]
+    small_seq()
+    small_bat()
+    s_seq, s_seq_ms = timed(small_seq, args.steps)
+    s_bat, s_bat_ms = timed(small_bat, args.steps)
+    s_same = all(torch.equal(a, b) for a, b in zip(s_seq, s_bat))
+    if rank != 0:
+        return
+    t_seq = float(np.median(seq_ms)) / 1e3
+    t_bat = float(np.median(bat_ms)) / 1e3
+    ts_seq = float(np.median(s_seq_ms)) / 1e3
+    ts_bat = float(np.median(s_bat_ms)) / 1e3
+    print(json.dumps({
+        "metric": METRIC, "value": walks / t_bat, "unit": "walks/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_bat,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"mixed batch of 64 instances (disc, annulus, square, L-shape, "
+                               f"ball, box), {walks:.3g} walks, operator builds only",
+                   "walks_per_step": walks},
+        "sequential_walks_per_s": walks / t_seq, "batched_over_sequential": t_seq / t_bat,
+        "batched_equals_sequential": bool(same), "tunings": tunings,
+        "small_requests": {"instances": len(small), "walks": swalks,
+                           "batched_walks_per_s": swalks / ts_bat,
+                           "sequential_walks_per_s": swalks / ts_seq,
+                           "batched_over_sequential": ts_seq / ts_bat,
+                           "requests_per_s_batched": len(small) / ts_bat,
+                           "requests_per_s_sequential": len(small) / ts_seq,
+                           "batched_equals_sequential": bool(s_same)},
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -417,6 +516,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="square-annulus")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="walks-per-point scale of the batch workload")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -428,6 +529,8 @@ def main():
         dist = D
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batch":
+        run_batch(args, rank, world, dist)
     else:
         run_gpu(args, rank, world, dist)
     if dist is not None:

@@ -116,6 +116,11 @@ typedef struct {
     int32_t tile_walks;  /* walks per warp tile (0 = automatic) */
     int32_t hist_slots;  /* shared-memory histogram slots per warp: 0 = auto,
                             1 or 2; -1 = tally straight to global memory */
+    int32_t refill_min;  /* refill granularity: finished lanes wait until at
+                            least this many lanes of the warp need a walk
+                            (0 or 1 = refill at every group of steps) */
+    int32_t tiles_per_warp; /* target tiles per warp when tile_walks = 0
+                            (0 = 16); walks per lane per tile follow */
     int32_t *trace_elem; /* device, optional: M_D x (k1-k0) exit element of
                             every walk (-1 = unterminated); for tests */
     uint32_t *trace_steps; /* device, optional: same shape, N_eps per walk */
@@ -251,8 +256,9 @@ typedef struct {
 } wos_problem;
 
 /* Many MC-REM builds (paper Sec. 5.1, Algorithm MC-REM, applied to each
- * problem) in one persistent launch per dimension: the walks of all the
- * problems of one dimension share a global tile queue, so problems of very
+ * problem) in one persistent launch per class (dimension x kernel kind:
+ * plain disc/ball, box, disc/ball with holes, other): the walks of all the
+ * problems of a class share a global tile queue, so problems of very
  * different sizes and walk lengths keep the whole GPU busy.  All problems
  * share `seed` and opts->precision; each problem's walks use counter
  * (block, walk lo, walk hi, stream_id), so its counts are bit-identical to
@@ -265,6 +271,32 @@ wos_status wos_build_operators_batched(wos_context *ctx, int32_t n,
                                        const wos_problem *problems, uint64_t seed,
                                        const wos_opts *opts, wos_stats *stats,
                                        void *stream);
+
+/* A launch configuration chosen by wos_autotune. */
+typedef struct {
+    int32_t block_size, blocks_per_sm, tiles_per_warp, hist_slots, refill_min;
+    int32_t trials;        /* configurations timed */
+    float best_ms;         /* walk-kernel time of the sample, best config */
+    float default_ms;      /* the same with the built-in defaults */
+} wos_tuning;
+
+/* Autotuner (no paper counterpart: it only picks launch parameters, which
+ * never change results since every walk's random numbers are fixed by its
+ * Philox counter).  Times the walk kernel of `sample` (its first points, at
+ * most sample_walks walks in all) with CUDA events under a coordinate search
+ * over block size {256, 128}, resident blocks per SM {max, 3, 2}, tiles per
+ * warp {16, 4, 64}, histogram slots {auto, none} and refill granularity
+ * {1, 4, 8}; keeps the fastest in the context for problems of the same
+ * precision, dimension and kernel kind (plain disc/ball, box, disc/ball with
+ * holes, other).  Later wos_build_operator / wos_build_operators_batched calls
+ * whose opts leave all launch fields 0 use it.  Synchronises `stream`.
+ * Errors: those of wos_build_operator. */
+wos_status wos_autotune(wos_context *ctx, const wos_problem *sample, uint64_t seed,
+                        int32_t precision, uint64_t sample_walks, wos_tuning *out,
+                        void *stream);
+
+/* Forget every tuned configuration of the context. */
+wos_status wos_autotune_reset(wos_context *ctx);
 
 /* Check that every point (host, M_D x dim) lies strictly inside D.  Returns
  * WOS_OK or WOS_POINT_OUTSIDE (first offending index in *bad if non-NULL). */

@@ -70,6 +70,7 @@ template <typename Real> struct WalkParams {
                                  // [3] unterminated, [4] max steps
     int32_t nslot;               // 0 (global tally), 1 or 2
     int32_t hist_words;          // ceil(M_tot / 2), max over a batch
+    int32_t refill_min;          // refill when >= this many lanes need a walk
 };
 
 template <typename Real, int DIM> struct Steps {
@@ -220,6 +221,8 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
     for (;;) {
         // ---- refill: lanes with `need` take walks from the warp's tile -----
         unsigned need_mask = __ballot_sync(FULL, need);
+        if (int32_t(__popc(need_mask)) < p.refill_min && __any_sync(FULL, active))
+            need_mask = 0u;  // refill granularity: let a few lanes idle
         while (need_mask != 0u && !no_more) {
             uint32_t avail = tile_kend - tile_k;
             if (avail == 0u) {

@@ -115,14 +115,15 @@ wos_status plan_grid(int kind, int32_t max_M_tot, const wos_opts &o, int sm_coun
     return WOS_OK;
 }
 
-// Tile size: about 16 tiles per warp over the whole launch, 64..16384 walks,
-// a multiple of 32, at most the walks of one point.
+// Tile size: about tiles_per_warp (default 16) tiles per warp over the whole
+// launch, 64..16384 walks, a multiple of 32, at most the walks of one point.
 inline uint32_t tile_size(const wos_opts &o, uint64_t total_walks, int grid, int block,
                           uint64_t per_point)
 {
     const int warps = block / 32;
+    const uint64_t tpw = o.tiles_per_warp > 0 ? uint64_t(o.tiles_per_warp) : 16ull;
     uint64_t tw = o.tile_walks > 0 ? uint64_t(o.tile_walks)
-                                   : total_walks / (16ull * uint64_t(grid) * warps);
+                                   : total_walks / (tpw * uint64_t(grid) * warps);
     tw = std::max<uint64_t>(tw, 64);
     tw = std::min<uint64_t>(tw, 16384);
     tw = (tw + 31) / 32 * 32;
@@ -158,6 +159,11 @@ void apply_plan(const WalkPlan &P, WalkParams<Real> *p)
     p->n_tiles = P.n_tiles;
     p->nslot = P.nslot;
     p->hist_words = (p->one.g.M_tot + 1) / 2;
+}
+
+inline int32_t refill_min_of(const wos_opts &o)
+{
+    return o.refill_min > 1 ? std::min(o.refill_min, 32) : 1;
 }
 
 }  // namespace wos

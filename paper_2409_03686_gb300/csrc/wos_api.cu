@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -23,6 +24,8 @@ using namespace wos;
 // ---------------------------------------------------------------------------
 struct wos_context {
     std::atomic<uint64_t> launches{0};
+    std::mutex tune_mu;
+    std::map<int, wos_tuning> tuned;  // key: precision, dim, kernel kind
     int device = 0;
     int sm_count = 0;
     int max_smem_optin = 0;
@@ -44,6 +47,25 @@ int ctx_device(const wos_context *c) { return c->device; }
 void count_launches(wos_context *c, int n) { c->launches += uint64_t(n); }
 int ctx_sm_count(const wos_context *c) { return c->sm_count; }
 int ctx_max_smem(const wos_context *c) { return c->max_smem_optin; }
+
+static int tune_key(int precision, int dim, int kind) { return (precision << 8) | (dim << 4) | kind; }
+
+void apply_tuning(const wos_context *c, int precision, int dim, int kind, wos_opts *o)
+{
+    if (o->block_size || o->blocks_per_sm || o->tile_walks || o->hist_slots ||
+        o->refill_min || o->tiles_per_warp)
+        return;
+    wos_context *cc = const_cast<wos_context *>(c);
+    std::lock_guard<std::mutex> lock(cc->tune_mu);
+    auto it = cc->tuned.find(tune_key(precision, dim, kind));
+    if (it == cc->tuned.end())
+        return;
+    o->block_size = it->second.block_size;
+    o->blocks_per_sm = it->second.blocks_per_sm;
+    o->tiles_per_warp = it->second.tiles_per_warp;
+    o->hist_slots = it->second.hist_slots;
+    o->refill_min = it->second.refill_min;
+}
 
 }  // namespace wos
 
@@ -499,7 +521,7 @@ template <typename Real>
 wos_status build_impl(wos_context *ctx, const wos_domain &d,
                       const wos_partition &part, const double *S,
                       const double *points, int32_t M_D, uint32_t N, double eps,
-                      uint64_t seed, const wos_opts &o, uint32_t *counts,
+                      uint64_t seed, const wos_opts &o_in, uint32_t *counts,
                       uint32_t *unterm, wos_stats *stats, cudaStream_t stream)
 {
     WalkParams<Real> *pp = new (std::nothrow) WalkParams<Real>();
@@ -508,6 +530,9 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
     WalkParams<Real> &p = *pp;
     std::memset(&p, 0, sizeof(p));
     const int dim = d.dim;
+    wos_opts o = o_in;
+    apply_tuning(ctx, sizeof(Real) == sizeof(double) ? WOS_FP64 : WOS_FP32, dim,
+                 walk_kind(d, part), &o);
     fill_inst<Real>(d, part, S, points, M_D, N, eps, o.stream_id, o.k0, o.k1, o.step_cap,
                     counts, unterm, &p.one);
     philox_round_keys(seed, p.rk);
@@ -525,6 +550,7 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
         return pst;
     }
     apply_plan(plan, &p);
+    p.refill_min = refill_min_of(o);
     const void *kfn = plan.kfn;
     const int grid = plan.grid, block = plan.block, nslot = plan.nslot;
     const size_t smem = plan.smem;
@@ -656,4 +682,116 @@ extern "C" wos_status wos_truncation_gap(const double *S, int32_t k, int32_t r)
     if (!(S[r] > 0.0))
         return WOS_OK;
     return S[r - 1] / S[r] >= 1.5 ? WOS_OK : WOS_TRUNCATION_IN_CLUSTER;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+extern "C" wos_status wos_autotune_reset(wos_context *ctx)
+{
+    if (!ctx)
+        return WOS_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->tune_mu);
+    ctx->tuned.clear();
+    return WOS_OK;
+}
+
+extern "C" wos_status wos_autotune(wos_context *ctx, const wos_problem *sp, uint64_t seed,
+                                   int32_t precision, uint64_t sample_walks, wos_tuning *out,
+                                   void *stream)
+{
+    if (!ctx || !sp || !out || sample_walks < 1 ||
+        (precision != WOS_FP32 && precision != WOS_FP64))
+        return WOS_INVALID_ARG;
+    wos_status st = validate(sp->domain, sp->partition);
+    if (st != WOS_OK)
+        return st;
+    if (sp->M_D < 1 || sp->N < 1 || !sp->points || !sp->counts)
+        return WOS_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the sample: the first points, about sample_walks walks in all
+    const int32_t md = std::min<int32_t>(sp->M_D, 256);
+    const uint32_t nn = uint32_t(std::max<uint64_t>(
+        1, std::min<uint64_t>(sp->N, sample_walks / uint64_t(md))));
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess)
+        return WOS_CUDA_ERROR;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return WOS_CUDA_ERROR;
+    }
+    auto trial = [&](const wos_opts &cand, float *ms) -> wos_status {
+        wos_opts o = cand;
+        o.precision = precision;
+        o.stream_id = sp->stream_id;
+        o.step_cap = sp->step_cap;
+        o.kernel_events[0] = e0;
+        o.kernel_events[1] = e1;
+        wos_status r = wos_build_operator(ctx, sp->domain, sp->K, sp->points, md, sp->partition,
+                                          nn, sp->eps, seed, &o, sp->counts, nullptr, nullptr,
+                                          stream);
+        if (r != WOS_OK && r != WOS_STEP_CAP_HIT)
+            return r;
+        if (cudaStreamSynchronize(s) != cudaSuccess)
+            return WOS_CUDA_ERROR;
+        cudaEventElapsedTime(ms, e0, e1);
+        return WOS_OK;
+    };
+    wos_opts best;
+    std::memset(&best, 0, sizeof(best));
+    best.block_size = 256;
+    best.tiles_per_warp = 16;
+    best.refill_min = 1;
+    float best_ms = 0.f, ms = 0.f;
+    int trials = 0;
+    st = trial(best, &ms);  // warm-up
+    if (st == WOS_OK)
+        st = trial(best, &best_ms);
+    const float default_ms = best_ms;
+    trials = 1;
+    auto consider = [&](int field, int value) {
+        if (st != WOS_OK)
+            return;
+        wos_opts c = best;
+        int *f = field == 0 ? &c.block_size : field == 1 ? &c.blocks_per_sm
+               : field == 2 ? &c.tiles_per_warp : field == 3 ? &c.hist_slots : &c.refill_min;
+        if (*f == value)
+            return;
+        *f = value;
+        wos_status r = trial(c, &ms);
+        ++trials;
+        if (r == WOS_INVALID_ARG)
+            return;  // configuration does not fit this device
+        if (r != WOS_OK) {
+            st = r;
+            return;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    };
+    for (int v : {128}) consider(0, v);
+    for (int v : {3, 2}) consider(1, v);
+    for (int v : {4, 64}) consider(2, v);
+    for (int v : {-1}) consider(3, v);
+    for (int v : {4, 8}) consider(4, v);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != WOS_OK)
+        return st;
+    std::memset(out, 0, sizeof(*out));
+    out->block_size = best.block_size;
+    out->blocks_per_sm = best.blocks_per_sm;
+    out->tiles_per_warp = best.tiles_per_warp;
+    out->hist_slots = best.hist_slots;
+    out->refill_min = best.refill_min;
+    out->trials = trials;
+    out->best_ms = best_ms;
+    out->default_ms = default_ms;
+    std::lock_guard<std::mutex> lock(ctx->tune_mu);
+    ctx->tuned[tune_key(precision, sp->domain->dim, walk_kind(*sp->domain, *sp->partition))] =
+        *out;
+    return WOS_OK;
 }

@@ -1,11 +1,11 @@
 // wos_batch.cu -- many operator builds in one persistent launch per
-// dimension (spec batching pattern; the paper builds one operator at a
-// time with Algorithm MC-REM).
+// class of dimension and kernel kind (spec batching pattern; the paper
+// builds one operator at a time with Algorithm MC-REM).
 //
 // All problems of one call share the Philox key and the walk precision; a
 // problem's stream_id is its fourth counter word, so every walk (and every
 // count) is bit-identical to the same problem built alone.  The problems of
-// one dimension go into one launch of walk_kernel<..., MULTI = true>: a
+// one class go into one launch of walk_kernel<..., MULTI = true>: a
 // global tile counter spans the tiles of all of them (instance records in
 // per-call device scratch), so instances of very different sizes and walk
 // lengths keep every warp busy until the last tile.
@@ -41,7 +41,7 @@ __global__ void convert_points_batch_kernel(const ConvJob *jobs, Real *dst)
 template <typename Real, int DIM>
 wos_status launch_class(wos_context *ctx, const std::vector<int> &idx,
                         const wos_problem *probs, const std::vector<std::vector<double>> &S,
-                        uint64_t seed, const wos_opts &o, cudaStream_t stream,
+                        uint64_t seed, const wos_opts &o_in, cudaStream_t stream,
                         unsigned long long *work_out)
 {
     const int n = int(idx.size());
@@ -56,6 +56,8 @@ wos_status launch_class(wos_context *ctx, const std::vector<int> &idx,
         max_M = std::max(max_M, num_elements(*pb.domain, *pb.partition));
         total += uint64_t(pb.M_D) * pb.N;
     }
+    wos_opts o = o_in;
+    apply_tuning(ctx, sizeof(Real) == sizeof(double) ? WOS_FP64 : WOS_FP32, DIM, kind, &o);
     WalkPlan plan;
     wos_status st = plan_grid<Real, DIM, true>(kind, max_M, o, ctx_sm_count(ctx),
                                                ctx_max_smem(ctx), &plan);
@@ -144,6 +146,7 @@ wos_status launch_class(wos_context *ctx, const std::vector<int> &idx,
     pp->work = reinterpret_cast<unsigned long long *>(scratch);
     pp->nslot = plan.nslot;
     pp->hist_words = (max_M + 1) / 2;
+    pp->refill_min = refill_min_of(o);
     if (o.kernel_events[0])
         cudaEventRecord(static_cast<cudaEvent_t>(o.kernel_events[0]), stream);
     void *args[] = {pp};
@@ -180,7 +183,8 @@ extern "C" wos_status wos_build_operators_batched(wos_context *ctx, int32_t n,
         o.trace_steps || o.trace_x)
         return WOS_INVALID_ARG;  // whole walk ranges only, no traces, in a batch
     std::vector<std::vector<double>> S(n, std::vector<double>(9, 0.0));
-    std::vector<int> by_dim[2];
+    // classes: dimension x kernel kind (4 kinds), one launch each
+    std::vector<int> by_class[2][4];
     for (int q = 0; q < n; ++q) {
         const wos_problem &pb = problems[q];
         wos_status st = validate(pb.domain, pb.partition);
@@ -195,34 +199,37 @@ extern "C" wos_status wos_build_operators_batched(wos_context *ctx, int32_t n,
             return st;
         if (o.precision == WOS_FP32 && pb.eps < fp32_floor(*pb.domain))
             return WOS_EPS_BELOW_FP32_FLOOR;
-        by_dim[pb.domain->dim - 2].push_back(q);
+        by_class[pb.domain->dim - 2][walk_kind(*pb.domain, *pb.partition)].push_back(q);
     }
     cudaSetDevice(ctx_device(ctx));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    unsigned long long w[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
+    unsigned long long w[8][5] = {};
     for (int dd = 0; dd < 2; ++dd) {
-        if (by_dim[dd].empty())
-            continue;
-        wos_status st;
-        unsigned long long *wo = stats ? w[dd] : nullptr;
-        if (o.precision == WOS_FP64)
-            st = dd == 0 ? launch_class<double, 2>(ctx, by_dim[dd], problems, S, seed, o, s, wo)
-                         : launch_class<double, 3>(ctx, by_dim[dd], problems, S, seed, o, s, wo);
-        else
-            st = dd == 0 ? launch_class<float, 2>(ctx, by_dim[dd], problems, S, seed, o, s, wo)
-                         : launch_class<float, 3>(ctx, by_dim[dd], problems, S, seed, o, s, wo);
-        if (st != WOS_OK)
-            return st;
+        for (int kk = 0; kk < 4; ++kk) {
+            const std::vector<int> &cls = by_class[dd][kk];
+            if (cls.empty())
+                continue;
+            wos_status st;
+            unsigned long long *wo = stats ? w[dd * 4 + kk] : nullptr;
+            if (o.precision == WOS_FP64)
+                st = dd == 0 ? launch_class<double, 2>(ctx, cls, problems, S, seed, o, s, wo)
+                             : launch_class<double, 3>(ctx, cls, problems, S, seed, o, s, wo);
+            else
+                st = dd == 0 ? launch_class<float, 2>(ctx, cls, problems, S, seed, o, s, wo)
+                             : launch_class<float, 3>(ctx, cls, problems, S, seed, o, s, wo);
+            if (st != WOS_OK)
+                return st;
+        }
     }
     if (!stats)
         return WOS_OK;
     wos_status st = cuda_status(cudaStreamSynchronize(s));
     std::memset(stats, 0, sizeof(*stats));
-    for (int dd = 0; dd < 2; ++dd) {
-        stats->steps += w[dd][1];
-        stats->walks += w[dd][2];
-        stats->unterminated += w[dd][3];
-        stats->max_steps = std::max<uint32_t>(stats->max_steps, uint32_t(w[dd][4]));
+    for (int c = 0; c < 8; ++c) {
+        stats->steps += w[c][1];
+        stats->walks += w[c][2];
+        stats->unterminated += w[c][3];
+        stats->max_steps = std::max<uint32_t>(stats->max_steps, uint32_t(w[c][4]));
     }
     if (st == WOS_OK && stats->unterminated > 0)
         st = WOS_STEP_CAP_HIT;

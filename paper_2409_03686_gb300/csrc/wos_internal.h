@@ -13,6 +13,9 @@ int ctx_device(const wos_context *c);
 int ctx_sm_count(const wos_context *c);
 void count_launches(wos_context *c, int n);
 int ctx_max_smem(const wos_context *c);
+// Launch fields of opts replaced by the context's tuned configuration for the
+// class (precision, dim, kind) when they are all zero.
+void apply_tuning(const wos_context *c, int precision, int dim, int kind, wos_opts *o);
 
 // descriptor handling shared by the entry points (wos_api.cu)
 wos_status validate(const wos_domain *d, const wos_partition *p);

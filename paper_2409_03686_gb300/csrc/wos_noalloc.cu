@@ -71,12 +71,15 @@ template <typename Real>
 wos_status build_noalloc(wos_context *ctx, unsigned char *scratch, const wos_domain &d,
                          const wos_partition &part, const double *S, const double *points,
                          int32_t M_D, uint32_t N, double eps, uint64_t seed,
-                         const wos_opts &o, uint32_t *counts, uint32_t *unterm,
+                         const wos_opts &o_in, uint32_t *counts, uint32_t *unterm,
                          wos_stats *stats, cudaStream_t stream)
 {
     WalkParams<Real> p;  // host stack, passed by value to the kernel
     std::memset(&p, 0, sizeof(p));
     const int dim = d.dim;
+    wos_opts o = o_in;
+    apply_tuning(ctx, sizeof(Real) == sizeof(double) ? WOS_FP64 : WOS_FP32, dim,
+                 walk_kind(d, part), &o);
     fill_inst<Real>(d, part, S, points, M_D, N, eps, o.stream_id, o.k0, o.k1, o.step_cap,
                     counts, unterm, &p.one);  // points_r stays null: converted per walk
     philox_round_keys(seed, p.rk);
@@ -92,6 +95,7 @@ wos_status build_noalloc(wos_context *ctx, unsigned char *scratch, const wos_dom
     if (pst != WOS_OK)
         return pst;
     apply_plan(plan, &p);
+    p.refill_min = refill_min_of(o);
     const void *kfn = plan.kfn;
     const int grid = plan.grid, block = plan.block, nslot = plan.nslot;
     const size_t smem = plan.smem;

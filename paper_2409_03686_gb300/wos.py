@@ -84,6 +84,8 @@ class WosOpts(ctypes.Structure):
         ("blocks_per_sm", ctypes.c_int32),
         ("tile_walks", ctypes.c_int32),
         ("hist_slots", ctypes.c_int32),
+        ("refill_min", ctypes.c_int32),
+        ("tiles_per_warp", ctypes.c_int32),
         ("trace_elem", ctypes.c_void_p),
         ("trace_steps", ctypes.c_void_p),
         ("trace_x", ctypes.c_void_p),
@@ -105,6 +107,22 @@ class WosProblem(ctypes.Structure):
         ("counts", ctypes.c_void_p),
         ("unterminated", ctypes.c_void_p),
     ]
+
+
+class WosTuning(ctypes.Structure):
+    _fields_ = [
+        ("block_size", ctypes.c_int32),
+        ("blocks_per_sm", ctypes.c_int32),
+        ("tiles_per_warp", ctypes.c_int32),
+        ("hist_slots", ctypes.c_int32),
+        ("refill_min", ctypes.c_int32),
+        ("trials", ctypes.c_int32),
+        ("best_ms", ctypes.c_float),
+        ("default_ms", ctypes.c_float),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class WosStats(ctypes.Structure):
@@ -160,6 +178,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.wos_build_operator_noalloc.argtypes = [vp, vp, vp, vp, i32, vp, u32, dbl, u64, vp,
                                              vp, vp, vp, vp]
     L.wos_build_operators_batched.argtypes = [vp, i32, vp, u64, vp, vp, vp]
+    L.wos_autotune.argtypes = [vp, vp, u64, i32, u64, vp, vp]
+    L.wos_autotune_reset.argtypes = [vp]
     L.wos_op_svd.argtypes = [vp, vp, i32, i32, u32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.wos_reconstruct.argtypes = [vp, vp, vp, vp, i32, i32, vp, i32, u32, vp, vp, vp, vp,
                                   vp, i32, dbl, vp, vp, vp]
@@ -310,6 +330,7 @@ def wos_check_points(domain, points: np.ndarray) -> int:
 def make_opts(precision: int = 0, step_cap: int = 0, stream_id: int = 0, k0: int = 0,
               k1: int = 0, accumulate: bool = False, block_size: int = 0,
               blocks_per_sm: int = 0, tile_walks: int = 0, hist_slots: int = 0,
+              refill_min: int = 0, tiles_per_warp: int = 0,
               trace_elem=None, trace_steps=None, trace_x=None,
               kernel_events=None) -> WosOpts:
     o = WosOpts()
@@ -322,6 +343,8 @@ def make_opts(precision: int = 0, step_cap: int = 0, stream_id: int = 0, k0: int
     o.blocks_per_sm = blocks_per_sm
     o.tile_walks = tile_walks
     o.hist_slots = hist_slots
+    o.refill_min = refill_min
+    o.tiles_per_warp = tiles_per_warp
     o.trace_elem = _ptr(trace_elem)
     o.trace_steps = _ptr(trace_steps)
     o.trace_x = _ptr(trace_x)
@@ -431,6 +454,35 @@ def wos_build_operators_batched(ctx: Context, insts, seed: int, points=None,
                                          _stream(stream))
     _check(code, "wos_build_operators_batched")
     return counts, unterminated, (st.as_dict() if st is not None else None)
+
+
+def wos_autotune(ctx: Context, inst, seed: int | None = None, sample_walks: int = 20_000_000,
+                 stream=None) -> dict:
+    """Tunes the launch of `inst`'s class (precision, dim, kernel kind) on a
+    bounded sample of its walks; later builds with default launch options use
+    the result.  Returns the chosen configuration and the sample timings."""
+    import torch
+    L = load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    D = make_domain(inst.domain)
+    P, kp = make_partition(inst.domain, inst.partition)
+    Kc = np.ascontiguousarray(inst.K, dtype=np.float64)
+    pts = torch.as_tensor(inst.points, dtype=torch.float64, device=dev)
+    M_tot = int(L.wos_num_elements(ctypes.byref(D), ctypes.byref(P)))
+    counts = torch.empty((inst.M_D, M_tot), dtype=torch.int32, device=dev)
+    pb = WosProblem(ctypes.addressof(D), ctypes.addressof(P), Kc.ctypes.data, pts.data_ptr(),
+                    inst.M_D, int(inst.N), float(inst.eps), int(inst.stream), 0,
+                    counts.data_ptr(), None)
+    out = WosTuning()
+    code = L.wos_autotune(ctx.h, ctypes.byref(pb), int(inst.seed if seed is None else seed),
+                          1 if inst.fp64 else 0, int(sample_walks), ctypes.byref(out),
+                          _stream(stream))
+    _check(code, "wos_autotune")
+    return out.as_dict()
+
+
+def wos_autotune_reset(ctx: Context) -> None:
+    _check(load().wos_autotune_reset(ctx.h), "wos_autotune_reset", False)
 
 
 def wos_op_svd(ctx: Context, counts, N: int, gamma1: np.ndarray, sigma, nu=None,

@@ -57,3 +57,17 @@ def test_batch_options_and_errors():
     with pytest.raises(wos.WosError) as e:
         wos.wos_build_operators_batched(ctx(), insts, seed=7, opts=wos.make_opts(k0=1))
     assert e.value.code == 1
+
+
+def test_autotune_picks_a_config_without_changing_results():
+    inst = W.square_config(N=3000, grid=8)
+    wos.wos_autotune_reset(ctx())
+    ref = gpu_build(inst, trace=False)["counts"]
+    t = wos.wos_autotune(ctx(), inst, sample_walks=2_000_000)
+    assert t["trials"] >= 6 and t["best_ms"] > 0 and t["best_ms"] <= t["default_ms"]
+    assert t["block_size"] in (128, 256) and t["refill_min"] in (1, 4, 8)
+    assert t["tiles_per_warp"] in (4, 16, 64) and t["hist_slots"] in (0, -1)
+    tuned = gpu_build(inst, trace=False)  # default opts now use the tuned config
+    np.testing.assert_array_equal(tuned["counts"], ref)
+    assert tuned["stats"]["block"] == t["block_size"]
+    wos.wos_autotune_reset(ctx())
