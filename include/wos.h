@@ -253,6 +253,7 @@ typedef struct {
     uint32_t step_cap;        /* 0 = 1,000,000 */
     uint32_t *counts;         /* device, M_D x M_tot */
     uint32_t *unterminated;   /* device, M_D, or NULL */
+    uint32_t k0, k1;          /* walk range [k0, k1) of every point; k1 = 0 -> N */
 } wos_problem;
 
 /* Many MC-REM builds (paper Sec. 5.1, Algorithm MC-REM, applied to each
@@ -264,8 +265,8 @@ typedef struct {
  * (block, walk lo, walk hi, stream_id), so its counts are bit-identical to
  * the same problem built alone with wos_build_operator (same stream_id).
  * opts may set precision, accumulate and the launch fields (block_size,
- * blocks_per_sm, tile_walks, hist_slots, kernel_events); k0 / k1 and traces
- * must be zero.  stats (host or NULL): totals over the batch; non-NULL waits.
+ * blocks_per_sm, tile_walks, hist_slots, kernel_events); opts->k0 / k1 and
+ * traces must be zero (each problem has its own walk range).  stats (host or NULL): totals over the batch; non-NULL waits.
  * Errors: those of wos_build_operator, for the first failing problem. */
 wos_status wos_build_operators_batched(wos_context *ctx, int32_t n,
                                        const wos_problem *problems, uint64_t seed,
@@ -297,6 +298,81 @@ wos_status wos_autotune(wos_context *ctx, const wos_problem *sample, uint64_t se
 
 /* Forget every tuned configuration of the context. */
 wos_status wos_autotune_reset(wos_context *ctx);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a request queue with continuous batching (spec serving
+ * pattern; no paper counterpart).  A request is one Cauchy problem end to
+ * end: MC-REM operator build, FP64 SVD and TSVD reconstruction (paper
+ * Algorithm Main).  A worker thread admits queued requests in arrival order
+ * while the device-memory budget and the slot count allow, keeps their counts
+ * resident on the device, and advances every admitted request by a slice of
+ * walks per point in one batched launch per slice, so requests arriving while
+ * others run join at the next slice.  A request whose walks are done gets its
+ * SVD and reconstruction on a side stream, overlapping other requests' walks.
+ * Results are bit-identical to running the same request alone (the walks of a
+ * request are fixed by the queue seed and the request's stream_id).
+ * ------------------------------------------------------------------------- */
+typedef struct wos_queue wos_queue;
+
+typedef struct {
+    int32_t max_inflight;   /* requests admitted at once (0 = 64) */
+    uint64_t device_budget; /* device bytes for admitted requests (0 = 8 GiB) */
+    uint32_t slice_walks;   /* walks per point per slice (0 = 4096) */
+    int32_t precision;      /* walk precision of every request (wos_precision) */
+    uint64_t seed;          /* Philox key of the queue */
+    int32_t side_streams;   /* concurrent SVD / reconstruction pipelines (0 = 8) */
+} wos_queue_opts;
+
+/* One request.  Every pointer is host memory: inputs are copied at submit
+ * time; outputs must stay valid until the request completes. */
+typedef struct {
+    const wos_domain *domain;
+    const wos_partition *partition;
+    const uint8_t *gamma1;  /* M_tot labels (1 = Gamma_1) */
+    const double *K;        /* dim x dim */
+    const double *points;   /* M_D x dim */
+    int32_t M_D;
+    uint32_t N;
+    double eps;
+    uint32_t stream_id;     /* Philox counter word: distinct per request */
+    const double *nu;       /* M_D, or NULL (1/sqrt(M_D)) */
+    const double *uD;       /* M_D measurements */
+    const double *u0;       /* M_0 Gamma_0 data, or NULL (zero) */
+    int32_t r;              /* truncation; 0 = first gap S_r/S_{r+1} >= 1.5
+                               after S_r/S_1 < 1e-3 (else the last gap) */
+    double tikhonov_alpha;  /* 0 = plain truncation */
+    double *u_gamma1;       /* out: M_1 reconstructed Gamma_1 data */
+    double *S;              /* out: k singular values, or NULL */
+    uint32_t *counts;       /* out: M_D x M_tot counts, or NULL */
+    int32_t *r_used;        /* out: the truncation used, or NULL */
+} wos_request;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, failed;
+    uint64_t slices;        /* batched walk launches */
+    uint64_t walks;         /* walks run */
+    int32_t inflight;       /* admitted, not completed */
+    int32_t queued;         /* waiting for admission */
+} wos_queue_stats;
+
+/* Create / destroy a queue on the context's device.  destroy waits for every
+ * submitted request to finish.  Errors: WOS_INVALID_ARG, WOS_CUDA_ERROR. */
+wos_status wos_queue_create(wos_context *ctx, const wos_queue_opts *opts,
+                            wos_queue **q);
+wos_status wos_queue_destroy(wos_queue *q);
+
+/* Submit a request; *ticket identifies it.  Validates it first (errors of
+ * wos_build_operator; WOS_INVALID_ARG if it can never fit the budget). */
+wos_status wos_submit(wos_queue *q, const wos_request *req, uint64_t *ticket);
+
+/* WOS_OK when the request completed (outputs written), WOS_NOT_READY while
+ * it runs, else the error it failed with. */
+wos_status wos_poll(wos_queue *q, uint64_t ticket);
+
+/* Wait up to timeout_ms (< 0: forever) for a request; returns as wos_poll. */
+wos_status wos_wait(wos_queue *q, uint64_t ticket, int32_t timeout_ms);
+
+wos_status wos_queue_get_stats(wos_queue *q, wos_queue_stats *stats);
 
 /* Check that every point (host, M_D x dim) lies strictly inside D.  Returns
  * WOS_OK or WOS_POINT_OUTSIDE (first offending index in *bad if non-NULL). */

@@ -15,7 +15,7 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 OUT = PKG / "_lib"
 LIB = OUT / "libwos.so"
-SOURCES = ["wos_api.cu", "wos_svd.cu", "wos_noalloc.cu", "wos_batch.cu"]
+SOURCES = ["wos_api.cu", "wos_svd.cu", "wos_noalloc.cu", "wos_batch.cu", "wos_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> Path:
                 print(log)
     tmp = LIB.with_suffix(f".{os.getpid()}.tmp")
     cmd = [nvcc(), "-shared", "-o", str(tmp)] + [str(o) for o in objs] + ARCH + [
-        "-lcudart"]
+        "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -54,7 +54,8 @@ wos_status launch_class(wos_context *ctx, const std::vector<int> &idx,
         if (walk_kind(*pb.domain, *pb.partition) != kind)
             kind = kGeneric;
         max_M = std::max(max_M, num_elements(*pb.domain, *pb.partition));
-        total += uint64_t(pb.M_D) * pb.N;
+        const uint32_t k1 = pb.k1 ? pb.k1 : pb.N;
+        total += uint64_t(pb.M_D) * (k1 - pb.k0);
     }
     wos_opts o = o_in;
     apply_tuning(ctx, sizeof(Real) == sizeof(double) ? WOS_FP64 : WOS_FP32, DIM, kind, &o);
@@ -95,8 +96,8 @@ wos_status launch_class(wos_context *ctx, const std::vector<int> &idx,
         const wos_problem &pb = probs[idx[q]];
         WalkInst<Real> &I = recs[q];
         fill_inst<Real>(*pb.domain, *pb.partition, S[idx[q]].data(), pb.points, pb.M_D, pb.N,
-                        pb.eps, pb.stream_id, 0, 0, pb.step_cap, pb.counts, pb.unterminated,
-                        &I);
+                        pb.eps, pb.stream_id, pb.k0, pb.k1, pb.step_cap, pb.counts,
+                        pb.unterminated, &I);
         if (pb.partition->voronoi_n > 0) {
             const size_t ns = size_t(pb.partition->voronoi_n) * DIM;
             for (size_t k = 0; k < ns; ++k)
@@ -109,8 +110,9 @@ wos_status launch_class(wos_context *ctx, const std::vector<int> &idx,
             I.points_r = dpts + p_at;
             p_at += size_t(pb.M_D) * DIM;
         }
-        I.tile_w = tile_size(o, total, plan.grid, plan.block, uint64_t(pb.N));
-        I.tiles_per_point = (pb.N + I.tile_w - 1) / I.tile_w;
+        const uint32_t per_point = I.k1 - I.k0;
+        I.tile_w = tile_size(o, total, plan.grid, plan.block, uint64_t(per_point));
+        I.tiles_per_point = (per_point + I.tile_w - 1) / I.tile_w;
         I.tile_begin = tile_at;
         tile_at += uint64_t(I.tiles_per_point) * uint64_t(pb.M_D);
         if (!o.accumulate) {
@@ -190,7 +192,9 @@ extern "C" wos_status wos_build_operators_batched(wos_context *ctx, int32_t n,
         wos_status st = validate(pb.domain, pb.partition);
         if (st != WOS_OK)
             return st;
-        if (pb.M_D < 1 || pb.N < 1 || !pb.points || !pb.counts || !(pb.eps > 0.0))
+        const uint32_t k1 = pb.k1 ? pb.k1 : pb.N;
+        if (pb.M_D < 1 || pb.N < 1 || !pb.points || !pb.counts || !(pb.eps > 0.0) ||
+            pb.k0 >= k1 || k1 > pb.N)
             return WOS_INVALID_ARG;
         if (num_elements(*pb.domain, *pb.partition) < 1)
             return WOS_INVALID_ARG;

@@ -556,6 +556,45 @@ def mixed_batch(n_instances: int = 64, seed: int = 7, m_lo: int = 64,
     return out
 
 
+@dataclass
+class Request:
+    """One request of a served stream: an instance, its measurement noise
+    level and its arrival offset in units of the mean inter-arrival time."""
+    index: int
+    arrival: float
+    inst: Instance
+    noise: float
+
+
+def serve_stream(n_requests: int = 10_000, seed: int = 11, first: int | None = None,
+                 N: int = 100_000, m_lo: int = 256, m_hi: int = 1024) -> list:
+    """Poisson-arrival stream over the 3-D mix of the ball / cube workloads
+    (1536 boundary patches, K = diag(1, 2, 4) or a random SPD K with
+    eigenvalues log-uniform in [0.5, 4]): per request a domain, a K, a point
+    count log-uniform in [m_lo, m_hi] (points uniform in the inner half), eps
+    in {1e-3, 1e-4}, noise uniform in [0.1, 5] % and an exponential
+    inter-arrival gap of mean 1.  Request q draws from its own generator
+    (seed, q), so a prefix ``first`` of the stream is the same requests as
+    the whole stream's first ones; its walks use stream id q."""
+    n = n_requests if first is None else min(first, n_requests)
+    gaps = np.random.default_rng(seed).exponential(1.0, n_requests)[:n]
+    arrival = np.cumsum(gaps) - gaps[0]
+    out = []
+    for q in range(n):
+        rng = np.random.default_rng([seed, q])
+        cube = bool(rng.integers(2))
+        K = K_DIAG124 if rng.integers(2) == 0 else random_spd(rng, 3, 0.5, 4.0)
+        MD = int(round(math.exp(rng.uniform(math.log(m_lo), math.log(m_hi)))))
+        eps = float(rng.choice([1e-3, 1e-4]))
+        noise = float(rng.uniform(0.001, 0.05))
+        gs = int(rng.integers(1 << 30))
+        inst = (cube_config if cube else ball_config)(N=N, eps=eps, K=K, seed=seed,
+                                                      geom_seed=gs, n_points=MD)
+        out.append(Request(q, float(arrival[q]),
+                           inst.replace(name=f"r{q}-{inst.name}", stream=q), noise))
+    return out
+
+
 def synthetic_counts(M_D: int, M_tot: int, N: int, seed: int = 0,
                      width: float = 0.05) -> np.ndarray:
     """Seeded multinomial count matrix shaped like an operator: row i draws N

@@ -106,6 +106,8 @@ class WosProblem(ctypes.Structure):
         ("step_cap", ctypes.c_uint32),
         ("counts", ctypes.c_void_p),
         ("unterminated", ctypes.c_void_p),
+        ("k0", ctypes.c_uint32),
+        ("k1", ctypes.c_uint32),
     ]
 
 
@@ -136,6 +138,56 @@ class WosStats(ctypes.Structure):
         ("tile_walks", ctypes.c_int32),
         ("hist_slots", ctypes.c_int32),
         ("kernel_ms", ctypes.c_float),
+    ]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class WosQueueOpts(ctypes.Structure):
+    _fields_ = [
+        ("max_inflight", ctypes.c_int32),
+        ("device_budget", ctypes.c_uint64),
+        ("slice_walks", ctypes.c_uint32),
+        ("precision", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+        ("side_streams", ctypes.c_int32),
+    ]
+
+
+class WosRequest(ctypes.Structure):
+    _fields_ = [
+        ("domain", ctypes.c_void_p),
+        ("partition", ctypes.c_void_p),
+        ("gamma1", ctypes.c_void_p),
+        ("K", ctypes.c_void_p),
+        ("points", ctypes.c_void_p),
+        ("M_D", ctypes.c_int32),
+        ("N", ctypes.c_uint32),
+        ("eps", ctypes.c_double),
+        ("stream_id", ctypes.c_uint32),
+        ("nu", ctypes.c_void_p),
+        ("uD", ctypes.c_void_p),
+        ("u0", ctypes.c_void_p),
+        ("r", ctypes.c_int32),
+        ("tikhonov_alpha", ctypes.c_double),
+        ("u_gamma1", ctypes.c_void_p),
+        ("S", ctypes.c_void_p),
+        ("counts", ctypes.c_void_p),
+        ("r_used", ctypes.c_void_p),
+    ]
+
+
+class WosQueueStats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_uint64),
+        ("admitted", ctypes.c_uint64),
+        ("completed", ctypes.c_uint64),
+        ("failed", ctypes.c_uint64),
+        ("slices", ctypes.c_uint64),
+        ("walks", ctypes.c_uint64),
+        ("inflight", ctypes.c_int32),
+        ("queued", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -184,6 +236,12 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.wos_reconstruct.argtypes = [vp, vp, vp, vp, i32, i32, vp, i32, u32, vp, vp, vp, vp,
                                   vp, i32, dbl, vp, vp, vp]
     L.wos_truncation_gap.argtypes = [vp, i32, i32]
+    L.wos_queue_create.argtypes = [vp, vp, ctypes.POINTER(vp)]
+    L.wos_queue_destroy.argtypes = [vp]
+    L.wos_submit.argtypes = [vp, vp, ctypes.POINTER(u64)]
+    L.wos_poll.argtypes = [vp, u64]
+    L.wos_wait.argtypes = [vp, u64, i32]
+    L.wos_queue_get_stats.argtypes = [vp, vp]
     _lib = L
     return L
 
@@ -472,7 +530,7 @@ def wos_autotune(ctx: Context, inst, seed: int | None = None, sample_walks: int 
     counts = torch.empty((inst.M_D, M_tot), dtype=torch.int32, device=dev)
     pb = WosProblem(ctypes.addressof(D), ctypes.addressof(P), Kc.ctypes.data, pts.data_ptr(),
                     inst.M_D, int(inst.N), float(inst.eps), int(inst.stream), 0,
-                    counts.data_ptr(), None)
+                    counts.data_ptr(), None, 0, 0)
     out = WosTuning()
     code = L.wos_autotune(ctx.h, ctypes.byref(pb), int(inst.seed if seed is None else seed),
                           1 if inst.fp64 else 0, int(sample_walks), ctypes.byref(out),
@@ -574,3 +632,97 @@ def solve_instance(ctx: Context, inst, uD, u0, r: int, points=None, sigma=None,
     u1, uhat = wos_reconstruct(ctx, U, S, V, counts, inst.N, inst.partition.gamma1,
                                sigma, uD, r, u0=u0, stream=stream)
     return Solution(counts, unterm, U, S, V, u1, uhat, st, sw)
+
+
+# ---------------------------------------------------------------------------
+# serving: request queue with continuous batching
+# ---------------------------------------------------------------------------
+@dataclass
+class Ticket:
+    id: int
+    u_gamma1: np.ndarray
+    S: np.ndarray
+    counts: np.ndarray | None
+    r_used: ctypes.c_int32
+    keep: list
+
+
+def wos_queue_create(ctx: Context, seed: int, precision: int = 0, max_inflight: int = 0,
+                     device_budget: int = 0, slice_walks: int = 0,
+                     side_streams: int = 0) -> ctypes.c_void_p:
+    o = WosQueueOpts(int(max_inflight), int(device_budget), int(slice_walks),
+                     int(precision), int(seed), int(side_streams))
+    h = ctypes.c_void_p()
+    _check(load().wos_queue_create(ctx.h, ctypes.byref(o), ctypes.byref(h)),
+           "wos_queue_create", False)
+    return h
+
+
+def wos_queue_destroy(q) -> None:
+    _check(load().wos_queue_destroy(q), "wos_queue_destroy", False)
+
+
+def wos_submit(q, inst, uD: np.ndarray, u0: np.ndarray | None = None, r: int = 0,
+               tikhonov_alpha: float = 0.0, nu: np.ndarray | None = None,
+               want_counts: bool = False) -> Ticket:
+    """Queues one workloads.Instance end to end (host inputs; outputs land in
+    the returned Ticket's host arrays once the request completes)."""
+    L = load()
+    D = make_domain(inst.domain)
+    P, kp = make_partition(inst.domain, inst.partition)
+    Kc = np.ascontiguousarray(inst.K, dtype=np.float64)
+    pts = np.ascontiguousarray(inst.points, dtype=np.float64)
+    g1 = np.ascontiguousarray(inst.partition.gamma1, dtype=np.uint8)
+    M_tot, M_1 = int(g1.size), int(g1.sum())
+    k = min(inst.M_D, M_1)
+    uDc = np.ascontiguousarray(uD, dtype=np.float64)
+    u0c = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64)
+    nuc = None if nu is None else np.ascontiguousarray(nu, dtype=np.float64)
+    u1 = np.zeros(M_1)
+    S = np.zeros(k)
+    cnt = np.zeros((inst.M_D, M_tot), dtype=np.uint32) if want_counts else None
+    r_used = ctypes.c_int32(0)
+    rq = WosRequest()
+    rq.domain = ctypes.addressof(D)
+    rq.partition = ctypes.addressof(P)
+    rq.gamma1 = g1.ctypes.data
+    rq.K = Kc.ctypes.data
+    rq.points = pts.ctypes.data
+    rq.M_D = inst.M_D
+    rq.N = int(inst.N)
+    rq.eps = float(inst.eps)
+    rq.stream_id = int(inst.stream)
+    rq.nu = None if nuc is None else nuc.ctypes.data
+    rq.uD = uDc.ctypes.data
+    rq.u0 = None if u0c is None else u0c.ctypes.data
+    rq.r = int(r)
+    rq.tikhonov_alpha = float(tikhonov_alpha)
+    rq.u_gamma1 = u1.ctypes.data
+    rq.S = S.ctypes.data
+    rq.counts = None if cnt is None else cnt.ctypes.data
+    rq.r_used = ctypes.addressof(r_used)
+    t = ctypes.c_uint64(0)
+    _check(L.wos_submit(q, ctypes.byref(rq), ctypes.byref(t)), "wos_submit", False)
+    return Ticket(int(t.value), u1, S, cnt, r_used, [D, P, kp, rq])
+
+
+def wos_poll(q, ticket: Ticket) -> bool:
+    code = load().wos_poll(q, ticket.id)
+    if code == 12:
+        return False
+    _check(code, "wos_poll", False)
+    return True
+
+
+def wos_wait(q, ticket: Ticket, timeout_ms: int = -1) -> bool:
+    code = load().wos_wait(q, ticket.id, int(timeout_ms))
+    if code == 12:
+        return False
+    _check(code, "wos_wait", False)
+    return True
+
+
+def wos_queue_get_stats(q) -> dict:
+    st = WosQueueStats()
+    _check(load().wos_queue_get_stats(q, ctypes.byref(st)), "wos_queue_get_stats", False)
+    return st.as_dict()

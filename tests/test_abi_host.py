@@ -59,14 +59,18 @@ int main(void) {
   printf("%zu %zu %zu %zu\\n", offsetof(wos_domain, hole_radius),
          offsetof(wos_partition, voronoi_sites), offsetof(wos_opts, kernel_events),
          offsetof(wos_stats, kernel_ms));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(wos_problem), sizeof(wos_request),
+         sizeof(wos_queue_opts), sizeof(wos_queue_stats), offsetof(wos_problem, k1),
+         offsetof(wos_request, r_used), offsetof(wos_queue_opts, side_streams),
+         offsetof(wos_queue_stats, queued));
   return 0;
 }
 """)
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", str(ROOT / "include"), str(src), "-o", str(exe)],
                    check=True)
-    a, b = subprocess.run([str(exe)], capture_output=True, text=True,
-                          check=True).stdout.split("\n")[:2]
+    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True,
+                             check=True).stdout.split("\n")[:3]
     sizes = [int(x) for x in a.split()]
     offs = [int(x) for x in b.split()]
     assert sizes == [ctypes.sizeof(wos.WosDomain), ctypes.sizeof(wos.WosPartition),
@@ -74,6 +78,11 @@ int main(void) {
     assert offs == [wos.WosDomain.hole_radius.offset,
                     wos.WosPartition.voronoi_sites.offset,
                     wos.WosOpts.kernel_events.offset, wos.WosStats.kernel_ms.offset]
+    assert [int(x) for x in c.split()] == [
+        ctypes.sizeof(wos.WosProblem), ctypes.sizeof(wos.WosRequest),
+        ctypes.sizeof(wos.WosQueueOpts), ctypes.sizeof(wos.WosQueueStats),
+        wos.WosProblem.k1.offset, wos.WosRequest.r_used.offset,
+        wos.WosQueueOpts.side_streams.offset, wos.WosQueueStats.queued.offset]
 
 
 def test_conductivity_sqrt_matches_oracle(lib):
