@@ -239,25 +239,7 @@ def run_gpu(args, rank: int, world: int, dist):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     streams = [torch.cuda.Stream(device=dev) for _ in prep]
-
-    def one(p, timing_events=None, host_io=False, stream=None):
-        inst = p["inst"]
-        opts = wos.make_opts(precision=0, stream_id=inst.stream,
-                             kernel_events=timing_events)
-        if host_io:
-            pts = p["host"]["points"].to(dev, non_blocking=True)
-            uD = p["host"]["uD"].to(dev, non_blocking=True)
-            u0 = p["host"]["u0"].to(dev, non_blocking=True)
-        else:
-            pts, uD, u0 = p["points"], p["uD"], p["u0"]
-        sol = wos.solve_instance(ctx, inst, uD, u0, p["r"], points=pts, sigma=p["sigma"],
-                                 opts=opts, stream=stream)
-        if host_io:
-            c = sol.counts.to("cpu", non_blocking=True)
-            u1 = sol.u_gamma1.to("cpu", non_blocking=True)
-            return sol, (c, u1)
-        return sol, None
-
+    build_stream = torch.cuda.Stream(device=dev)
     # warm-up: truncation ranks from the spectra, step counts from stats
     steps_per_inst = []
     for p in prep:
@@ -272,25 +254,58 @@ def run_gpu(args, rank: int, world: int, dist):
         p["kind"] = "box" if inst.domain.outer == "box" else "annulus"
         steps_per_inst.append(st["steps"])
     def step(timing=None, host_io=False, start_ev=None):
-        """One step: every instance's pipeline on its own stream, joined on
-        the current stream (instances overlap on the GPU)."""
+        """One step: the operator builds back to back on one stream (a
+        persistent walk launch fills the GPU), then every instance's SVD and
+        reconstruction on its own stream (the latency-bound SVDs overlap),
+        joined on the current stream."""
         main = torch.cuda.current_stream()
-        outs = []
-        done = []
+        bs = build_stream
+        if start_ev is not None:
+            bs.wait_event(start_ev)
+        else:
+            bs.wait_stream(main)
+        built = []
+        with torch.cuda.stream(bs):
+            for q, p in enumerate(prep):
+                inst = p["inst"]
+                if host_io:
+                    pts = p["host"]["points"].to(dev, non_blocking=True)
+                    uD = p["host"]["uD"].to(dev, non_blocking=True)
+                    u0 = p["host"]["u0"].to(dev, non_blocking=True)
+                else:
+                    pts, uD, u0 = p["points"], p["uD"], p["u0"]
+                opts = wos.make_opts(precision=0, stream_id=inst.stream,
+                                     kernel_events=timing[q] if timing else None)
+                c, _, _ = wos.wos_build_operator(ctx, inst.domain, inst.K, pts,
+                                                 inst.partition, inst.N, inst.eps, inst.seed,
+                                                 opts=opts, stats=False, stream=bs)
+                built.append((c, uD, u0))
+        ev_built = torch.cuda.Event()
+        ev_built.record(bs)
+        outs, done = [], []
         for q, p in enumerate(prep):
             s = streams[q]
-            if start_ev is not None:
-                s.wait_event(start_ev)
-            else:
-                s.wait_stream(main)
+            s.wait_event(ev_built)
+            inst = p["inst"]
+            c, uD, u0 = built[q]
+            for t in (c, uD, u0):
+                t.record_stream(s)
             with torch.cuda.stream(s):
-                outs.append(one(p, timing_events=timing[q] if timing else None,
-                                host_io=host_io, stream=s))
-                ev = torch.cuda.Event()
-                ev.record(s)
-                done.append(ev)
-        for ev in done:
-            main.wait_event(ev)
+                g1 = inst.partition.gamma1
+                U, S, V, _ = wos.wos_op_svd(ctx, c, inst.N, g1, p["sigma"], sync=False,
+                                            stream=s)
+                u1, _ = wos.wos_reconstruct(ctx, U, S, V, c, inst.N, g1, p["sigma"], uD,
+                                            p["r"], u0=u0, stream=s)
+                if host_io:
+                    outs.append((c.to("cpu", non_blocking=True),
+                                 u1.to("cpu", non_blocking=True)))
+                else:
+                    outs.append((c, u1))
+                e = torch.cuda.Event()
+                e.record(s)
+                done.append(e)
+        for e in done:
+            main.wait_event(e)
         return outs
 
     for _ in range(args.warmup):
@@ -367,7 +382,7 @@ def run_gpu(args, rank: int, world: int, dist):
     e2e_s.record(stream)
     for it in range(args.steps):
         outs = step(host_io=True)
-        d2h = sum(o[1][0].numel() * 4 + o[1][1].numel() * 8 for o in outs)
+        d2h = sum(o[0].numel() * 4 + o[1].numel() * 8 for o in outs)
     e2e_e.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e2e_s.elapsed_time(e2e_e)

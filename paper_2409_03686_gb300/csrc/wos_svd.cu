@@ -7,9 +7,10 @@
 // FP64, oriented so that the worked matrix W has m >= n columns-of-length-m,
 // and its columns are orthogonalised by one-sided (Hestenes) Jacobi rotations
 // in the parallel round-robin order: each round pairs the n columns into n/2
-// disjoint pairs, one warp per pair; n - 1 rounds make a sweep that touches
-// every pair once.  Rounds are separated by a grid barrier of a cooperative
-// launch (every wait is bounded and reports WOS_DEVICE_TIMEOUT).  A pair is
+// disjoint pairs, one CTA per pair; n - 1 rounds make a sweep that touches
+// every pair once.  Rounds are ordered by per-column version flags, sweeps by
+// a grid barrier of a cooperative launch (every wait is bounded and reports
+// WOS_DEVICE_TIMEOUT).  A pair is
 // rotated when |w_p . w_q| > tol sqrt(|w_p|^2 |w_q|^2), tol = 1e-15, the
 // relative test of Demmel & Veselic (1992); the build stops after a sweep
 // without rotations.  FP64 is used for everything here: the operator is
@@ -30,9 +31,7 @@ namespace {
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr double kTol = 1e-15;
 constexpr int kMaxSweeps = 80;
-constexpr int kSvdBlock = 256;
 constexpr int kPairThreads = 128;
-constexpr int kRowsPerThread = 4;  // rows kept in registers per thread
 static_assert(kPairThreads == 128, "the partial sums below assume four warps");
 
 struct SvdWork {
@@ -104,9 +103,9 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *a)
     return v;
 }
 
-__device__ __forceinline__ void st_release(unsigned *a, unsigned v)
+__device__ __forceinline__ void st_relaxed(unsigned *a, unsigned v)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
 }
 
 // Wait (bounded, about 2 s) until column version ver[c] >= want.
@@ -129,19 +128,59 @@ __device__ bool wait_version(const unsigned *ver, int c, unsigned want, unsigned
     }
 }
 
+// Sums of (a, b, g) over the 32 lanes of a warp with six additions per lane
+// (instead of fifteen for three butterflies): the first two exchange steps
+// split the values between lane halves and quarters, the last three are a
+// butterfly on one value.  On return lanes 0-7 hold sum(a), lanes 8-15
+// sum(b), lanes 16-23 sum(g).
+__device__ __forceinline__ double warp_sum3(double a, double b, double g, int lane)
+{
+    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+    double k0 = hi16 ? g : a, k1 = hi16 ? 0.0 : b;
+    k0 += __shfl_xor_sync(FULL, hi16 ? a : g, 16);
+    k1 += __shfl_xor_sync(FULL, hi16 ? b : 0.0, 16);
+    double k = hi8 ? k1 : k0;
+    k += __shfl_xor_sync(FULL, hi8 ? k0 : k1, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1)
+        k += __shfl_xor_sync(FULL, k, o);
+    return k;
+}
+
+// Rotation (c, s) that makes the pair orthogonal, from the Gram entries
+// al = |x|^2, be = |y|^2, ga = x.y (Hestenes; Rutishauser's smaller angle):
+// with h = (be - al) / 2 and r = sqrt(h^2 + ga^2), cos(2 theta) = |h| / r, so
+// c^2 = (1 + |h| / r) / 2 and s = sign(h) ga / (2 r c).  Two reciprocal
+// square roots and no division: the dependent FP64 chain is the critical
+// path of a round.
+__device__ __forceinline__ void jacobi_rotation(double al, double be, double ga, double &c,
+                                                double &s)
+{
+    const double h = 0.5 * (be - al);
+    const double y = rsqrt(fma(h, h, ga * ga));  // 1 / r
+    const double c2 = fma(fabs(h) * y, 0.5, 0.5);
+    const double gy = copysign(0.5, h) * ga * y;
+    const double z = rsqrt(c2);                  // 1 / c
+    c = c2 * z;
+    s = gy * z;
+}
+
 // One pair per CTA of kPairThreads threads; the m rows are split over the
-// CTA so a pair uses a whole SM's FP64 pipe.  Rounds are ordered by column
-// versions: ver[c] counts the rounds that have finished with column c, so the
-// pair (p, q) of global round R starts once ver[p] >= R and ver[q] >= R (the
-// previous round's writers of p and q are done).  Only one grid barrier per
-// sweep remains, for the convergence test.  Columns are read and written
-// through L2 (ld.cg / st.cg): other SMs update them between rounds.
+// CTA (RPT rows per thread kept in registers, the rest streamed) so a pair
+// uses a whole SM's FP64 pipe.  Rounds are ordered by column versions: ver[c]
+// counts the rounds that have finished with column c, so the pair (p, q) of
+// global round R starts once ver[p] >= R and ver[q] >= R (the previous
+// round's writers of p and q are done; warps 0 and 1 wait for one each).
+// Only one grid barrier per sweep remains, for the convergence test.  Columns
+// are read and written through L2 (ld.cg / st.cg): other SMs update them
+// between rounds; one fence orders a pair's stores before its two flags.
+template <int RPT>
 __global__ void __launch_bounds__(kPairThreads)
 jacobi_kernel(SvdWork w)
 {
     __shared__ double part[3][kPairThreads / 32];
     __shared__ double cs[2];
-    __shared__ int go, flag;
+    __shared__ int flag;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int half = w.n_pad / 2;
     const int m = w.m, n = w.n;
@@ -156,26 +195,21 @@ jacobi_kernel(SvdWork w)
                 int a = rr_player(pr, r, w.n_pad);
                 int b = rr_player(w.n_pad - 1 - pr, r, w.n_pad);
                 int p = min(a, b), q = max(a, b);
-                if (tid == 0) {
-                    bool ok = wait_version(w.ver, p, R, status);
-                    if (ok && q < n)
-                        ok = wait_version(w.ver, q, R, status);
-                    go = ok;
-                }
-                __syncthreads();
-                if (!go)
+                bool ok = true;
+                if (tid == 0)
+                    ok = wait_version(w.ver, p, R, status);
+                else if (tid == 32 && q < n)
+                    ok = wait_version(w.ver, q, R, status);
+                if (!__syncthreads_and(ok))
                     return;
                 bool rotated = false;
                 if (q < n) {
                     double *wp = w.W + size_t(p) * m, *wq = w.W + size_t(q) * m;
                     double *vp = w.Vw + size_t(p) * n, *vq = w.Vw + size_t(q) * n;
-                    // this thread's rows stay in registers between the dot
-                    // products and the rotation (m <= kRowsPerThread * CTA)
-                    double xr[kRowsPerThread], yr[kRowsPerThread];
-                    double vx[kRowsPerThread], vy[kRowsPerThread];
+                    double xr[RPT], yr[RPT], vx[RPT], vy[RPT];
                     double al = 0.0, be = 0.0, ga = 0.0;
 #pragma unroll
-                    for (int k = 0; k < kRowsPerThread; ++k) {
+                    for (int k = 0; k < RPT; ++k) {
                         int i = tid + k * kPairThreads;
                         xr[k] = i < m ? __ldcg(wp + i) : 0.0;
                         yr[k] = i < m ? __ldcg(wq + i) : 0.0;
@@ -183,33 +217,26 @@ jacobi_kernel(SvdWork w)
                         vy[k] = i < n ? __ldcg(vq + i) : 0.0;
                     }
 #pragma unroll
-                    for (int k = 0; k < kRowsPerThread; ++k) {
-                        al = fma(xr[k], xr[k], al);
-                        be = fma(yr[k], yr[k], be);
-                        ga = fma(xr[k], yr[k], ga);
+                    for (int k = 0; k < RPT; ++k) {
+                        if (tid + k * kPairThreads < m) {
+                            al = fma(xr[k], xr[k], al);
+                            be = fma(yr[k], yr[k], be);
+                            ga = fma(xr[k], yr[k], ga);
+                        }
                     }
-                    for (int i = tid + kRowsPerThread * kPairThreads; i < m; i += kPairThreads) {
+                    for (int i = tid + RPT * kPairThreads; i < m; i += kPairThreads) {
                         double x = __ldcg(wp + i), y = __ldcg(wq + i);
                         al = fma(x, x, al);
                         be = fma(y, y, be);
                         ga = fma(x, y, ga);
                     }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        al += __shfl_xor_sync(FULL, al, o);
-                        be += __shfl_xor_sync(FULL, be, o);
-                        ga += __shfl_xor_sync(FULL, ga, o);
-                    }
-                    if (lane == 0) {
-                        part[0][wid] = al;
-                        part[1][wid] = be;
-                        part[2][wid] = ga;
-                    }
+                    const double red = warp_sum3(al, be, ga, lane);
+                    if ((lane & 7) == 0 && lane < 24)
+                        part[lane >> 3][wid] = red;
                     __syncthreads();
                     // one thread combines the partial sums and computes the
                     // rotation (FP64 is scarce on this part: 2 FMA/clk/SM)
                     if (tid == 0) {
-                        // pairwise sums of the four warp partials
                         al = (part[0][0] + part[0][1]) + (part[0][2] + part[0][3]);
                         be = (part[1][0] + part[1][1]) + (part[1][2] + part[1][3]);
                         ga = (part[2][0] + part[2][1]) + (part[2][2] + part[2][3]);
@@ -217,13 +244,7 @@ jacobi_kernel(SvdWork w)
                         int rot_flag = 0;
                         // rotate when |ga| > tol sqrt(al be), tested squared
                         if (al != 0.0 && be != 0.0 && ga * ga > (kTol * kTol) * (al * be)) {
-                            // t = ga / (h + sign(h) sqrt(h^2 + ga^2)), h = (be - al) / 2:
-                            // the smaller root of t^2 + 2 zeta t - 1, zeta = h / ga
-                            double h = 0.5 * (be - al);
-                            double rt = sqrt(fma(h, h, ga * ga));
-                            double t = ga / (h >= 0.0 ? h + rt : h - rt);
-                            c = rsqrt(fma(t, t, 1.0));
-                            sn = c * t;
+                            jacobi_rotation(al, be, ga, c, sn);
                             rot_flag = 1;
                         }
                         cs[0] = c;
@@ -235,7 +256,7 @@ jacobi_kernel(SvdWork w)
                         rotated = true;
                         const double c = cs[0], s = cs[1];
 #pragma unroll
-                        for (int k = 0; k < kRowsPerThread; ++k) {
+                        for (int k = 0; k < RPT; ++k) {
                             int i = tid + k * kPairThreads;
                             if (i < m) {
                                 __stcg(wp + i, c * xr[k] - s * yr[k]);
@@ -246,12 +267,12 @@ jacobi_kernel(SvdWork w)
                                 __stcg(vq + i, s * vx[k] + c * vy[k]);
                             }
                         }
-                        for (int i = tid + kRowsPerThread * kPairThreads; i < m; i += kPairThreads) {
+                        for (int i = tid + RPT * kPairThreads; i < m; i += kPairThreads) {
                             double x = __ldcg(wp + i), y = __ldcg(wq + i);
                             __stcg(wp + i, c * x - s * y);
                             __stcg(wq + i, s * x + c * y);
                         }
-                        for (int i = tid + kRowsPerThread * kPairThreads; i < n; i += kPairThreads) {
+                        for (int i = tid + RPT * kPairThreads; i < n; i += kPairThreads) {
                             double x = __ldcg(vp + i), y = __ldcg(vq + i);
                             __stcg(vp + i, c * x - s * y);
                             __stcg(vq + i, s * x + c * y);
@@ -261,11 +282,12 @@ jacobi_kernel(SvdWork w)
                 __syncthreads();
                 if (tid == 0) {
                     // the CTA's stores are ordered before the flags by the
-                    // barrier above and the release fence here
+                    // barrier above and this fence (a fence followed by
+                    // relaxed stores is a release pattern)
                     __threadfence();
-                    st_release(w.ver + p, R + 1u);
+                    st_relaxed(w.ver + p, R + 1u);
                     if (q < n)
-                        st_release(w.ver + q, R + 1u);
+                        st_relaxed(w.ver + q, R + 1u);
                     if (rotated)
                         atomicAdd(rot, 1u);
                 }
@@ -281,6 +303,16 @@ jacobi_kernel(SvdWork w)
     }
     if (blockIdx.x == 0 && tid == 0)
         atomicExch(w.bar + 5, unsigned(WOS_NO_CONVERGENCE));
+}
+
+// Kernel instance by rows per thread kept in registers: the fewest that hold
+// a column (up to 8; longer columns stream the rest).
+const void *jacobi_kernel_for(int m)
+{
+    if (m <= kPairThreads) return reinterpret_cast<const void *>(&jacobi_kernel<1>);
+    if (m <= 2 * kPairThreads) return reinterpret_cast<const void *>(&jacobi_kernel<2>);
+    if (m <= 4 * kPairThreads) return reinterpret_cast<const void *>(&jacobi_kernel<4>);
+    return reinterpret_cast<const void *>(&jacobi_kernel<8>);
 }
 
 // B (worked orientation): W[:, col] with col over Gamma_1 elements (or
@@ -496,11 +528,12 @@ extern "C" wos_status wos_op_svd(wos_context *ctx, const uint32_t *counts, int32
                                           nu, sigma, transposed);
     // cooperative Jacobi: one pair per CTA at a time, all CTAs co-resident
     int bps = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, jacobi_kernel, kPairThreads, 0);
+    const void *jk = jacobi_kernel_for(w.m);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, jk, kPairThreads, 0);
     int pairs = w.n_pad / 2;
     int grid = std::max(1, std::min({pairs, 2 * sms, std::max(1, bps) * sms}));
     void *args[] = {&w};
-    e = cudaLaunchCooperativeKernel(reinterpret_cast<void *>(jacobi_kernel), dim3(grid),
+    e = cudaLaunchCooperativeKernel(jk, dim3(grid),
                                     dim3(kPairThreads), args, 0, st);
     if (e == cudaSuccess) {
         column_norms_kernel<<<sms, 256, 0, st>>>(w, sv);

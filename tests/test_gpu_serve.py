@@ -44,7 +44,7 @@ _alone_cache = {}
 
 
 def _alone(inst, m, r=0, alpha=0.0):
-    key = (inst.name, r, alpha)
+    key = (inst.name, inst.fp64, r, alpha)
     if key in _alone_cache:
         return _alone_cache[key]
     dev = torch.device("cuda:0")
