@@ -108,6 +108,20 @@ __device__ __forceinline__ int32_t walk_classify(const Geom<Real> &g, const Real
     return classify<Real, DIM>(g, x);
 }
 
+// X += re S U (re = 0 leaves X as it is: a stopped walk keeps its point).
+template <typename Real, int DIM>
+__device__ __forceinline__ void step_move(const Real *S, const Real *U, Real re, Real *X)
+{
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        Real su = S[a * DIM] * U[0];
+#pragma unroll
+        for (int b = 1; b < DIM; ++b)
+            su = fma(S[a * DIM + b], U[b], su);
+        X[a] = fma(re, su, X[a]);
+    }
+}
+
 constexpr int kQueue = 64;  // per-warp exit queue (entries)
 
 // Shared-memory bytes of one warp's exit queue: DIM coordinates and five
@@ -184,7 +198,7 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
             for (int a = 0; a < DIM; ++a)
                 Xe[a] = qx[a * kQueue + e];
             const int32_t ei = int32_t(qi[e]);
-            const WalkInst<Real> &I = inst(int32_t(qinst[e]));
+            const WalkInst<Real> &I = inst(MULTI ? int32_t(qinst[e]) : 0);
             const uint32_t sg = qsg[e];
             const int32_t j = walk_classify<Real, DIM, KIND>(I.g, Xe);
             if (!MULTI && p.trace_elem) {
@@ -214,163 +228,181 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
     int32_t lslot = 0;
     uint32_t lgen = 0;
     bool active = false;
-    unsigned long long my_steps = 0, my_walks = 0, my_unterm = 0;
-    uint32_t my_max = 0;
+    unsigned long long my_steps = 0;
+    uint32_t my_walks = 0, my_max = 0, my_unterm = 0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+        X[a] = Real(0);
+    // warp-uniform state of the current tile: start point and walk-id base
+    Real tile_x[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+        tile_x[a] = Real(0);
+    uint64_t tile_wbase = 0;
 
-    bool need = true;
     for (;;) {
-        // ---- refill: lanes with `need` take walks from the warp's tile -----
-        unsigned need_mask = __ballot_sync(FULL, need);
-        if (int32_t(__popc(need_mask)) < p.refill_min && __any_sync(FULL, active))
-            need_mask = 0u;  // refill granularity: let a few lanes idle
-        while (need_mask != 0u && !no_more) {
-            uint32_t avail = tile_kend - tile_k;
-            if (avail == 0u) {
-                unsigned long long t = 0;
-                if (lane == 0)
-                    t = atomicAdd(p.work, 1ull);
-                t = __shfl_sync(FULL, t, 0);
-                if (t >= p.n_tiles) {
-                    no_more = true;
-                    break;
-                }
-                int32_t q = 0;
-                if (MULTI) {  // last instance whose first tile is <= t
-                    int32_t lo = 0, hi = p.n_inst - 1;
-                    while (lo < hi) {
-                        int32_t mid = (lo + hi + 1) >> 1;
-                        if (insts[mid].tile_begin <= t) lo = mid;
-                        else hi = mid - 1;
+        // ---- refill: lanes without a walk take the next walks of the warp's
+        // tile; every lane runs the same select sequence (no divergence).
+        unsigned need_mask = __ballot_sync(FULL, !active);
+        if (need_mask != 0u &&
+            (int32_t(__popc(need_mask)) >= p.refill_min || need_mask == FULL)) {
+            while (need_mask != 0u && !no_more) {
+                if (tile_k == tile_kend) {
+                    unsigned long long t = 0;
+                    if (lane == 0)
+                        t = atomicAdd(p.work, 1ull);
+                    t = __shfl_sync(FULL, t, 0);
+                    if (t >= p.n_tiles) {
+                        no_more = true;
+                        break;
                     }
-                    q = lo;
-                }
-                const WalkInst<Real> &T = inst(q);
-                const uint64_t tl = t - T.tile_begin;
-                const uint32_t ti = uint32_t(tl / T.tiles_per_point);
-                const uint32_t tr = uint32_t(tl - uint64_t(ti) * T.tiles_per_point);
-                tile_inst = q;
-                tile_i = int32_t(ti);
-                tile_k = T.k0 + tr * T.tile_w;
-                tile_kend = min(tile_k + T.tile_w, T.k1);
-                if (p.nslot > 0) {
-                    int32_t s = (p.nslot == 2) ? (slot_cur ^ 1) : 0;
-                    int32_t old_pt = s ? pt1 : pt0;
-                    if (old_pt >= 0) {
-                        const WalkInst<Real> &O = inst(s ? in1 : in0);
-                        flush_slot(hist + s * p.hist_words, p.hist_words,
-                                   O.counts + size_t(old_pt) * O.g.M_tot, lane);
+                    int32_t q = 0;
+                    if (MULTI) {  // last instance whose first tile is <= t
+                        int32_t lo = 0, hi = p.n_inst - 1;
+                        while (lo < hi) {
+                            int32_t mid = (lo + hi + 1) >> 1;
+                            if (insts[mid].tile_begin <= t) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        q = lo;
                     }
-                    if (s) { ++gen1; pt1 = tile_i; in1 = tile_inst; }
-                    else { ++gen0; pt0 = tile_i; in0 = tile_inst; }
-                    slot_cur = s;
+                    const WalkInst<Real> &T = inst(q);
+                    const uint64_t tl = t - T.tile_begin;
+                    const uint32_t ti = uint32_t(tl / T.tiles_per_point);
+                    const uint32_t tr = uint32_t(tl - uint64_t(ti) * T.tiles_per_point);
+                    tile_inst = q;
+                    tile_i = int32_t(ti);
+                    tile_k = T.k0 + tr * T.tile_w;
+                    tile_kend = min(tile_k + T.tile_w, T.k1);
+                    tile_wbase = uint64_t(ti) * T.N;
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a)
+                        tile_x[a] = T.points_r ? T.points_r[size_t(ti) * DIM + a]
+                                               : Real(T.points[size_t(ti) * DIM + a]);
+                    if (p.nslot > 0) {
+                        int32_t s = (p.nslot == 2) ? (slot_cur ^ 1) : 0;
+                        int32_t old_pt = s ? pt1 : pt0;
+                        if (old_pt >= 0) {
+                            const WalkInst<Real> &O = inst(s ? in1 : in0);
+                            flush_slot(hist + s * p.hist_words, p.hist_words,
+                                       O.counts + size_t(old_pt) * O.g.M_tot, lane);
+                        }
+                        if (s) { ++gen1; pt1 = tile_i; in1 = tile_inst; }
+                        else { ++gen0; pt0 = tile_i; in0 = tile_inst; }
+                        slot_cur = s;
+                    }
+                    continue;
                 }
-                continue;
-            }
-            bool mine = (need_mask >> lane) & 1u;
-            uint32_t rank = __popc(need_mask & lt_mask);
-            uint32_t n = __popc(need_mask);
-            uint32_t take = n < avail ? n : avail;
-            if (mine && rank < take) {
-                const WalkInst<Real> &T = inst(tile_inst);
-                linst = tile_inst;
-                li = tile_i;
-                lk = tile_k + rank;
-                uint64_t wid = uint64_t(li) * T.N + lk;
-                wlo = uint32_t(wid);
-                whi = uint32_t(wid >> 32);
+                const uint32_t avail = tile_kend - tile_k;
+                const uint32_t rank = __popc(need_mask & lt_mask);
+                const uint32_t n = __popc(need_mask);
+                const uint32_t take = n < avail ? n : avail;
+                const bool got = ((need_mask >> lane) & 1u) && rank < take;
+                const uint32_t k = tile_k + rank;
+                const uint64_t wid = tile_wbase + k;
 #pragma unroll
                 for (int a = 0; a < DIM; ++a)
-                    X[a] = T.points_r ? T.points_r[size_t(li) * DIM + a]
-                                      : Real(T.points[size_t(li) * DIM + a]);
-                nstep = 0;
-                active = true;
-                lslot = slot_cur;
-                lgen = slot_cur ? gen1 : gen0;
+                    X[a] = got ? tile_x[a] : X[a];
+                wlo = got ? uint32_t(wid) : wlo;
+                whi = got ? uint32_t(wid >> 32) : whi;
+                lk = got ? k : lk;
+                li = got ? tile_i : li;
+                if (MULTI)
+                    linst = got ? tile_inst : linst;
+                nstep = got ? 0u : nstep;
+                lslot = got ? slot_cur : lslot;
+                lgen = got ? (slot_cur ? gen1 : gen0) : lgen;
+                active = active || got;
+                tile_k += take;
+                need_mask &= ~__ballot_sync(FULL, got);
             }
-            tile_k += take;
-            need_mask = __ballot_sync(FULL, mine && rank >= take);
         }
         if (!__any_sync(FULL, active))
             break;
 
         // ---- one group of G steps of the chain (Eq. (wos chain)) -----------
-        // Branch-free: every step is evaluated and a stopped walk keeps X.
+        // Branch-free: every lane evaluates every step (a lane without a walk
+        // computes values nobody reads) and a stopped walk keeps X.  The cap
+        // test runs per group: per step only within G steps of the cap.
         bool stop = false, capped = false;
-        if (active) {
+        {
             const WalkInst<Real> &I = inst(linst);
             uint32_t w[4];
             philox4x32_10(nstep / G, wlo, whi, I.stream_id, p.rk, w);
+            if (!active || nstep + uint32_t(G) <= I.step_cap) {
 #pragma unroll
-            for (int s = 0; s < G; ++s) {
-                Real r = walk_dist<Real, DIM, KIND>(I.g, X);
-                bool at_eps = r <= I.eps;
-                bool at_cap = nstep >= I.step_cap;
-                bool go = !stop && !at_eps && !at_cap;
-                capped = capped || (!stop && !at_eps && at_cap);
-                stop = stop || !go;
-                Real U[DIM];
-                direction<Real, DIM>(w + s * WPS, U);
-#pragma unroll
-                for (int a = 0; a < DIM; ++a) {
-                    Real su = Real(0);
-#pragma unroll
-                    for (int b = 0; b < DIM; ++b)
-                        su += I.S[a * DIM + b] * U[b];
-                    Real xn = X[a] + r * su;
-                    X[a] = go ? xn : X[a];
+                for (int s = 0; s < G; ++s) {
+                    const Real r = walk_dist<Real, DIM, KIND>(I.g, X);
+                    const bool go = !stop && !(r <= I.eps);
+                    stop = !go;
+                    Real U[DIM];
+                    direction<Real, DIM>(w + s * WPS, U);
+                    step_move<Real, DIM>(I.S, U, go ? r : Real(0), X);
+                    nstep += go ? 1u : 0u;
                 }
-                nstep += go ? 1u : 0u;
+            } else {
+#pragma unroll
+                for (int s = 0; s < G; ++s) {
+                    const Real r = walk_dist<Real, DIM, KIND>(I.g, X);
+                    const bool at_eps = r <= I.eps;
+                    const bool at_cap = nstep >= I.step_cap;
+                    const bool go = !stop && !at_eps && !at_cap;
+                    capped = capped || (!stop && !at_eps && at_cap);
+                    stop = stop || !go;
+                    Real U[DIM];
+                    direction<Real, DIM>(w + s * WPS, U);
+                    step_move<Real, DIM>(I.S, U, go ? r : Real(0), X);
+                    nstep += go ? 1u : 0u;
+                }
             }
         }
-        bool fin = active && stop;
-        need = !active || fin;
-        if (!__any_sync(FULL, fin))
+        const bool fin = active && stop;
+        const unsigned fin_mask = __ballot_sync(FULL, fin);
+        if (fin_mask == 0u)
             continue;
 
         // ---- queue the finished walks; tally 32 at a time (Eq. (WoE_matrix_MC))
-        {
-            bool cap_fin = fin && capped;
-            if (cap_fin) {
-                const WalkInst<Real> &I = inst(linst);
-                ++my_unterm;
-                if (I.unterm)
-                    atomicAdd(I.unterm + li, 1u);
-                if (!MULTI && p.trace_elem) {
-                    size_t q = size_t(li) * (I.k1 - I.k0) + (lk - I.k0);
-                    p.trace_elem[q] = -1;
-                    if (p.trace_steps) p.trace_steps[q] = nstep;
-                    if (p.trace_x) {
+        const unsigned cap_mask = __ballot_sync(FULL, fin && capped);
+        if (cap_mask != 0u && fin && capped) {  // walk left unterminated at the cap
+            const WalkInst<Real> &I = inst(linst);
+            ++my_unterm;
+            if (I.unterm)
+                atomicAdd(I.unterm + li, 1u);
+            if (!MULTI && p.trace_elem) {
+                size_t q = size_t(li) * (I.k1 - I.k0) + (lk - I.k0);
+                p.trace_elem[q] = -1;
+                if (p.trace_steps) p.trace_steps[q] = nstep;
+                if (p.trace_x) {
 #pragma unroll
-                        for (int a = 0; a < DIM; ++a)
-                            p.trace_x[q * DIM + a] = double(X[a]);
-                    }
+                    for (int a = 0; a < DIM; ++a)
+                        p.trace_x[q * DIM + a] = double(X[a]);
                 }
             }
-            bool push = fin && !capped;
-            unsigned pm = __ballot_sync(FULL, push);
-            if (push) {
-                int32_t e = qn + int32_t(__popc(pm & lt_mask));
+        }
+        const unsigned push_mask = fin_mask & ~cap_mask;
+        if ((push_mask >> lane) & 1u) {
+            const int32_t e = qn + int32_t(__popc(push_mask & lt_mask));
 #pragma unroll
-                for (int a = 0; a < DIM; ++a)
-                    qx[a * kQueue + e] = X[a];
-                qi[e] = uint32_t(li);
+            for (int a = 0; a < DIM; ++a)
+                qx[a * kQueue + e] = X[a];
+            qi[e] = uint32_t(li);
+            if (MULTI)
                 qinst[e] = uint32_t(linst);
+            qsg[e] = (lgen << 1) | uint32_t(lslot);
+            if (!MULTI && p.trace_elem) {
                 qk[e] = lk;
-                qsg[e] = (lgen << 1) | uint32_t(lslot);
                 qn_steps[e] = nstep;
             }
-            qn += int32_t(__popc(pm));
-            if (fin) {
-                my_steps += nstep;
-                ++my_walks;
-                my_max = nstep > my_max ? nstep : my_max;
-                active = false;
-            }
-            __syncwarp();
-            if (qn >= 32) {
-                drain(qn - 32, 32);
-                qn -= 32;
-            }
+        }
+        qn += int32_t(__popc(push_mask));
+        my_steps += fin ? nstep : 0u;
+        my_walks += fin ? 1u : 0u;
+        my_max = (fin && nstep > my_max) ? nstep : my_max;
+        active = active && !fin;
+        __syncwarp();
+        if (qn >= 32) {
+            drain(qn - 32, 32);
+            qn -= 32;
         }
     }
 
@@ -398,8 +430,8 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
     }
     if (lane == 0) {
         atomicAdd(p.work + 1, my_steps);
-        atomicAdd(p.work + 2, my_walks);
-        if (my_unterm) atomicAdd(p.work + 3, my_unterm);
+        atomicAdd(p.work + 2, (unsigned long long)my_walks);
+        if (my_unterm) atomicAdd(p.work + 3, (unsigned long long)my_unterm);
         atomicMax(p.work + 4, (unsigned long long)my_max);
     }
 }
