@@ -36,7 +36,13 @@
 
 namespace wos {
 
-enum KernelKind : int { kGeneric = 0, kSphereOnly = 1, kBoxOnly = 2, kSphereHoles = 3 };
+// Kernel kinds: any domain; a disc / ball; a box; a disc / ball with holes;
+// a disc / ball with one concentric hole (annulus, spherical shell: both
+// boundary distances come from one radius).
+enum KernelKind : int {
+    kGeneric = 0, kSphereOnly = 1, kBoxOnly = 2, kSphereHoles = 3, kAnnulus = 4
+};
+constexpr int kNumKinds = 5;
 
 // One instance of the operator build.
 template <typename Real> struct WalkInst {
@@ -92,6 +98,16 @@ __device__ __forceinline__ Real walk_dist(const Geom<Real> &g, const Real *x)
             r = w_min(r, hole_dist<Real, DIM>(g, h, x));
         return r;
     }
+    if (KIND == kAnnulus) {  // |x - c| once: the same values as the two distances
+        Real s = Real(0);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            Real d = x[a] - g.c[a];
+            s += d * d;
+        }
+        const Real rho = w_sqrt(s);
+        return w_min(g.R - rho, rho - g.hr[0]);
+    }
     return domain_dist<Real, DIM>(g, x);
 }
 
@@ -103,7 +119,7 @@ __device__ __forceinline__ int32_t walk_classify(const Geom<Real> &g, const Real
         return outer_sphere_cell<Real, DIM>(g, x);
     if (KIND == kBoxOnly)
         return outer_box_cell<Real, DIM>(g, x);
-    if (KIND == kSphereHoles)
+    if (KIND == kSphereHoles || KIND == kAnnulus)
         return sphere_holes_cell<Real, DIM>(g, x);
     return classify<Real, DIM>(g, x);
 }

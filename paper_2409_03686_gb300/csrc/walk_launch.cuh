@@ -36,15 +36,22 @@ const void *pick_walk_kernel(int kind)
     if (kind == kSphereOnly) return walk_kernel_ptr<Real, DIM, kSphereOnly, MULTI>();
     if (kind == kBoxOnly) return walk_kernel_ptr<Real, DIM, kBoxOnly, MULTI>();
     if (kind == kSphereHoles) return walk_kernel_ptr<Real, DIM, kSphereHoles, MULTI>();
+    if (kind == kAnnulus) return walk_kernel_ptr<Real, DIM, kAnnulus, MULTI>();
     return walk_kernel_ptr<Real, DIM, kGeneric, MULTI>();
 }
 
-// Kernel kind: specialised distance for a plain disc / ball, a box, or a
-// disc / ball with holes.
+// Kernel kind: specialised distance for a plain disc / ball, a box, a disc /
+// ball with holes, or a disc / ball with one hole of the same centre.
 inline int walk_kind(const wos_domain &d, const wos_partition &part)
 {
-    if (part.voronoi_n <= 0 && d.outer_kind == WOS_OUTER_SPHERE)
-        return d.n_holes == 0 ? kSphereOnly : kSphereHoles;
+    if (part.voronoi_n <= 0 && d.outer_kind == WOS_OUTER_SPHERE) {
+        if (d.n_holes == 0)
+            return kSphereOnly;
+        bool concentric = d.n_holes == 1;
+        for (int a = 0; a < d.dim; ++a)
+            concentric = concentric && d.hole_center[0][a] == d.center[a];
+        return concentric ? kAnnulus : kSphereHoles;
+    }
     if (part.voronoi_n <= 0 && d.n_holes == 0 && d.outer_kind == WOS_OUTER_BOX)
         return kBoxOnly;
     return kGeneric;

@@ -185,8 +185,8 @@ extern "C" wos_status wos_build_operators_batched(wos_context *ctx, int32_t n,
         o.trace_steps || o.trace_x)
         return WOS_INVALID_ARG;  // whole walk ranges only, no traces, in a batch
     std::vector<std::vector<double>> S(n, std::vector<double>(9, 0.0));
-    // classes: dimension x kernel kind (4 kinds), one launch each
-    std::vector<int> by_class[2][4];
+    // classes: dimension x kernel kind, one launch each
+    std::vector<int> by_class[2][kNumKinds];
     for (int q = 0; q < n; ++q) {
         const wos_problem &pb = problems[q];
         wos_status st = validate(pb.domain, pb.partition);
@@ -207,14 +207,14 @@ extern "C" wos_status wos_build_operators_batched(wos_context *ctx, int32_t n,
     }
     cudaSetDevice(ctx_device(ctx));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    unsigned long long w[8][5] = {};
+    unsigned long long w[2 * kNumKinds][5] = {};
     for (int dd = 0; dd < 2; ++dd) {
-        for (int kk = 0; kk < 4; ++kk) {
+        for (int kk = 0; kk < kNumKinds; ++kk) {
             const std::vector<int> &cls = by_class[dd][kk];
             if (cls.empty())
                 continue;
             wos_status st;
-            unsigned long long *wo = stats ? w[dd * 4 + kk] : nullptr;
+            unsigned long long *wo = stats ? w[dd * kNumKinds + kk] : nullptr;
             if (o.precision == WOS_FP64)
                 st = dd == 0 ? launch_class<double, 2>(ctx, cls, problems, S, seed, o, s, wo)
                              : launch_class<double, 3>(ctx, cls, problems, S, seed, o, s, wo);
@@ -229,7 +229,7 @@ extern "C" wos_status wos_build_operators_batched(wos_context *ctx, int32_t n,
         return WOS_OK;
     wos_status st = cuda_status(cudaStreamSynchronize(s));
     std::memset(stats, 0, sizeof(*stats));
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < 2 * kNumKinds; ++c) {
         stats->steps += w[c][1];
         stats->walks += w[c][2];
         stats->unterminated += w[c][3];
