@@ -16,7 +16,12 @@ the paper writes as matrix algebra:
   Sec. 4.3, Eq. (u_omega_M1_r_MC A); Rem. (b and u0 simulations)), optionally
   with the Tikhonov filter sigma / (sigma^2 + alpha) in place of 1 / sigma;
 * the fitted interior values u^D_hat = A_{Gamma_1} u_{Gamma_1} + A_{Gamma_0} u^0
-  (Sec. 5.2, item (iv)).
+  (Sec. 5.2, item (iv));
+* the spectral diagnostics of Sec. 5.2 items (i)-(iv): eigenvalues of
+  Lambda^nu (Eq. (Lambda_tilde_nu)), the eigenfunction estimators
+  (Eq. (eigenfunctions_MC)), the averaged density estimator (Eq. (rho omega1
+  MC) averaged over the poles) and the TSVD solutions and fitted interior
+  data for every truncation r.
 """
 from __future__ import annotations
 
@@ -361,3 +366,48 @@ def reconstruct(U, s, V, r, counts, N, gamma1, nu, measures, uD, u0=None,
     if u0 is not None and A0.shape[1] > 0:
         uhat = uhat + A0 @ np.asarray(u0, dtype=np.float64)
     return u1, uhat
+
+
+def spectral(U, s, V, counts, N, gamma1, nu, measures, uD=None, u0=None, r_max=0):
+    """Spectral diagnostics of one operator, from their definitions
+    (Sec. 5.2 items (i)-(iv)).
+
+    * lam: the eigenvalues of Lambda^nu = diag(nu) A_1 diag(sigma)^{-1} A_1^T
+      diag(nu) (Eq. (Lambda_tilde_nu)), descending, the first k = len(s);
+    * eigfun[l, j]: u~_j on Gamma_1 element l = lambda_j^{-1/2} sum_i nu_i
+      U[i, j] rho_i(l), with rho_i(l) = A_1[i, l] / sigma_l (Eq. (rho omega1
+      MC), (eigenfunctions_MC)) and lambda_j = s_j^2 (Prop. coro:B-Lambda);
+    * density[l] = (1 / M_D) sum_i rho_i(l), the averaged estimator the
+      paper maps in every example (Sec. 5.2);
+    * u_sweep[r - 1] = the r-TSVD solution on Gamma_1 (Eq. (tsvd solution
+      simulations)), r = 1..r_max;
+    * uD_sweep[r - 1] = A_1 u_sweep[r - 1] + A_0 u^0, the fitted interior data
+      of item (iv).
+    Returns a dict."""
+    g1 = np.asarray(gamma1).astype(bool)
+    A = np.asarray(counts, dtype=np.float64) / float(N)
+    A1, A0 = A[:, g1], A[:, ~g1]
+    sig1 = np.asarray(measures, float)[g1]
+    nu = np.asarray(nu, float)
+    k = len(s)
+    Lam = (nu[:, None] * A1 / sig1[None, :]) @ (A1.T * nu[None, :])
+    lam = np.sort(np.linalg.eigvalsh(Lam))[::-1][:k]
+    rho = A1 / sig1[None, :]
+    eigfun = (rho.T @ (nu[:, None] * U)) / s[None, :]
+    density = rho.mean(axis=0)
+    out = dict(lam=lam, eigfun=eigfun, density=density)
+    if r_max > 0:
+        b = np.asarray(uD, dtype=np.float64).copy()
+        f0 = np.zeros(A.shape[0])
+        if u0 is not None and A0.shape[1] > 0:
+            f0 = A0 @ np.asarray(u0, dtype=np.float64)
+        b = b - f0
+        us, ys = [], []
+        for r in range(1, r_max + 1):
+            w = V[:, :r] @ ((U[:, :r].T @ (nu * b)) / s[:r])
+            u1 = w / np.sqrt(sig1)
+            us.append(u1)
+            ys.append(A1 @ u1 + f0)
+        out["u_sweep"] = np.array(us)
+        out["uD_sweep"] = np.array(ys)
+    return out
