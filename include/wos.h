@@ -421,6 +421,32 @@ wos_status wos_reconstruct(wos_context *ctx, const double *U, const double *S,
                            const double *u0, int32_t r, double tikhonov_alpha,
                            double *u_gamma1, double *uD_hat, void *stream);
 
+/* Spectral diagnostics of one operator from its SVD (paper Sec. 5.2 items
+ * (i)-(iv); Eq. (Lambda_tilde_nu), (rho omega1 MC), (eigenfunctions_MC),
+ * (tsvd solution simulations)), FP64:
+ *   lambda[j]            = S_j^2, the eigenvalues of Lambda^nu (Prop.
+ *                          coro:B-Lambda), j < k;
+ *   eigfun[l * k + j]    = the eigenfunction estimator u~_j on Gamma_1
+ *                          element l: S_j^{-1} sum_i nu_i U_ij A_il / sigma_l;
+ *   density[l]           = (1 / M_D) sum_i A_il / sigma_l, the averaged
+ *                          estimator of the elliptic densities on Gamma_1;
+ *   u_sweep[(r-1) * M_1 + l]  = the r-TSVD solution on element l, r = 1..r_max
+ *                          (equal to wos_reconstruct at truncation r, bit for bit);
+ *   uD_sweep[(r-1) * M_D + i] = A_Gamma_1 u^(r) + A_Gamma_0 u0 at point i
+ *                          (the fitted interior data of item (iv)).
+ * Inputs as wos_reconstruct (U, S, V from wos_op_svd; counts, gamma1, nu,
+ * sigma, uD, u0).  Every output is a device buffer or NULL (not computed);
+ * u_sweep is required when uD_sweep is given; r_max in 0..k.
+ * Errors: WOS_INVALID_ARG, WOS_OOM, WOS_CUDA_ERROR. */
+wos_status wos_spectral(wos_context *ctx, const double *U, const double *S,
+                        const double *V, int32_t M_D, int32_t k,
+                        const uint32_t *counts, int32_t M_tot, uint32_t N,
+                        const uint8_t *gamma1, const double *nu,
+                        const double *sigma, const double *uD, const double *u0,
+                        int32_t r_max, double *lambda, double *eigfun,
+                        double *density, double *u_sweep, double *uD_sweep,
+                        void *stream);
+
 /* Truncation rule for degenerate spectra: returns WOS_OK when
  * S[r-1] / S[r] >= 1.5 (or r = k), else WOS_TRUNCATION_IN_CLUSTER.
  * S: host, k doubles. */

@@ -472,6 +472,43 @@ def perforated_disc_config(N: int = 1_000_000, eps: float = 1e-10,
                     seed=seed, fp64=fp64)
 
 
+def square_perimeter_points(half: float, n: int) -> np.ndarray:
+    """n points equally spaced along the perimeter of the square of
+    half-side `half` centred at the origin, counter-clockwise from
+    (-half, -half)."""
+    t = 8.0 * half * (np.arange(n) + 0.5) / n
+    out = np.zeros((n, 2))
+    for q, s in enumerate(t):
+        side, u = int(s // (2 * half)), s % (2 * half) - half
+        out[q] = [(u, -half), (half, u), (-u, half), (-half, -u)][side]
+    return out
+
+
+def square_hole_config(example: int = 1, N: int = 1_000_000, eps: float = 1e-7,
+                       m_edge: int = 100, m_hole: int = 50, n_points: int = 40,
+                       seed: int = 13, fp64: bool = True) -> Instance:
+    """Ex. 5.1 / 5.5: the square (-1, 1)^2 minus the disc of radius 0.2 at
+    (0.5, 0); m_edge cells per side (counter-clockwise from (-1, -1)) and
+    m_hole arcs.  Ex. 5.1: Gamma_0 = the square, Gamma_1 = the circle, points
+    on {dist(x, Gamma_0) = 0.05} (the square of half-side 0.95).  Ex. 5.5:
+    Gamma_0 empty, Gamma_1 = both boundaries, points on the circle of radius
+    0.3 about (-0.5, 0.5)."""
+    dom = Domain(dim=2, outer="box", half=(1.0, 1.0, 0.0),
+                 holes=(((0.5, 0.0, 0.0), 0.2),))
+    part = Partition(edge_m=(m_edge,) * 4, hole_m=(m_hole,), hole_theta0=(0.0,))
+    if example == 1:
+        part.gamma1 = np.concatenate([np.zeros(4 * m_edge, np.uint8),
+                                      np.ones(m_hole, np.uint8)])
+        pts = square_perimeter_points(0.95, n_points)
+    elif example == 5:
+        part.gamma1 = np.ones(4 * m_edge + m_hole, np.uint8)
+        pts = circle_points((-0.5, 0.5), 0.3, n_points)
+    else:
+        raise ValueError("Ex. 5.1 or 5.5")
+    return Instance(f"square-hole-ex{example}", dom, part, np.eye(2), pts, N=N, eps=eps,
+                    seed=seed, fp64=fp64)
+
+
 def shell_config(N: int = 100_000, eps: float = 1e-4, shift: float = 0.0,
                  nb: int = 16, ns: int = 24, n_points: int = 100, seed: int = 12,
                  K: np.ndarray | None = None) -> Instance:

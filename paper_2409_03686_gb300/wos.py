@@ -236,6 +236,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.wos_reconstruct.argtypes = [vp, vp, vp, vp, i32, i32, vp, i32, u32, vp, vp, vp, vp,
                                   vp, i32, dbl, vp, vp, vp]
     L.wos_truncation_gap.argtypes = [vp, i32, i32]
+    L.wos_spectral.argtypes = [vp, vp, vp, vp, i32, i32, vp, i32, u32, vp, vp, vp, vp, vp,
+                               i32, vp, vp, vp, vp, vp, vp]
     L.wos_queue_create.argtypes = [vp, vp, ctypes.POINTER(vp)]
     L.wos_queue_destroy.argtypes = [vp]
     L.wos_submit.argtypes = [vp, vp, ctypes.POINTER(u64)]
@@ -586,6 +588,36 @@ def wos_reconstruct(ctx: Context, U, S, V, counts, N: int, gamma1: np.ndarray, s
                              _stream(stream))
     _check(code, "wos_reconstruct", allow_warning=False)
     return u1, uhat
+
+
+def wos_spectral(ctx: Context, U, S, V, counts, N: int, gamma1: np.ndarray, sigma,
+                 uD=None, u0=None, nu=None, r_max: int = 0, want_eigfun: bool = True,
+                 stream=None) -> dict:
+    """Spectral diagnostics (Sec. 5.2 items (i)-(iv)): lambda (k), eigfun
+    (M_1 x k), density (M_1), and for r_max > 0 the TSVD family u_sweep
+    (r_max x M_1) with its fitted interior data uD_sweep (r_max x M_D)."""
+    import torch
+    L = load()
+    M_D, M_tot = int(counts.shape[0]), int(counts.shape[1])
+    g1 = np.ascontiguousarray(gamma1, dtype=np.uint8)
+    M_1 = int(g1.sum())
+    k = int(S.shape[0])
+    dev = counts.device
+    f64 = dict(dtype=torch.float64, device=dev)
+    out = dict(lambda_=torch.empty(k, **f64),
+               eigfun=torch.empty((M_1, k), **f64) if want_eigfun else None,
+               density=torch.empty(M_1, **f64))
+    if r_max > 0:
+        out["u_sweep"] = torch.empty((r_max, M_1), **f64)
+        out["uD_sweep"] = torch.empty((r_max, M_D), **f64)
+    code = L.wos_spectral(ctx.h, U.data_ptr(), S.data_ptr(), V.data_ptr(), M_D, k,
+                          counts.data_ptr(), M_tot, int(N), g1.ctypes.data, _ptr(nu),
+                          sigma.data_ptr(), _ptr(uD), _ptr(u0), int(r_max),
+                          out["lambda_"].data_ptr(), _ptr(out["eigfun"]),
+                          out["density"].data_ptr(), _ptr(out.get("u_sweep")),
+                          _ptr(out.get("uD_sweep")), _stream(stream))
+    _check(code, "wos_spectral", allow_warning=False)
+    return out
 
 
 def wos_truncation_gap(S: np.ndarray, r: int) -> bool:

@@ -60,6 +60,9 @@ GEOMS = {
     "ball_rand_K": lambda: W.config3_instances(N=500, n_points=40)[1],
     "cube": lambda: W.cube_config(N=500, n_points=40),
     "shell": lambda: W.shell_config(N=500, shift=0.3, n_points=40),
+    "shell_concentric": lambda: W.shell_config(N=500, shift=0.0, n_points=40),
+    "square_hole": lambda: W.square_hole_config(example=1, N=600, eps=1e-5, fp64=False),
+    "square_hole_ex5": lambda: W.square_hole_config(example=5, N=600, eps=1e-5, fp64=False),
     "ball64": lambda: W.ball_config(N=300, n_points=20).replace(fp64=True),
     "lshape64": lambda: W.lshape_config(N=300, n_points=20).replace(fp64=True, eps=1e-8),
 }

@@ -140,6 +140,10 @@ def test_exact_recovery_of_harmonic_polynomials_2d(fp64):
     sq = W.square_config(N=4000, grid=3, K=np.eye(2)).replace(fp64=fp64, eps=1e-4)
     for u in sols:
         _harmonic_check(sq, u, 4000)
+    # the CSG domain of Ex. 5.1 / 5.5 (square minus a disc)
+    sh = W.square_hole_config(example=5, N=4000, eps=1e-4, n_points=6, fp64=fp64)
+    for u in sols:
+        _harmonic_check(sh, u, 4000)
     # anisotropic: the cubic of Eq. (2D-sol4) for the paper's K and for the
     # benchmark K, on the annulus and the L-shape
     for K in (np.array([[1.0, 0.3], [0.3, 0.4]]), W.K_CONFIG2):

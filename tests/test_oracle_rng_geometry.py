@@ -192,6 +192,7 @@ GEOMS = {
     "ball": lambda: W.ball_config(nb=4, ns=6, n_points=4),
     "cube": lambda: W.cube_config(n_face=3, n_points=4),
     "shell": lambda: W.shell_config(nb=4, ns=6, shift=0.3),
+    "square_hole": lambda: W.square_hole_config(m_edge=6, m_hole=8),
 }
 
 
