@@ -282,7 +282,7 @@ def element_measures(dom, part) -> np.ndarray:
     """sigma(omega_j): arc length / edge-cell length / patch area of every
     element (surface measure of the cell, Eq. (boundary_weights))."""
     if part.voronoi_sites is not None:
-        raise NotImplementedError("Voronoi cell measures are supplied by the caller")
+        return voronoi_measures(dom, part)
     d = dom.dim
     out = []
     if dom.outer == "sphere":
@@ -317,6 +317,46 @@ def element_measures(dom, part) -> np.ndarray:
             n = part.hole_nb[h] * part.hole_ns[h]
             out.append(np.full(n, 4 * math.pi * r ** 2 / n))
     return np.concatenate(out)
+
+
+def voronoi_measures(dom, part) -> np.ndarray:
+    """sigma(omega_j) of extrinsic Voronoi cells (App. A, Ex. A.2) whose sites
+    lie on circles / spheres of the domain (outer boundary and holes), each
+    component's surface shared by its own sites only: the arc between the
+    angular bisectors of a site's neighbours (2-D) or the spherical Voronoi
+    cell area (3-D, scipy.spatial.SphericalVoronoi).  Sites on a box or
+    polygon are not supported."""
+    from scipy.spatial import SphericalVoronoi
+    sites = np.asarray(part.voronoi_sites, dtype=np.float64)
+    d = dom.dim
+    comps = []
+    if dom.outer == "sphere":
+        comps.append((np.asarray(dom.center[:d], float), dom.radius))
+    for c, r in dom.holes:
+        comps.append((np.asarray(c[:d], float), r))
+    if dom.outer != "sphere":
+        raise NotImplementedError("Voronoi measures on circles / spheres only")
+    out = np.zeros(len(sites))
+    owner = np.full(len(sites), -1)
+    for q, (c, r) in enumerate(comps):
+        on = np.abs(np.linalg.norm(sites - c, axis=1) - r) <= 1e-9 * max(r, 1.0)
+        owner[on & (owner < 0)] = q
+    if (owner < 0).any():
+        raise ValueError("a Voronoi site lies on no circle / sphere of the domain")
+    for q, (c, r) in enumerate(comps):
+        idx = np.flatnonzero(owner == q)
+        if d == 2:
+            ang = np.arctan2(sites[idx, 1] - c[1], sites[idx, 0] - c[0])
+            order = np.argsort(ang)
+            a = ang[order]
+            nxt = np.roll(a, -1) - a
+            nxt[-1] += 2 * math.pi
+            prv = np.roll(nxt, 1)
+            out[idx[order]] = r * 0.5 * (nxt + prv)
+        else:
+            sv = SphericalVoronoi(sites[idx], radius=r, center=c)
+            out[idx] = sv.calculate_areas()
+    return out
 
 
 def operator_B(counts, N, gamma1, nu, measures):

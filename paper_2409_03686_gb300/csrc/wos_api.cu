@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "wos.h"
+#include "voronoi_grid.h"
 #include "wos_internal.h"
 #include "walk_launch.cuh"
 
@@ -560,9 +561,13 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
     // walks) the points in walk precision, so that no walk converts FP64
     size_t site_bytes = part.voronoi_n > 0 ? size_t(part.voronoi_n) * dim * sizeof(Real) : 0;
     site_bytes = (site_bytes + 255) / 256 * 256;
+    VoronoiGrid vgrid;
+    const bool has_grid = part.voronoi_n > 0 && build_voronoi_grid(d, part, &vgrid);
+    const size_t gstart_bytes = has_grid ? (vgrid.start.size() * 4 + 255) / 256 * 256 : 0;
+    const size_t grid_bytes = has_grid ? gstart_bytes + (vgrid.cand.size() * 4 + 255) / 256 * 256 : 0;
     const bool convert = sizeof(Real) != sizeof(double);
     size_t pts_bytes = convert ? size_t(M_D) * dim * sizeof(Real) : 0;
-    size_t scratch_bytes = 256 + site_bytes + pts_bytes;
+    size_t scratch_bytes = 256 + site_bytes + grid_bytes + pts_bytes;
     void *scratch = nullptr;
     cudaError_t e = cudaMallocAsync(&scratch, scratch_bytes, stream);
     if (e != cudaSuccess) { delete pp; return cuda_status(e); }
@@ -576,9 +581,21 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
                         cudaMemcpyHostToDevice, stream);
         p.one.g.vsites = dsites;
     }
+    if (has_grid) {
+        char *gbase = static_cast<char *>(scratch) + 256 + site_bytes;
+        int32_t *dstart = reinterpret_cast<int32_t *>(gbase);
+        int32_t *dcand = reinterpret_cast<int32_t *>(gbase + gstart_bytes);
+        cudaMemcpyAsync(dstart, vgrid.start.data(), vgrid.start.size() * 4,
+                        cudaMemcpyHostToDevice, stream);
+        if (!vgrid.cand.empty())
+            cudaMemcpyAsync(dcand, vgrid.cand.data(), vgrid.cand.size() * 4,
+                            cudaMemcpyHostToDevice, stream);
+        set_voronoi_grid(vgrid, dstart, dcand, p.one.g);
+    }
     cudaMemsetAsync(scratch, 0, 64, stream);
     if (convert) {
-        Real *dpts = reinterpret_cast<Real *>(static_cast<char *>(scratch) + 256 + site_bytes);
+        Real *dpts = reinterpret_cast<Real *>(static_cast<char *>(scratch) + 256 + site_bytes +
+                                              grid_bytes);
         int n = M_D * dim;
         convert_points_kernel<Real><<<(n + 255) / 256, 256, 0, stream>>>(points, n, dpts);
         count_launches(ctx, 1);

@@ -16,6 +16,7 @@
 #include <new>
 #include <vector>
 
+#include "voronoi_grid.h"
 #include "walk_launch.cuh"
 #include "wos.h"
 #include "wos_internal.h"
@@ -66,14 +67,25 @@ wos_status launch_class(wos_context *ctx, const std::vector<int> &idx,
         return st;
 
     // host-side instance records and scratch layout:
-    // [work 64 B][instances][conversion jobs][sites][points in Real]
+    // [work 64 B][instances][conversion jobs][sites][Voronoi grids][points in Real]
     std::vector<WalkInst<Real>> recs(n);
     std::vector<ConvJob> jobs;
+    std::vector<VoronoiGrid> grids(n);
+    std::vector<char> has_grid(n, 0);
+    std::vector<int32_t> host_grid;  // every grid's offsets then candidates
+    std::vector<size_t> grid_at(n, 0);
     size_t sites_elems = 0, pts_elems = 0;
     for (int q = 0; q < n; ++q) {
         const wos_problem &pb = probs[idx[q]];
-        if (pb.partition->voronoi_n > 0)
+        if (pb.partition->voronoi_n > 0) {
             sites_elems += size_t(pb.partition->voronoi_n) * DIM;
+            if (build_voronoi_grid(*pb.domain, *pb.partition, &grids[q])) {
+                has_grid[q] = 1;
+                grid_at[q] = host_grid.size();
+                host_grid.insert(host_grid.end(), grids[q].start.begin(), grids[q].start.end());
+                host_grid.insert(host_grid.end(), grids[q].cand.begin(), grids[q].cand.end());
+            }
+        }
         pts_elems += size_t(pb.M_D) * DIM;
     }
     const bool convert = sizeof(Real) != sizeof(double);
@@ -81,7 +93,8 @@ wos_status launch_class(wos_context *ctx, const std::vector<int> &idx,
     const size_t off_inst = 256;
     const size_t off_jobs = off_inst + align(sizeof(WalkInst<Real>) * n);
     const size_t off_sites = off_jobs + align(sizeof(ConvJob) * n);
-    const size_t off_pts = off_sites + align(sites_elems * sizeof(Real));
+    const size_t off_grid = off_sites + align(sites_elems * sizeof(Real));
+    const size_t off_pts = off_grid + align(host_grid.size() * sizeof(int32_t));
     const size_t bytes = off_pts + (convert ? pts_elems * sizeof(Real) : 0);
     char *scratch = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), bytes, stream);
@@ -104,6 +117,11 @@ wos_status launch_class(wos_context *ctx, const std::vector<int> &idx,
                 host_sites[s_at + k] = Real(pb.partition->voronoi_sites[k]);
             I.g.vsites = dsites + s_at;
             s_at += ns;
+            if (has_grid[q]) {
+                const int32_t *dg = reinterpret_cast<const int32_t *>(scratch + off_grid) +
+                                    grid_at[q];
+                set_voronoi_grid(grids[q], dg, dg + grids[q].start.size(), I.g);
+            }
         }
         if (convert) {
             jobs.push_back(ConvJob{pb.points, p_at, pb.M_D * DIM});
@@ -127,6 +145,9 @@ wos_status launch_class(wos_context *ctx, const std::vector<int> &idx,
                     cudaMemcpyHostToDevice, stream);
     if (sites_elems)
         cudaMemcpyAsync(dsites, host_sites.data(), sites_elems * sizeof(Real),
+                        cudaMemcpyHostToDevice, stream);
+    if (!host_grid.empty())
+        cudaMemcpyAsync(scratch + off_grid, host_grid.data(), host_grid.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice, stream);
     if (convert) {
         cudaMemcpyAsync(scratch + off_jobs, jobs.data(), sizeof(ConvJob) * jobs.size(),

@@ -76,6 +76,14 @@ template <typename Real> struct Geom {
     int32_t M_tot;
     int32_t vn;              // extrinsic Voronoi sites (0 = cells below)
     const Real *vsites;      // device, vn x dim
+    // candidate grid of the sites (null vcell = scan every site): cell
+    // (ix, iy, iz) = ((iz g1 + iy) g0 + ix) keeps sites vcand[vcell[c] ..
+    // vcell[c + 1]) in ascending order
+    const int32_t *vcell;
+    const int32_t *vcand;
+    int32_t vg[3];
+    Real vlo[3];
+    Real vinv_h;
     Real c[3];               // sphere / box centre
     Real R;                  // sphere radius
     Real h[3];               // box half-extents
@@ -343,9 +351,28 @@ template <typename Real, int DIM>
 WOS_HD int32_t classify(const Geom<Real> &g, const Real *x)
 {
     if (g.vn > 0) {
+        int32_t lo = 0, hi = g.vn;
+        const int32_t *cand = nullptr;
+        if (g.vcell) {  // candidate list of the grid cell of x, if x is inside the grid
+            int32_t c = 0;
+            bool inside = true;
+#pragma unroll
+            for (int a = DIM - 1; a >= 0; --a) {
+                const Real t = (x[a] - g.vlo[a]) * g.vinv_h;
+                const int32_t q = int32_t(floor(t));
+                inside = inside && t >= Real(0) && q < g.vg[a];
+                c = c * g.vg[a] + q;
+            }
+            if (inside) {
+                lo = g.vcell[c];
+                hi = g.vcell[c + 1];
+                cand = g.vcand;
+            }
+        }
         Real best = Real(INFINITY);
         int32_t bj = 0;
-        for (int32_t j = 0; j < g.vn; ++j) {
+        for (int32_t q = lo; q < hi; ++q) {
+            const int32_t j = cand ? cand[q] : q;
             Real s = Real(0);
 #pragma unroll
             for (int a = 0; a < DIM; ++a) {

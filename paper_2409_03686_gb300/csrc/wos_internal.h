@@ -25,4 +25,18 @@ void fill_geom(const wos_domain &d, const wos_partition &p, Geom<Real> &g);
 wos_status setup_S(int d, const double *K, double *S);
 double fp32_floor(const wos_domain &d);
 
+// Points the geometry at a Voronoi candidate grid already on the device.
+template <typename Real, typename Grid>
+void set_voronoi_grid(const Grid &G, const int32_t *dstart, const int32_t *dcand,
+                      Geom<Real> &g)
+{
+    g.vcell = dstart;
+    g.vcand = dcand;
+    for (int a = 0; a < 3; ++a) {
+        g.vg[a] = G.g[a];
+        g.vlo[a] = Real(G.lo[a]);
+    }
+    g.vinv_h = Real(1.0 / G.h);
+}
+
 }  // namespace wos

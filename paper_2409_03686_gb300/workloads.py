@@ -511,17 +511,43 @@ def square_hole_config(example: int = 1, N: int = 1_000_000, eps: float = 1e-7,
 
 def shell_config(N: int = 100_000, eps: float = 1e-4, shift: float = 0.0,
                  nb: int = 16, ns: int = 24, n_points: int = 100, seed: int = 12,
-                 K: np.ndarray | None = None) -> Instance:
+                 K: np.ndarray | None = None, voronoi: tuple | None = None,
+                 fp64: bool = False) -> Instance:
     """Ex. 5.6 / 5.7: unit ball minus the ball of radius 0.5 centred at
     (shift, 0, 0); Gamma_1 = inner sphere; points on the Bauer spiral of the
-    sphere at distance 0.05 from Gamma_0."""
+    sphere at distance 0.05 from Gamma_0.  Elements: nb x ns bands x sectors
+    on each sphere, or with voronoi = (M_0, M_1) the paper's extrinsic
+    Voronoi cells of M_0 Bauer-spiral sites on the outer sphere and M_1 on the
+    inner one (Sec. 5.3; Ex. 5.6 / 5.7 use (1000, 100))."""
     dom = Domain(dim=3, outer="sphere", radius=1.0,
                  holes=(((shift, 0.0, 0.0), 0.5),))
-    g1 = np.concatenate([np.zeros(nb * ns, np.uint8), np.ones(nb * ns, np.uint8)])
-    part = Partition(outer_nb=nb, outer_ns=ns, hole_nb=(nb,), hole_ns=(ns,),
-                     gamma1=g1)
-    return Instance("shell", dom, part, np.eye(3) if K is None else K,
-                    bauer_spiral(n_points, 0.95), N=N, eps=eps, seed=seed)
+    if voronoi is None:
+        g1 = np.concatenate([np.zeros(nb * ns, np.uint8), np.ones(nb * ns, np.uint8)])
+        part = Partition(outer_nb=nb, outer_ns=ns, hole_nb=(nb,), hole_ns=(ns,),
+                         gamma1=g1)
+    else:
+        m0, m1 = voronoi
+        sites = np.concatenate([bauer_spiral(m0, 1.0), bauer_spiral(m1, 0.5, (shift, 0, 0))])
+        part = Partition(voronoi_sites=sites,
+                         gamma1=np.concatenate([np.zeros(m0, np.uint8), np.ones(m1, np.uint8)]))
+    return Instance("shell" if voronoi is None else "shell-voronoi", dom, part,
+                    np.eye(3) if K is None else K, bauer_spiral(n_points, 0.95), N=N,
+                    eps=eps, seed=seed, fp64=fp64)
+
+
+def annulus_voronoi_config(N: int = 1_000_000, eps: float = 1e-10, m0: int = 500,
+                           m1: int = 100, n_points: int = 100, r_in: float = 0.5,
+                           seed: int = 14, fp64: bool = True) -> Instance:
+    """Ex. 5.2 / 5.3 with the paper's element choice: the annulus
+    r in [r_in, 1], extrinsic Voronoi cells of m0 equally spaced points on the
+    outer circle (Gamma_0) and m1 on the inner circle (Gamma_1); points on the
+    circle at distance 0.05 from Gamma_0."""
+    dom = Domain(dim=2, outer="sphere", radius=1.0, holes=(((0.0, 0.0, 0.0), r_in),))
+    sites = np.concatenate([circle_points((0, 0), 1.0, m0), circle_points((0, 0), r_in, m1)])
+    part = Partition(voronoi_sites=sites,
+                     gamma1=np.concatenate([np.zeros(m0, np.uint8), np.ones(m1, np.uint8)]))
+    return Instance("annulus-voronoi", dom, part, np.eye(2), circle_points((0, 0), 0.95, n_points),
+                    N=N, eps=eps, seed=seed, fp64=fp64)
 
 
 def mixed_batch(n_instances: int = 64, seed: int = 7, m_lo: int = 64,

@@ -71,3 +71,20 @@ def test_autotune_picks_a_config_without_changing_results():
     np.testing.assert_array_equal(tuned["counts"], ref)
     assert tuned["stats"]["block"] == t["block_size"]
     wos.wos_autotune_reset(ctx())
+
+
+def test_batch_with_voronoi_instances_equals_lone_builds():
+    """Extrinsic-Voronoi instances (candidate grids in the batch scratch) next
+    to cell-partition ones: every instance's counts equal its lone build."""
+    insts = [W.shell_config(N=400, shift=0.3, n_points=24, voronoi=(300, 60)).replace(stream=1),
+             W.annulus_voronoi_config(N=500, eps=1e-5, fp64=False, n_points=24, m0=200,
+                                      m1=60).replace(stream=2),
+             W.disc_config(N=500, fp64=False).replace(stream=3),
+             W.ball_config(N=300, n_points=24).replace(stream=4)]
+    insts = [i.replace(seed=7) for i in insts]
+    counts, unterm, st = wos.wos_build_operators_batched(ctx(), insts, seed=7)
+    torch.cuda.synchronize()
+    for q, inst in enumerate(insts):
+        lone = gpu_build(inst, trace=False)
+        np.testing.assert_array_equal(counts[q].cpu().numpy().astype(np.int64),
+                                      lone["counts"], err_msg=inst.name)

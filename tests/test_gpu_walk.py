@@ -63,6 +63,11 @@ GEOMS = {
     "shell_concentric": lambda: W.shell_config(N=500, shift=0.0, n_points=40),
     "square_hole": lambda: W.square_hole_config(example=1, N=600, eps=1e-5, fp64=False),
     "square_hole_ex5": lambda: W.square_hole_config(example=5, N=600, eps=1e-5, fp64=False),
+    "shell_voronoi": lambda: W.shell_config(N=500, shift=0.3, n_points=40, voronoi=(300, 60)),
+    "shell_voronoi64": lambda: W.shell_config(N=300, shift=0.3, n_points=20, voronoi=(300, 60),
+                                              fp64=True, eps=1e-8),
+    "annulus_voronoi": lambda: W.annulus_voronoi_config(N=600, eps=1e-5, fp64=False,
+                                                        n_points=40, m0=200, m1=60),
     "ball64": lambda: W.ball_config(N=300, n_points=20).replace(fp64=True),
     "lshape64": lambda: W.lshape_config(N=300, n_points=20).replace(fp64=True, eps=1e-8),
 }

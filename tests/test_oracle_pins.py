@@ -345,3 +345,29 @@ def test_row_sums_and_step_cap():
     np.testing.assert_array_equal(C1 + C2, C)
     np.testing.assert_array_equal(U1 + U2, U)
     assert s1 + s2 == steps
+
+
+def test_voronoi_cell_measures():
+    """Extrinsic Voronoi cell measures (App. A, Ex. A.2): equally spaced sites
+    on a circle own equal arcs 2 pi r / m; Bauer-spiral sites on a sphere own
+    spherical cells whose areas match a Monte Carlo estimate (uniform points
+    on the sphere assigned to their nearest site) within a binomial band."""
+    a = W.annulus_voronoi_config(m0=40, m1=12)
+    m = O.element_measures(a.domain, a.partition)
+    np.testing.assert_allclose(m[:40], 2 * np.pi / 40, rtol=1e-12)
+    np.testing.assert_allclose(m[40:], 2 * np.pi * 0.5 / 12, rtol=1e-12)
+    sh = W.shell_config(voronoi=(60, 20), shift=0.3)
+    m = O.element_measures(sh.domain, sh.partition)
+    sites = sh.partition.voronoi_sites
+    rng = np.random.default_rng(9)
+    n = 400_000
+    u = rng.standard_normal((n, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    for lo, hi, c, r in ((0, 60, np.zeros(3), 1.0), (60, 80, np.array([0.3, 0, 0]), 0.5)):
+        x = c + r * u
+        near = np.argmin(((x[:, None, :] - sites[None, lo:hi, :]) ** 2).sum(-1), axis=1)
+        frac = np.bincount(near, minlength=hi - lo) / n
+        p = m[lo:hi] / (4 * np.pi * r * r)
+        sd = np.sqrt(p * (1 - p) / n)
+        assert np.all(np.abs(frac - p) <= 5 * sd), np.max(np.abs(frac - p) / sd)
+        assert abs(p.sum() - 1) < 1e-12
