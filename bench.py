@@ -39,6 +39,10 @@ ALU_PEAK_GOPS = 152 * 4 * 32 * 2.070
 # Philox4x32-10 share 80/4 = 20, uniform 3, sin/cos 4, move 6, eps and cap
 # tests 3, step counter 1, plus the distance: box 5, disc-minus-disc 9.
 OPS_PER_STEP = {"box": 42, "annulus": 46}
+# FP64 peak of one GB300: 152 SMs x 2 FP64 FMA per clock (ncu:
+# sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 per
+# chip) x 2 flop x 2070 MHz, in GFLOP/s.
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
 PROFILE_NOTE = ROOT / "profiles" / "walk_kernel_square_annulus.md"
 
 
@@ -250,10 +254,13 @@ def run_gpu(args, rank: int, world: int, dist):
                                           opts=wos.make_opts(stream_id=inst.stream))
         U, S, V, sw = wos.wos_op_svd(ctx, c, inst.N, inst.partition.gamma1, p["sigma"])
         p["r"] = pick_rank(S.cpu().numpy())
+        p["sweeps"] = sw
+        M_1 = int(inst.partition.gamma1.sum())
+        p["svd_mn"] = (max(inst.M_D, M_1), min(inst.M_D, M_1))
         p["steps"] = st["steps"]
         p["kind"] = "box" if inst.domain.outer == "box" else "annulus"
         steps_per_inst.append(st["steps"])
-    def step(timing=None, host_io=False, start_ev=None):
+    def step(timing=None, host_io=False, start_ev=None, svd_timing=None):
         """One step: the operator builds back to back on one stream (a
         persistent walk launch fills the GPU), then every instance's SVD and
         reconstruction on its own stream (the latency-bound SVDs overlap),
@@ -292,8 +299,12 @@ def run_gpu(args, rank: int, world: int, dist):
                 t.record_stream(s)
             with torch.cuda.stream(s):
                 g1 = inst.partition.gamma1
+                if svd_timing is not None:
+                    svd_timing[q][0].record(s)
                 U, S, V, _ = wos.wos_op_svd(ctx, c, inst.N, g1, p["sigma"], sync=False,
                                             stream=s)
+                if svd_timing is not None:
+                    svd_timing[q][1].record(s)
                 u1, _ = wos.wos_reconstruct(ctx, U, S, V, c, inst.N, g1, p["sigma"], uD,
                                             p["r"], u0=u0, stream=s)
                 if host_io:
@@ -321,6 +332,8 @@ def run_gpu(args, rank: int, world: int, dist):
         for pair in row:
             for e in pair:
                 e.record(stream)
+    sev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in prep] for _ in range(args.steps)]
     clocks = ClockSampler(local)
     if dist is not None:
         dist.barrier()
@@ -331,7 +344,7 @@ def run_gpu(args, rank: int, world: int, dist):
     for it in range(args.steps):
         flush.zero_()
         starts[it].record(stream)
-        step(timing=kev[it], start_ev=starts[it])
+        step(timing=kev[it], start_ev=starts[it], svd_timing=sev[it])
         ends[it].record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t_wall
@@ -372,6 +385,36 @@ def run_gpu(args, rank: int, world: int, dist):
     kernel_ms_step = float(np.mean(unions))
     achieved = ops / (kernel_ms_step / 1e3) / 1e9
     traffic = _traffic_from_profile()
+    walk_roof = {"kernel": "walk_kernel", "bound": "alu", "achieved": achieved,
+                 "peak": ALU_PEAK_GOPS, "unit": "Gop/s", "frac": achieved / ALU_PEAK_GOPS,
+                 "traffic": traffic,
+                 "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz "
+                                "(recipe unit counts and max clock)",
+                 "unit_of_work": "one step of the chain: 42 (box) / 46 (annulus) "
+                                 "algorithmic lane-operations"}
+    # the SVD calls (form_B + Jacobi + norms + finalize; the Jacobi kernel is
+    # > 99 % of them): FP64 roofline with every pair visit counted as rotated
+    # (dots 6m + column updates 6m + 6n flop), an upper bound on the work
+    svd_ms = [[a.elapsed_time(b) for (a, b) in row] for row in sev]
+    svd_ms_sum = float(np.mean([sum(r) for r in svd_ms]))
+    walk_ms_sum = float(np.mean([sum(a.elapsed_time(b) for (a, b) in row) for row in kev]))
+    flop = sum(p["sweeps"] * (p["svd_mn"][1] * (p["svd_mn"][1] - 1) // 2)
+               * (12 * p["svd_mn"][0] + 6 * p["svd_mn"][1]) for p in prep)
+    svd_achieved = flop / (svd_ms_sum / 1e3) / 1e9
+    svd_roof = {"kernel": "jacobi_kernel", "bound": "fp64", "achieved": svd_achieved,
+                "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": svd_achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                "peak_source": "152 SMs x 2 FP64 FMA/clk (ncu dfma peak_sustained 304 "
+                               "per chip) x 2 flop x 2070 MHz",
+                "unit_of_work": "one pair visit of a sweep: 12m + 6n flop (m x n worked "
+                                "matrix; upper bound: every visit counted as rotated)",
+                "sweeps": [p["sweeps"] for p in prep],
+                "ms_per_call": svd_ms_sum / len(prep)}
+    # the kernel with the larger summed device time per step is the dominant one
+    if svd_ms_sum > walk_ms_sum:
+        roof, roof2 = svd_roof, walk_roof
+    else:
+        roof, roof2 = walk_roof, svd_roof
 
     # ---- e2e: public API with host buffers and copies in the timed region ---
     e2e_s = torch.cuda.Event(enable_timing=True)
@@ -403,11 +446,9 @@ def run_gpu(args, rank: int, world: int, dist):
         "steps_per_walk": steps_per_step / walks_per_step,
         "walk_kernel_ms_per_step": kernel_ms_step,
         "truncation_r": [p["r"] for p in prep],
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_GOPS,
-                     "unit": "Gop/s", "frac": achieved / ALU_PEAK_GOPS,
-                     "traffic": traffic,
-                     "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz "
-                                    "(recipe unit counts and max clock)"},
+        "roofline": roof,
+        "roofline_secondary": roof2,
+        "device_ms_per_step": {"walk_kernels": walk_ms_sum, "svd_calls": svd_ms_sum},
         "gpu_launches": int(launches),
         "wall_s_timed": wall,
         "e2e": {"value": e2e_value, "unit": "walks/s", "h2d_bytes_per_step": int(h2d),
