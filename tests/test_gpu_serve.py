@@ -181,3 +181,21 @@ def test_invalid_requests_rejected_at_submit():
         wos.wos_queue_destroy(q)
     with pytest.raises(wos.WosError):
         wos.wos_queue_create(ctx(), seed=SEED, precision=5)
+
+
+def test_preconditioned_svd_requests_equal_lone_solves():
+    """Requests large enough for the QR-preconditioned SVD (n >= 32)."""
+    insts = [W.annulus_config(N=3000, grid=7, m_each=48).replace(stream=1, seed=SEED),
+             W.square_config(N=3000, grid=7, n_side=16).replace(stream=2, seed=SEED),
+             W.ball_config(N=2000, n_points=64, nb=8, ns=12).replace(stream=3, seed=SEED)]
+    meas = [W.measurements(inst, noise=0.01, seed=q) for q, inst in enumerate(insts)]
+    q = wos.wos_queue_create(ctx(), seed=SEED, slice_walks=800)
+    try:
+        tickets = [wos.wos_submit(q, inst, m.uD, m.u0, want_counts=True)
+                   for inst, m in zip(insts, meas)]
+        for t in tickets:
+            assert wos.wos_wait(q, t, 120_000)
+    finally:
+        wos.wos_queue_destroy(q)
+    for inst, m, t in zip(insts, meas, tickets):
+        _check(t, _alone(inst, m), inst.name)

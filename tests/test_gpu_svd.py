@@ -104,3 +104,50 @@ def test_reconstruction_matches_oracle():
     ro, _ = O.reconstruct(Uo, so, Vo, len(so), C, inst.N, g1, nu, sigma, meas.uD, meas.u0,
                           tikhonov=1e-6)
     assert np.linalg.norm(u1.cpu().numpy() - ro) <= 1e-8 * np.linalg.norm(ro)
+
+
+@pytest.mark.parametrize("transposed", [False, True])
+def test_rank_deficient_operator(transposed):
+    """Zero Gamma_1 columns and repeated rows (rank deficiency) on the
+    preconditioned path (n >= 32): singular values as the oracle's, B
+    reproduced, singular vectors of the non-zero singular values
+    orthonormal."""
+    M_D, M_1 = (64, 48) if not transposed else (48, 64)
+    M_tot = M_1 + 16
+    N = 50_000
+    C = W.synthetic_counts(M_D, M_tot, N, seed=5)
+    g1 = np.zeros(M_tot, np.uint8)
+    g1[:M_1] = 1
+    C[:, [3, 7, 20]] = 0               # elements no walk reached
+    C[10] = C[11] = C[12]              # repeated rows
+    sigma = np.full(M_tot, 2 * np.pi / M_tot)
+    nu = np.full(M_D, 1 / np.sqrt(M_D))
+    (U, s, V, sweeps), (Uo, so, Vo), _ = _svd_pair(C, N, g1, sigma, nu)
+    _check_sv(s, so)
+    B = O.operator_B(C, N, g1, nu, sigma)
+    np.testing.assert_allclose(U @ np.diag(s) @ V.T, B, atol=1e-13 * so[0])
+    nz = s > 1e-12 * s[0]
+    np.testing.assert_allclose(U[:, nz].T @ U[:, nz], np.eye(nz.sum()), atol=1e-12)
+    np.testing.assert_allclose(V[:, nz].T @ V[:, nz], np.eye(nz.sum()), atol=1e-12)
+
+
+@pytest.mark.parametrize("shape", [(256, 256, 128), (300, 1536, 768)])
+def test_svd_is_deterministic(shape):
+    """Repeated SVDs of the same counts are bit-identical (the preconditioned
+    path's cooperative QR and the Jacobi dataflow take the same decisions
+    whatever the CTA timing)."""
+    M_D, M_tot, M_1 = shape
+    C = W.synthetic_counts(M_D, M_tot, 100_000, seed=M_D + 1)
+    g1 = np.zeros(M_tot, np.uint8)
+    g1[:M_1] = 1
+    Ct = torch.as_tensor(C.astype(np.int32), device=DEV)
+    sg = torch.full((M_tot,), 2 * np.pi / M_tot, dtype=torch.float64, device=DEV)
+    ref = wos.wos_op_svd(ctx(), Ct, 100_000, g1, sg)
+    side = torch.cuda.Stream()
+    for rep in range(4):
+        with torch.cuda.stream(side):  # another stream and a busy GPU
+            busy = torch.randn(4096, 4096, device=DEV) @ torch.randn(4096, 4096, device=DEV)
+        got = wos.wos_op_svd(ctx(), Ct, 100_000, g1, sg)
+        torch.cuda.synchronize()
+        for a, b in zip(ref[:3], got[:3]):
+            assert torch.equal(a, b), rep
