@@ -399,6 +399,27 @@ wos_status wos_op_svd(wos_context *ctx, const uint32_t *counts, int32_t M_D,
                       const double *nu, const double *sigma, double *U,
                       double *S, double *V, int32_t *sweeps, void *stream);
 
+/* Many SVDs of wos_op_svd in one pass (one cooperative QR launch and one
+ * Jacobi launch per class of problem size, their CTAs split among the
+ * problems, each synchronising only its own CTAs): independent operators of
+ * a benchmark step or of the serving queue share the GPU instead of queueing
+ * one latency-bound launch after another.  Every field as the argument of
+ * the same name of wos_op_svd (counts, nu, sigma, U, S, V on the device;
+ * gamma1 on the host).  Results equal wos_op_svd's for each problem, bit for
+ * bit.  sweeps: host, n entries, or NULL (as wos_op_svd). */
+typedef struct {
+    const uint32_t *counts;
+    int32_t M_D, M_tot;
+    uint32_t N;
+    const uint8_t *gamma1;
+    const double *nu, *sigma;
+    double *U, *S, *V;
+} wos_svd_problem;
+
+wos_status wos_op_svd_batched(wos_context *ctx, int32_t n,
+                              const wos_svd_problem *problems, int32_t *sweeps,
+                              void *stream);
+
 /* r-TSVD reconstruction (paper Sec. 2, Eq. (u1r); Sec. 4.3, Eq.
  * (u_omega_M1_r_MC A); Sec. 5.1, Rem. (b and u0 simulations), Eq. (tsvd
  * solution simulations)):

@@ -298,6 +298,7 @@ void worker_main(wos_queue *q)
                 ++q->stats.slices;
                 q->stats.walks += walks;
             }
+            std::vector<std::shared_ptr<Req>> fin;
             for (size_t i = 0; i < walking.size(); ++i) {
                 auto &R = walking[i];
                 if (st != WOS_OK) {
@@ -306,21 +307,32 @@ void worker_main(wos_queue *q)
                     continue;
                 }
                 R->k_done = probs[i].k1;
-                if (R->k_done < R->N)
-                    continue;
-                // walks done: SVD on a side stream after this slice
-                R->side = next_side++ % int(q->side.size());
-                cudaStream_t s = q->side[R->side];
+                if (R->k_done >= R->N)
+                    fin.push_back(R);
+            }
+            if (!fin.empty()) {
+                // walks done: their SVDs in one batched pass on a side
+                // stream after this slice
+                const int side = next_side++ % int(q->side.size());
+                cudaStream_t s = q->side[side];
                 cudaStreamWaitEvent(s, ev, 0);
-                wos_status s2 = wos_op_svd(q->ctx, R->d_counts, R->M_D, R->M_tot, R->N,
-                                           R->gamma1.data(), R->nu_ptr(), R->d_sigma, R->d_U,
-                                           R->d_S, R->d_V, nullptr, s);
-                cudaMemcpyAsync(R->h_S, R->d_S, size_t(R->k) * 8, cudaMemcpyDeviceToHost, s);
-                cudaEventRecord(R->ev, s);
-                R->state = kSvd;
-                if (s2 != WOS_OK) {
-                    release(q, *R);
-                    finish(q, R, s2);
+                std::vector<wos_svd_problem> sp(fin.size());
+                for (size_t i = 0; i < fin.size(); ++i) {
+                    Req &R = *fin[i];
+                    sp[i] = wos_svd_problem{R.d_counts, R.M_D, R.M_tot, R.N, R.gamma1.data(),
+                                            R.nu_ptr(), R.d_sigma, R.d_U, R.d_S, R.d_V};
+                }
+                wos_status s2 = wos_op_svd_batched(q->ctx, int32_t(sp.size()), sp.data(),
+                                                   nullptr, s);
+                for (auto &R : fin) {
+                    R->side = side;
+                    cudaMemcpyAsync(R->h_S, R->d_S, size_t(R->k) * 8, cudaMemcpyDeviceToHost, s);
+                    cudaEventRecord(R->ev, s);
+                    R->state = kSvd;
+                    if (s2 != WOS_OK) {
+                        release(q, *R);
+                        finish(q, R, s2);
+                    }
                 }
             }
             did = true;

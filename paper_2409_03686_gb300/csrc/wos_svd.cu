@@ -175,8 +175,7 @@ __device__ __forceinline__ void jacobi_rotation(double al, double be, double ga,
 // are read and written through L2 (ld.cg / st.cg): other SMs update them
 // between rounds; one fence orders a pair's stores before its two flags.
 template <int RPT>
-__global__ void __launch_bounds__(kPairThreads)
-jacobi_kernel(SvdWork w)
+__device__ void jacobi_body(const SvdWork &w, const int bid, const int nblk)
 {
     __shared__ double part[3][kPairThreads / 32];
     __shared__ double cs[2];
@@ -187,11 +186,11 @@ jacobi_kernel(SvdWork w)
     unsigned *status = w.bar + 5;
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
         unsigned *rot = w.bar + 2 + (sweep % 3);
-        if (blockIdx.x == 0 && tid == 0)
+        if (bid == 0 && tid == 0)
             w.bar[2 + ((sweep + 1) % 3)] = 0u;
         for (int r = 0; r < w.n_pad - 1; ++r) {
             const unsigned R = unsigned(sweep) * unsigned(w.n_pad - 1) + unsigned(r);
-            for (int pr = blockIdx.x; pr < half; pr += gridDim.x) {
+            for (int pr = bid; pr < half; pr += nblk) {
                 int a = rr_player(pr, r, w.n_pad);
                 int b = rr_player(w.n_pad - 1 - pr, r, w.n_pad);
                 int p = min(a, b), q = max(a, b);
@@ -293,27 +292,41 @@ jacobi_kernel(SvdWork w)
                 }
             }
         }
-        if (!grid_barrier(w.bar, gridDim.x))
+        if (!grid_barrier(w.bar, unsigned(nblk)))
             return;
         bool done = *(volatile unsigned *)rot == 0u;
-        if (blockIdx.x == 0 && tid == 0)
+        if (bid == 0 && tid == 0)
             w.bar[6] = unsigned(sweep + 1);
         if (done)
             return;
     }
-    if (blockIdx.x == 0 && tid == 0)
+    if (bid == 0 && tid == 0)
         atomicExch(w.bar + 5, unsigned(WOS_NO_CONVERGENCE));
 }
 
-// Kernel instance by rows per thread kept in registers: the fewest that hold
-// a column (up to 8; longer columns stream the rest).
-const void *jacobi_kernel_for(int m)
+// The CTAs of a launch are split among np problems: problem p owns CTAs
+// [begin[p], begin[p + 1]) and synchronises only among them (its own
+// flags and barrier words).
+__device__ __forceinline__ int problem_of(const int *begin, int np)
 {
-    if (m <= kPairThreads) return reinterpret_cast<const void *>(&jacobi_kernel<1>);
-    if (m <= 2 * kPairThreads) return reinterpret_cast<const void *>(&jacobi_kernel<2>);
-    if (m <= 4 * kPairThreads) return reinterpret_cast<const void *>(&jacobi_kernel<4>);
-    return reinterpret_cast<const void *>(&jacobi_kernel<8>);
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {  // last p with begin[p] <= blockIdx.x
+        const int mid = (lo + hi + 1) >> 1;
+        if (begin[mid] <= int(blockIdx.x)) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
+
+template <int RPT>
+__global__ void __launch_bounds__(kPairThreads)
+jacobi_kernel(const SvdWork *works, const int *begin, int np)
+{
+    const int p = problem_of(begin, np);
+    const SvdWork w = works[p];
+    jacobi_body<RPT>(w, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
+}
+
 
 // B (worked orientation): W[:, col] with col over Gamma_1 elements (or
 // over points when transposed); V_w = I.
@@ -463,11 +476,11 @@ __device__ int block_argmax(double v, int i, double *red, int *ired)
 // CTA applies it to its remaining columns and downdates their norms,
 // recomputing one exactly when cancellation has eaten half its digits
 // (xLAQP2's test).  Barriers are bounded (WOS_DEVICE_TIMEOUT).
-__global__ void __launch_bounds__(kQrThreads) qrcp_kernel(QrWork q)
+__device__ void qrcp_body(const QrWork &q, const int b, const int G)
 {
     __shared__ double red[32];
     __shared__ int ired[32];
-    const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+    const int tid = threadIdx.x;
     const int m = q.m, n = q.n;
     for (int c = b; c < n; c += G) {
         const double *col = q.A + size_t(c) * m;
@@ -593,6 +606,14 @@ __global__ void __launch_bounds__(kQrThreads) qrcp_kernel(QrWork q)
     }
 }
 
+__global__ void __launch_bounds__(kQrThreads)
+qrcp_kernel(const QrWork *works, const int *begin, int np)
+{
+    const int p = problem_of(begin, np);
+    const QrWork q = works[p];
+    qrcp_body(q, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
+}
+
 // X = R^T (n x n column-major): column i of X = row i of R, R[i][j] =
 // A[i][perm[j]] for j >= i; V_X = I.
 __global__ void build_x_kernel(const QrWork q, double *X, double *Vx)
@@ -608,15 +629,33 @@ __global__ void build_x_kernel(const QrWork q, double *X, double *Vx)
 
 // L = Q [V_X; 0] = H_0 H_1 ... H_{n-1} [V_X; 0]: one warp per column, the
 // reflectors applied last to first (columns are independent: no barrier).
-__global__ void form_left_kernel(const QrWork q, const double *Vx, double *L)
+// The columns of every problem of a batch are numbered consecutively
+// (problem p's start at jobs[p].col0).
+struct LeftJob {
+    QrWork q;
+    const double *Vx;
+    double *L;
+    int col0;
+};
+
+__global__ void form_left_kernel(const LeftJob *jobs, int njobs, int ncols)
 {
-    const int m = q.m, n = q.n, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int c = gw; c < n; c += nw) {
-        double *y = L + size_t(c) * m;
+    for (int g = gw; g < ncols; g += nw) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].col0 <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const LeftJob &J = jobs[lo];
+        const QrWork &q = J.q;
+        const int m = q.m, n = q.n, c = g - J.col0;
+        double *y = J.L + size_t(c) * m;
         for (int i = lane; i < m; i += 32)
-            y[i] = i < n ? Vx[size_t(c) * n + i] : 0.0;
+            y[i] = i < n ? J.Vx[size_t(c) * n + i] : 0.0;
         __syncwarp();
         for (int k = n - 1; k >= 0; --k) {
             const double tau = q.tau[k];
@@ -837,6 +876,288 @@ Lists split(const uint8_t *gamma1, int M_tot)
     return L;
 }
 
+// One SVD problem of a batch: inputs, orientation and its workspace.
+struct SvdProb {
+    const uint32_t *counts;
+    int M_D, M_tot, M_1, transposed;
+    uint32_t N;
+    const double *nu, *sigma;
+    double *U, *S, *V;
+    Lists L;
+    bool pre;
+    SvdWork w, wj;   // W itself, and the matrix Jacobi works on (W or X = R^T)
+    QrWork q;
+    double *sv, *Lb;
+    int *g1;
+    int qgrid;
+};
+
+int rpt_of(int m)
+{
+    return m <= kPairThreads ? 1 : m <= 2 * kPairThreads ? 2 : m <= 4 * kPairThreads ? 4 : 8;
+}
+
+const void *jacobi_kernel_rpt(int rpt)
+{
+    if (rpt == 1) return reinterpret_cast<const void *>(&jacobi_kernel<1>);
+    if (rpt == 2) return reinterpret_cast<const void *>(&jacobi_kernel<2>);
+    if (rpt == 4) return reinterpret_cast<const void *>(&jacobi_kernel<4>);
+    return reinterpret_cast<const void *>(&jacobi_kernel<8>);
+}
+
+// Cooperative launches over groups of problems whose CTAs are co-resident:
+// problem p's CTAs are [begin[p], begin[p] + grid_p).  The work records and
+// the begin table go to the device (dev_recs: room for all problems).
+template <typename Rec>
+cudaError_t launch_groups(const void *kfn, int threads, int budget, const std::vector<int> &idx,
+                          const std::vector<int> &grids, const std::vector<Rec> &recs,
+                          Rec *dev_recs, int *dev_begin, cudaStream_t st, int *launches)
+{
+    size_t at = 0;
+    while (at < idx.size()) {
+        size_t end = at;
+        int total = 0;
+        while (end < idx.size() && (end == at || total + grids[idx[end]] <= budget))
+            total += grids[idx[end++]];
+        const int np = int(end - at);
+        std::vector<Rec> r(np);
+        std::vector<int> begin(np + 1, 0);
+        for (int q = 0; q < np; ++q) {
+            r[q] = recs[idx[at + q]];
+            begin[q + 1] = begin[q] + grids[idx[at + q]];
+        }
+        Rec *dr = dev_recs + at;
+        int *db = dev_begin + at;
+        cudaMemcpyAsync(dr, r.data(), sizeof(Rec) * np, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(db, begin.data(), sizeof(int) * (np + 1), cudaMemcpyHostToDevice, st);
+        const Rec *cdr = dr;
+        const int *cdb = db;
+        int cnp = np;
+        void *args[] = {&cdr, &cdb, &cnp};
+        cudaError_t e = cudaLaunchCooperativeKernel(kfn, dim3(total), dim3(threads), args, 0, st);
+        ++*launches;
+        if (e != cudaSuccess)
+            return e;
+        at = end;
+    }
+    return cudaSuccess;
+}
+
+// The whole SVD pipeline for a batch of problems (one stream): per-problem
+// small kernels, batched cooperative QR and Jacobi launches.
+wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
+                     cudaStream_t st)
+{
+    const int np = int(P.size());
+    const int sms = wos::ctx_sm_count(ctx);
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    int qbps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&qbps, qrcp_kernel, kQrThreads, 0);
+    const int qbudget = std::max(1, qbps) * sms;
+    // workspace layout
+    std::vector<size_t> o_base(np);
+    size_t off = 0;
+    auto take = [&](size_t b) { size_t o = off; off += al(b); return o; };
+    struct Off { size_t W, V, sv, bar, ver, g1, X, L, tau, perm, cn, cn0, done, pv, pi, qbar; };
+    std::vector<Off> O(np);
+    for (int p = 0; p < np; ++p) {
+        SvdProb &b = P[p];
+        SvdWork &w = b.w;
+        w.m = b.transposed ? b.M_1 : b.M_D;
+        w.n = b.transposed ? b.M_D : b.M_1;
+        w.n_pad = std::max(2, w.n + (w.n & 1));
+        b.pre = w.n >= kPrecondMinN;
+        b.qgrid = b.pre ? std::max(1, std::min({w.n, 2 * sms, qbudget})) : 0;
+        Off &o = O[p];
+        o.W = take(size_t(w.m) * w.n * 8);
+        o.V = take(size_t(w.n) * w.n * 8);
+        o.sv = take(size_t(w.n) * 8);
+        o.bar = take(64);
+        o.ver = take(size_t(w.n_pad) * 4);
+        o.g1 = take(size_t(b.M_1) * 4);
+        if (b.pre) {
+            o.X = take(size_t(w.n) * w.n * 8);
+            o.L = take(size_t(w.m) * w.n * 8);
+            o.tau = take(size_t(w.n) * 8);
+            o.perm = take(size_t(w.n) * 4);
+            o.cn = take(size_t(w.n) * 8);
+            o.cn0 = take(size_t(w.n) * 8);
+            o.done = take(size_t(w.n) * 4);
+            o.pv = take(size_t(b.qgrid) * 2 * 8);
+            o.pi = take(size_t(b.qgrid) * 2 * 4);
+            o.qbar = take(64);
+        }
+    }
+    const size_t o_jrec = take(sizeof(SvdWork) * np), o_qrec = take(sizeof(QrWork) * np);
+    const size_t o_left = take(sizeof(LeftJob) * np);
+    const size_t o_begin = take(sizeof(int) * (2 * np + 2));
+    char *base = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&base), off, st);
+    if (e != cudaSuccess)
+        return wos::cuda_status(e);
+    int launches = 0;
+    std::vector<SvdWork> jrecs(np);
+    std::vector<QrWork> qrecs(np);
+    std::vector<int> qidx, jgrids(np, 0), qgrids(np, 0);
+    for (int p = 0; p < np; ++p) {
+        SvdProb &b = P[p];
+        const Off &o = O[p];
+        SvdWork &w = b.w;
+        w.W = reinterpret_cast<double *>(base + o.W);
+        w.Vw = reinterpret_cast<double *>(base + o.V);
+        w.bar = reinterpret_cast<unsigned *>(base + o.bar);
+        w.ver = reinterpret_cast<unsigned *>(base + o.ver);
+        b.sv = reinterpret_cast<double *>(base + o.sv);
+        b.g1 = reinterpret_cast<int *>(base + o.g1);
+        cudaMemsetAsync(w.bar, 0, 64, st);
+        cudaMemsetAsync(w.ver, 0, al(size_t(w.n_pad) * 4), st);
+        cudaMemcpyAsync(b.g1, b.L.g1.data(), size_t(b.M_1) * 4, cudaMemcpyHostToDevice, st);
+        form_B_kernel<<<sms * 4, 256, 0, st>>>(w, b.counts, b.M_D, b.M_tot, 1.0 / double(b.N),
+                                              b.g1, b.M_1, b.nu, b.sigma, b.transposed);
+        ++launches;
+        b.wj = w;
+        if (b.pre) {
+            QrWork &q = b.q;
+            q.A = w.W;
+            q.m = w.m;
+            q.n = w.n;
+            q.tau = reinterpret_cast<double *>(base + o.tau);
+            q.perm = reinterpret_cast<int *>(base + o.perm);
+            q.cn = reinterpret_cast<double *>(base + o.cn);
+            q.cn0 = reinterpret_cast<double *>(base + o.cn0);
+            q.done = reinterpret_cast<int *>(base + o.done);
+            q.pval = reinterpret_cast<double *>(base + o.pv);
+            q.pidx = reinterpret_cast<int *>(base + o.pi);
+            q.bar = reinterpret_cast<unsigned *>(base + o.qbar);
+            cudaMemsetAsync(q.done, 0, size_t(w.n) * 4, st);
+            cudaMemsetAsync(q.bar, 0, 64, st);
+            b.wj.W = reinterpret_cast<double *>(base + o.X);
+            b.wj.m = w.n;
+            b.Lb = reinterpret_cast<double *>(base + o.L);
+            qrecs[p] = q;
+            qgrids[p] = b.qgrid;
+            qidx.push_back(p);
+        }
+        jrecs[p] = b.wj;
+    }
+    QrWork *dq = reinterpret_cast<QrWork *>(base + o_qrec);
+    SvdWork *dj = reinterpret_cast<SvdWork *>(base + o_jrec);
+    int *dbegin = reinterpret_cast<int *>(base + o_begin);
+    {
+        long long want = 0;
+        for (int p : qidx)
+            want += qgrids[p];
+        if (want > qbudget)
+            for (int p : qidx)
+                qgrids[p] = std::max(1, int(qgrids[p] * (long long)qbudget / want));
+    }
+    if (!qidx.empty())
+        e = launch_groups(reinterpret_cast<const void *>(qrcp_kernel), kQrThreads, qbudget,
+                          qidx, qgrids, qrecs, dq, dbegin, st, &launches);
+    for (int p = 0; e == cudaSuccess && p < np; ++p)
+        if (P[p].pre) {
+            build_x_kernel<<<sms * 4, 256, 0, st>>>(P[p].q, P[p].wj.W, P[p].wj.Vw);
+            ++launches;
+        }
+    // Jacobi: one cooperative launch per class of rows per thread (and per
+    // group of co-resident problems); the CTAs are shared in proportion to
+    // the pairs when the batch is larger than the GPU
+    for (int rpt : {1, 2, 4, 8}) {
+        if (e != cudaSuccess)
+            break;
+        std::vector<int> idx;
+        for (int p = 0; p < np; ++p)
+            if (rpt_of(P[p].wj.m) == rpt)
+                idx.push_back(p);
+        if (idx.empty())
+            continue;
+        const void *jk = jacobi_kernel_rpt(rpt);
+        int bps = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, jk, kPairThreads, 0);
+        const int budget = std::max(1, bps) * sms;
+        long long want = 0;
+        for (int p : idx) {
+            jgrids[p] = std::min({P[p].wj.n_pad / 2, 2 * sms, budget});
+            want += jgrids[p];
+        }
+        if (want > budget)
+            for (int p : idx)
+                jgrids[p] = std::max(1, int(jgrids[p] * (long long)budget / want));
+        e = launch_groups(jk, kPairThreads, budget, idx, jgrids, jrecs, dj,
+                          dbegin + np + 1, st, &launches);
+    }
+    if (e == cudaSuccess && !qidx.empty()) {  // left vectors of every preconditioned problem
+        std::vector<LeftJob> jobs;
+        int ncols = 0;
+        for (int p : qidx) {
+            jobs.push_back(LeftJob{P[p].q, P[p].wj.Vw, P[p].Lb, ncols});
+            ncols += P[p].w.n;
+        }
+        LeftJob *dl = reinterpret_cast<LeftJob *>(base + o_left);
+        cudaMemcpyAsync(dl, jobs.data(), sizeof(LeftJob) * jobs.size(), cudaMemcpyHostToDevice,
+                        st);
+        form_left_kernel<<<std::max(1, std::min((ncols + 7) / 8, sms * 8)), 256, 0, st>>>(
+            dl, int(jobs.size()), ncols);
+        ++launches;
+    }
+    for (int p = 0; e == cudaSuccess && p < np; ++p) {
+        SvdProb &b = P[p];
+        column_norms_kernel<<<sms, 256, 0, st>>>(b.wj, b.sv);
+        if (b.pre)
+            finalize_pre_kernel<<<sms, 256, 0, st>>>(b.Lb, b.wj.W, b.q.perm, b.sv, b.w.m, b.w.n,
+                                                     b.transposed, b.U, b.S, b.V);
+        else
+            finalize_kernel<<<sms, 256, 0, st>>>(b.w, b.sv, b.transposed, b.U, b.S, b.V);
+        launches += 2;
+    }
+    if (e == cudaSuccess)
+        e = cudaGetLastError();
+    wos::count_launches(ctx, launches);
+    wos_status status = wos::cuda_status(e);
+    if (status == WOS_OK && sweeps) {
+        std::vector<unsigned> hb(size_t(np) * 14, 0u);
+        for (int p = 0; p < np; ++p) {
+            cudaMemcpyAsync(hb.data() + p * 14, P[p].w.bar, 7 * 4, cudaMemcpyDeviceToHost, st);
+            if (P[p].pre)
+                cudaMemcpyAsync(hb.data() + p * 14 + 7, P[p].q.bar, 7 * 4, cudaMemcpyDeviceToHost,
+                                st);
+        }
+        e = cudaStreamSynchronize(st);
+        status = wos::cuda_status(e);
+        for (int p = 0; p < np; ++p) {
+            sweeps[p] = int32_t(hb[p * 14 + 6]);
+            if (status == WOS_OK && hb[p * 14 + 7 + 5] != 0u)
+                status = wos_status(hb[p * 14 + 7 + 5]);
+            if (status == WOS_OK && hb[p * 14 + 5] != 0u)
+                status = wos_status(hb[p * 14 + 5]);
+        }
+    }
+    cudaFreeAsync(base, st);
+    return status;
+}
+
+wos_status svd_prob(const wos_svd_problem &in, SvdProb *b)
+{
+    if (!in.counts || !in.gamma1 || !in.sigma || !in.U || !in.S || !in.V || in.M_D < 1 ||
+        in.M_tot < 1 || in.N < 1)
+        return WOS_INVALID_ARG;
+    b->counts = in.counts;
+    b->M_D = in.M_D;
+    b->M_tot = in.M_tot;
+    b->N = in.N;
+    b->nu = in.nu;
+    b->sigma = in.sigma;
+    b->U = in.U;
+    b->S = in.S;
+    b->V = in.V;
+    b->L = split(in.gamma1, in.M_tot);
+    b->M_1 = int(b->L.g1.size());
+    if (b->M_1 < 1)
+        return WOS_INVALID_ARG;
+    b->transposed = b->M_D < b->M_1;
+    return WOS_OK;
+}
+
 }  // namespace
 
 extern "C" wos_status wos_op_svd(wos_context *ctx, const uint32_t *counts, int32_t M_D,
@@ -844,135 +1165,31 @@ extern "C" wos_status wos_op_svd(wos_context *ctx, const uint32_t *counts, int32
                                  const double *nu, const double *sigma, double *U,
                                  double *S, double *V, int32_t *sweeps, void *stream)
 {
-    if (!ctx || !counts || !gamma1 || !sigma || !U || !S || !V || M_D < 1 ||
-        M_tot < 1 || N < 1)
+    if (!ctx)
         return WOS_INVALID_ARG;
+    wos_svd_problem in = {counts, M_D, M_tot, N, gamma1, nu, sigma, U, S, V};
+    std::vector<SvdProb> P(1);
+    wos_status st = svd_prob(in, &P[0]);
+    if (st != WOS_OK)
+        return st;
     cudaSetDevice(wos::ctx_device(ctx));
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    Lists L = split(gamma1, M_tot);
-    const int M_1 = int(L.g1.size());
-    if (M_1 < 1)
+    return svd_batch(ctx, P, sweeps, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" wos_status wos_op_svd_batched(wos_context *ctx, int32_t n,
+                                         const wos_svd_problem *problems, int32_t *sweeps,
+                                         void *stream)
+{
+    if (!ctx || n < 1 || !problems)
         return WOS_INVALID_ARG;
-    const int transposed = M_D < M_1;
-    SvdWork w;
-    w.m = transposed ? M_1 : M_D;
-    w.n = transposed ? M_D : M_1;
-    w.n_pad = w.n + (w.n & 1);
-    if (w.n_pad < 2) w.n_pad = 2;
-    const bool pre = w.n >= kPrecondMinN;
-    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
-    const int sms = wos::ctx_sm_count(ctx);
-    // QR: grid of co-resident CTAs, each owning at least one column
-    int qbps = 0;
-    if (pre)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&qbps, qrcp_kernel, kQrThreads, 0);
-    const int qgrid = pre ? std::max(1, std::min({w.n, 2 * sms, std::max(1, qbps) * sms})) : 0;
-    const size_t bytes_W = al(size_t(w.m) * w.n * 8), bytes_V = al(size_t(w.n) * w.n * 8);
-    const size_t bytes_ver = al(size_t(w.n_pad) * 4);
-    size_t off = 0;
-    auto take = [&](size_t b) { size_t o = off; off += al(b); return o; };
-    const size_t o_W = take(bytes_W), o_V = take(bytes_V), o_sv = take(size_t(w.n) * 8);
-    const size_t o_bar = take(64), o_ver = take(bytes_ver), o_g1 = take(size_t(M_1) * 4);
-    size_t o_X = 0, o_L = 0, o_tau = 0, o_perm = 0, o_cn = 0, o_cn0 = 0, o_done = 0,
-           o_pv = 0, o_pi = 0, o_qbar = 0;
-    if (pre) {
-        o_X = take(bytes_V);
-        o_L = take(bytes_W);
-        o_tau = take(size_t(w.n) * 8);
-        o_perm = take(size_t(w.n) * 4);
-        o_cn = take(size_t(w.n) * 8);
-        o_cn0 = take(size_t(w.n) * 8);
-        o_done = take(size_t(w.n) * 4);
-        o_pv = take(size_t(qgrid) * 2 * 8);
-        o_pi = take(size_t(qgrid) * 2 * 4);
-        o_qbar = take(64);
+    std::vector<SvdProb> P(n);
+    for (int q = 0; q < n; ++q) {
+        wos_status st = svd_prob(problems[q], &P[q]);
+        if (st != WOS_OK)
+            return st;
     }
-    char *base = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&base), off, st);
-    if (e != cudaSuccess)
-        return wos::cuda_status(e);
-    w.W = reinterpret_cast<double *>(base + o_W);
-    w.Vw = reinterpret_cast<double *>(base + o_V);
-    double *sv = reinterpret_cast<double *>(base + o_sv);
-    w.bar = reinterpret_cast<unsigned *>(base + o_bar);
-    w.ver = reinterpret_cast<unsigned *>(base + o_ver);
-    int *g1 = reinterpret_cast<int *>(base + o_g1);
-    cudaMemsetAsync(w.bar, 0, 64, st);
-    cudaMemsetAsync(w.ver, 0, bytes_ver, st);
-    cudaMemcpyAsync(g1, L.g1.data(), size_t(M_1) * 4, cudaMemcpyHostToDevice, st);
-    form_B_kernel<<<sms * 4, 256, 0, st>>>(w, counts, M_D, M_tot, 1.0 / double(N), g1, M_1,
-                                          nu, sigma, transposed);
-    int launches = 1;
-    QrWork q;
-    SvdWork wj = w;  // the matrix Jacobi works on: W, or X = R^T
-    if (pre) {
-        q.A = w.W;
-        q.m = w.m;
-        q.n = w.n;
-        q.tau = reinterpret_cast<double *>(base + o_tau);
-        q.perm = reinterpret_cast<int *>(base + o_perm);
-        q.cn = reinterpret_cast<double *>(base + o_cn);
-        q.cn0 = reinterpret_cast<double *>(base + o_cn0);
-        q.done = reinterpret_cast<int *>(base + o_done);
-        q.pval = reinterpret_cast<double *>(base + o_pv);
-        q.pidx = reinterpret_cast<int *>(base + o_pi);
-        q.bar = reinterpret_cast<unsigned *>(base + o_qbar);
-        cudaMemsetAsync(q.done, 0, size_t(w.n) * 4, st);
-        cudaMemsetAsync(q.bar, 0, 64, st);
-        void *qargs[] = {&q};
-        e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(qrcp_kernel),
-                                        dim3(qgrid), dim3(kQrThreads), qargs, 0, st);
-        ++launches;
-        if (e == cudaSuccess) {
-            wj.W = reinterpret_cast<double *>(base + o_X);
-            wj.m = w.n;
-            build_x_kernel<<<sms * 4, 256, 0, st>>>(q, wj.W, wj.Vw);
-            ++launches;
-        }
-    }
-    if (e == cudaSuccess) {
-        // cooperative Jacobi: one pair per CTA at a time, all CTAs co-resident
-        int bps = 0;
-        const void *jk = jacobi_kernel_for(wj.m);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, jk, kPairThreads, 0);
-        int pairs = wj.n_pad / 2;
-        int grid = std::max(1, std::min({pairs, 2 * sms, std::max(1, bps) * sms}));
-        void *args[] = {&wj};
-        e = cudaLaunchCooperativeKernel(jk, dim3(grid), dim3(kPairThreads), args, 0, st);
-        ++launches;
-    }
-    if (e == cudaSuccess) {
-        column_norms_kernel<<<sms, 256, 0, st>>>(wj, sv);
-        if (pre) {
-            double *Lb = reinterpret_cast<double *>(base + o_L);
-            form_left_kernel<<<std::max(1, std::min((w.n + 7) / 8, sms * 8)), 256, 0, st>>>(
-                q, wj.Vw, Lb);
-            finalize_pre_kernel<<<sms, 256, 0, st>>>(Lb, wj.W, q.perm, sv, w.m, w.n,
-                                                     transposed, U, S, V);
-            launches += 3;
-        } else {
-            finalize_kernel<<<sms, 256, 0, st>>>(w, sv, transposed, U, S, V);
-            launches += 2;
-        }
-        e = cudaGetLastError();
-    }
-    wos::count_launches(ctx, launches);
-    wos_status status = wos::cuda_status(e);
-    if (status == WOS_OK && sweeps) {
-        unsigned hb[7], qb[7] = {0, 0, 0, 0, 0, 0, 0};
-        cudaMemcpyAsync(hb, w.bar, sizeof(hb), cudaMemcpyDeviceToHost, st);
-        if (pre)
-            cudaMemcpyAsync(qb, q.bar, sizeof(qb), cudaMemcpyDeviceToHost, st);
-        e = cudaStreamSynchronize(st);
-        status = wos::cuda_status(e);
-        *sweeps = int32_t(hb[6]);
-        if (status == WOS_OK && qb[5] != 0u)
-            status = wos_status(qb[5]);
-        if (status == WOS_OK && hb[5] != 0u)
-            status = wos_status(hb[5]);
-    }
-    cudaFreeAsync(base, st);
-    return status;
+    cudaSetDevice(wos::ctx_device(ctx));
+    return svd_batch(ctx, P, sweeps, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" wos_status wos_reconstruct(wos_context *ctx, const double *U, const double *S,

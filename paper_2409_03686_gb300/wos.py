@@ -144,6 +144,21 @@ class WosStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class WosSvdProblem(ctypes.Structure):
+    _fields_ = [
+        ("counts", ctypes.c_void_p),
+        ("M_D", ctypes.c_int32),
+        ("M_tot", ctypes.c_int32),
+        ("N", ctypes.c_uint32),
+        ("gamma1", ctypes.c_void_p),
+        ("nu", ctypes.c_void_p),
+        ("sigma", ctypes.c_void_p),
+        ("U", ctypes.c_void_p),
+        ("S", ctypes.c_void_p),
+        ("V", ctypes.c_void_p),
+    ]
+
+
 class WosQueueOpts(ctypes.Structure):
     _fields_ = [
         ("max_inflight", ctypes.c_int32),
@@ -236,6 +251,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.wos_reconstruct.argtypes = [vp, vp, vp, vp, i32, i32, vp, i32, u32, vp, vp, vp, vp,
                                   vp, i32, dbl, vp, vp, vp]
     L.wos_truncation_gap.argtypes = [vp, i32, i32]
+    L.wos_op_svd_batched.argtypes = [vp, i32, vp, vp, vp]
     L.wos_spectral.argtypes = [vp, vp, vp, vp, i32, i32, vp, i32, u32, vp, vp, vp, vp, vp,
                                i32, vp, vp, vp, vp, vp, vp]
     L.wos_queue_create.argtypes = [vp, vp, ctypes.POINTER(vp)]
@@ -566,6 +582,42 @@ def wos_op_svd(ctx: Context, counts, N: int, gamma1: np.ndarray, sigma, nu=None,
                         _stream(stream))
     _check(code, "wos_op_svd", allow_warning=False)
     return U, S, V, int(sw.value)
+
+
+def wos_op_svd_batched(ctx: Context, items, sync: bool = True, stream=None):
+    """Many SVDs in one pass.  items: list of (counts, N, gamma1, sigma[, nu]).
+    Returns a list of (U, S, V, sweeps)."""
+    import torch
+    L = load()
+    probs = (WosSvdProblem * len(items))()
+    keep, out = [], []
+    for q, it in enumerate(items):
+        counts, N, gamma1, sigma = it[:4]
+        nu = it[4] if len(it) > 4 else None
+        M_D, M_tot = int(counts.shape[0]), int(counts.shape[1])
+        g1 = np.ascontiguousarray(gamma1, dtype=np.uint8)
+        M_1 = int(g1.sum())
+        k = min(M_D, M_1)
+        dev = counts.device
+        U = torch.empty((M_D, k), dtype=torch.float64, device=dev)
+        S = torch.empty(k, dtype=torch.float64, device=dev)
+        V = torch.empty((M_1, k), dtype=torch.float64, device=dev)
+        keep.append(g1)
+        out.append([U, S, V, 0])
+        pb = probs[q]
+        pb.counts = counts.data_ptr()
+        pb.M_D, pb.M_tot, pb.N = M_D, M_tot, int(N)
+        pb.gamma1 = g1.ctypes.data
+        pb.nu = _ptr(nu)
+        pb.sigma = sigma.data_ptr()
+        pb.U, pb.S, pb.V = U.data_ptr(), S.data_ptr(), V.data_ptr()
+    sw = (ctypes.c_int32 * len(items))()
+    code = L.wos_op_svd_batched(ctx.h, len(items), ctypes.byref(probs),
+                                sw if sync else None, _stream(stream))
+    _check(code, "wos_op_svd_batched", allow_warning=False)
+    for q in range(len(items)):
+        out[q][3] = int(sw[q])
+    return [tuple(o) for o in out]
 
 
 def wos_reconstruct(ctx: Context, U, S, V, counts, N: int, gamma1: np.ndarray, sigma,

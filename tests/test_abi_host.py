@@ -59,6 +59,7 @@ int main(void) {
   printf("%zu %zu %zu %zu\\n", offsetof(wos_domain, hole_radius),
          offsetof(wos_partition, voronoi_sites), offsetof(wos_opts, kernel_events),
          offsetof(wos_stats, kernel_ms));
+  printf("%zu %zu\\n", sizeof(wos_svd_problem), offsetof(wos_svd_problem, V));
   printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(wos_problem), sizeof(wos_request),
          sizeof(wos_queue_opts), sizeof(wos_queue_stats), offsetof(wos_problem, k1),
          offsetof(wos_request, r_used), offsetof(wos_queue_opts, side_streams),
@@ -69,8 +70,10 @@ int main(void) {
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", str(ROOT / "include"), str(src), "-o", str(exe)],
                    check=True)
-    a, b, c = subprocess.run([str(exe)], capture_output=True, text=True,
-                             check=True).stdout.split("\n")[:3]
+    a, b, sp, c = subprocess.run([str(exe)], capture_output=True, text=True,
+                                 check=True).stdout.split("\n")[:4]
+    assert [int(x) for x in sp.split()] == [ctypes.sizeof(wos.WosSvdProblem),
+                                            wos.WosSvdProblem.V.offset]
     sizes = [int(x) for x in a.split()]
     offs = [int(x) for x in b.split()]
     assert sizes == [ctypes.sizeof(wos.WosDomain), ctypes.sizeof(wos.WosPartition),

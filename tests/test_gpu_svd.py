@@ -151,3 +151,27 @@ def test_svd_is_deterministic(shape):
         torch.cuda.synchronize()
         for a, b in zip(ref[:3], got[:3]):
             assert torch.equal(a, b), rep
+
+
+def test_batched_svd_equals_single_calls():
+    """wos_op_svd_batched: problems of different shapes and orientations
+    (direct path n < 32 and preconditioned n >= 32), and a batch larger than
+    the co-resident CTAs of one launch, give each problem's single-call
+    results bit for bit."""
+    shapes = [(256, 256, 128), (96, 300, 200), (40, 60, 20), (64, 96, 48), (300, 400, 150)]
+    shapes += [(128, 200, 96)] * 24
+    items, refs = [], []
+    for q, (M_D, M_tot, M_1) in enumerate(shapes):
+        C = W.synthetic_counts(M_D, M_tot, 50_000, seed=q + 11)
+        g1 = np.zeros(M_tot, np.uint8)
+        g1[:M_1] = 1
+        Ct = torch.as_tensor(C.astype(np.int32), device=DEV)
+        sg = torch.full((M_tot,), 2 * np.pi / M_tot, dtype=torch.float64, device=DEV)
+        items.append((Ct, 50_000, g1, sg))
+        refs.append(wos.wos_op_svd(ctx(), Ct, 50_000, g1, sg))
+    got = wos.wos_op_svd_batched(ctx(), items)
+    torch.cuda.synchronize()
+    for q, (r, g) in enumerate(zip(refs, got)):
+        for a, b in zip(r[:3], g[:3]):
+            assert torch.equal(a, b), q
+        assert r[3] == g[3]
