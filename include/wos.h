@@ -418,7 +418,9 @@ typedef struct {
 
 wos_status wos_op_svd_batched(wos_context *ctx, int32_t n,
                               const wos_svd_problem *problems, int32_t *sweeps,
-                              void *stream);
+                              void *stream, void *const *jacobi_events);
+/* jacobi_events: NULL, or two cudaEvent_t recorded on the stream before the
+ * first and after the last Jacobi launch (for profiling). */
 
 /* r-TSVD reconstruction (paper Sec. 2, Eq. (u1r); Sec. 4.3, Eq.
  * (u_omega_M1_r_MC A); Sec. 5.1, Rem. (b and u0 simulations), Eq. (tsvd

@@ -323,7 +323,7 @@ void worker_main(wos_queue *q)
                                             R.nu_ptr(), R.d_sigma, R.d_U, R.d_S, R.d_V};
                 }
                 wos_status s2 = wos_op_svd_batched(q->ctx, int32_t(sp.size()), sp.data(),
-                                                   nullptr, s);
+                                                   nullptr, s, nullptr);
                 for (auto &R : fin) {
                     R->side = side;
                     cudaMemcpyAsync(R->h_S, R->d_S, size_t(R->k) * 8, cudaMemcpyDeviceToHost, s);

@@ -946,7 +946,7 @@ cudaError_t launch_groups(const void *kfn, int threads, int budget, const std::v
 // The whole SVD pipeline for a batch of problems (one stream): per-problem
 // small kernels, batched cooperative QR and Jacobi launches.
 wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
-                     cudaStream_t st)
+                     cudaStream_t st, void *const *jacobi_events = nullptr)
 {
     const int np = int(P.size());
     const int sms = wos::ctx_sm_count(ctx);
@@ -1059,6 +1059,8 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
             build_x_kernel<<<sms * 4, 256, 0, st>>>(P[p].q, P[p].wj.W, P[p].wj.Vw);
             ++launches;
         }
+    if (jacobi_events && jacobi_events[0])
+        cudaEventRecord(static_cast<cudaEvent_t>(jacobi_events[0]), st);
     // Jacobi: one cooperative launch per class of rows per thread (and per
     // group of co-resident problems); the CTAs are shared in proportion to
     // the pairs when the batch is larger than the GPU
@@ -1086,6 +1088,8 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         e = launch_groups(jk, kPairThreads, budget, idx, jgrids, jrecs, dj,
                           dbegin + np + 1, st, &launches);
     }
+    if (jacobi_events && jacobi_events[1])
+        cudaEventRecord(static_cast<cudaEvent_t>(jacobi_events[1]), st);
     if (e == cudaSuccess && !qidx.empty()) {  // left vectors of every preconditioned problem
         std::vector<LeftJob> jobs;
         int ncols = 0;
@@ -1178,7 +1182,7 @@ extern "C" wos_status wos_op_svd(wos_context *ctx, const uint32_t *counts, int32
 
 extern "C" wos_status wos_op_svd_batched(wos_context *ctx, int32_t n,
                                          const wos_svd_problem *problems, int32_t *sweeps,
-                                         void *stream)
+                                         void *stream, void *const *jacobi_events)
 {
     if (!ctx || n < 1 || !problems)
         return WOS_INVALID_ARG;
@@ -1189,7 +1193,7 @@ extern "C" wos_status wos_op_svd_batched(wos_context *ctx, int32_t n,
             return st;
     }
     cudaSetDevice(wos::ctx_device(ctx));
-    return svd_batch(ctx, P, sweeps, static_cast<cudaStream_t>(stream));
+    return svd_batch(ctx, P, sweeps, static_cast<cudaStream_t>(stream), jacobi_events);
 }
 
 extern "C" wos_status wos_reconstruct(wos_context *ctx, const double *U, const double *S,

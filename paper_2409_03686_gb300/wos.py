@@ -251,7 +251,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.wos_reconstruct.argtypes = [vp, vp, vp, vp, i32, i32, vp, i32, u32, vp, vp, vp, vp,
                                   vp, i32, dbl, vp, vp, vp]
     L.wos_truncation_gap.argtypes = [vp, i32, i32]
-    L.wos_op_svd_batched.argtypes = [vp, i32, vp, vp, vp]
+    L.wos_op_svd_batched.argtypes = [vp, i32, vp, vp, vp, vp]
     L.wos_spectral.argtypes = [vp, vp, vp, vp, i32, i32, vp, i32, u32, vp, vp, vp, vp, vp,
                                i32, vp, vp, vp, vp, vp, vp]
     L.wos_queue_create.argtypes = [vp, vp, ctypes.POINTER(vp)]
@@ -584,9 +584,11 @@ def wos_op_svd(ctx: Context, counts, N: int, gamma1: np.ndarray, sigma, nu=None,
     return U, S, V, int(sw.value)
 
 
-def wos_op_svd_batched(ctx: Context, items, sync: bool = True, stream=None):
+def wos_op_svd_batched(ctx: Context, items, sync: bool = True, stream=None,
+                       jacobi_events=None):
     """Many SVDs in one pass.  items: list of (counts, N, gamma1, sigma[, nu]).
-    Returns a list of (U, S, V, sweeps)."""
+    jacobi_events: optional pair of torch.cuda.Event recorded around the
+    Jacobi launches.  Returns a list of (U, S, V, sweeps)."""
     import torch
     L = load()
     probs = (WosSvdProblem * len(items))()
@@ -612,8 +614,11 @@ def wos_op_svd_batched(ctx: Context, items, sync: bool = True, stream=None):
         pb.sigma = sigma.data_ptr()
         pb.U, pb.S, pb.V = U.data_ptr(), S.data_ptr(), V.data_ptr()
     sw = (ctypes.c_int32 * len(items))()
+    evs = None
+    if jacobi_events is not None:
+        evs = (ctypes.c_void_p * 2)(jacobi_events[0].cuda_event, jacobi_events[1].cuda_event)
     code = L.wos_op_svd_batched(ctx.h, len(items), ctypes.byref(probs),
-                                sw if sync else None, _stream(stream))
+                                sw if sync else None, _stream(stream), evs)
     _check(code, "wos_op_svd_batched", allow_warning=False)
     for q in range(len(items)):
         out[q][3] = int(sw[q])
