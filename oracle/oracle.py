@@ -106,6 +106,11 @@ class OrcInstance(ctypes.Structure):
         ("N", ctypes.c_uint32),
         ("step_cap", ctypes.c_uint32),
         ("words_per_uniform", ctypes.c_int32),
+        ("mapped", ctypes.c_int32),
+        ("n_planes", ctypes.c_int32),
+        ("plane_n", (ctypes.c_double * 3) * 64),
+        ("plane_d", ctypes.c_double * 64),
+        ("Sinv", ctypes.c_double * 9),
     ]
 
 
@@ -171,6 +176,41 @@ def setup_S(K):
     return S[: d * d].reshape(d, d).copy(), lam.value
 
 
+def mapped_planes(dom, S):
+    """Faces of the polytope S^{-1} D (D a box or a convex polygon without
+    holes): unit outward normals n_f and offsets d_f in y = S^{-1} x, so that
+    dist(y, boundary) = min_f (d_f - n_f . y) inside.  A face a.x = c of D
+    becomes (S a).y = c, S symmetric."""
+    d = dom.dim
+    if dom.holes:
+        raise ValueError("mapped walks: domains without holes only")
+    faces = []  # (a, c): a.x <= c inside
+    if dom.outer == "box":
+        for a in range(d):
+            for sgn in (-1.0, 1.0):
+                n = np.zeros(d)
+                n[a] = sgn
+                faces.append((n, sgn * dom.center[a] + dom.half[a]))
+    elif dom.outer == "polygon" and d == 2:
+        v = np.asarray(dom.vertices, dtype=np.float64)
+        for e in range(len(v)):
+            t = v[(e + 1) % len(v)] - v[e]
+            t2 = v[(e + 2) % len(v)] - v[(e + 1) % len(v)]
+            if t[0] * t2[1] - t[1] * t2[0] <= 0:
+                raise ValueError("mapped walks: convex counter-clockwise polygons only")
+            n = np.array([t[1], -t[0]]) / np.hypot(t[0], t[1])
+            faces.append((n, float(n @ v[e])))
+    else:
+        raise ValueError("mapped walks: boxes and convex polygons only")
+    out_n, out_d = [], []
+    for a, c in faces:
+        m = S @ a
+        L = np.linalg.norm(m)
+        out_n.append(m / L)
+        out_d.append(c / L)
+    return np.array(out_n), np.array(out_d)
+
+
 def make_instance(inst, words_per_uniform: int | None = None):
     D, keep = make_domain(inst.domain, inst.partition)
     I = OrcInstance()
@@ -186,6 +226,17 @@ def make_instance(inst, words_per_uniform: int | None = None):
     if words_per_uniform is None:
         words_per_uniform = 2 if inst.fp64 else 1
     I.words_per_uniform = words_per_uniform
+    if getattr(inst, "mapped", False):
+        pn, pd = mapped_planes(inst.domain, S)
+        I.mapped = 1
+        I.n_planes = len(pd)
+        for f in range(len(pd)):
+            for a in range(inst.dim):
+                I.plane_n[f][a] = pn[f, a]
+            I.plane_d[f] = pd[f]
+        Sinv = np.linalg.inv(S)
+        for q, v in enumerate(Sinv.ravel()):
+            I.Sinv[q] = v
     return I, keep
 
 

@@ -357,9 +357,69 @@ int orc_classify(const orc_domain *D, const double *x)
 /* ------------------------------------------------------------------ */
 /* One walk of the chain (Eq. wos chain) stopped at N_eps.             */
 /* ------------------------------------------------------------------ */
+/* The mapped chain (a reading of Sec. 4.2 with the exact distance): in
+ * y = S^{-1} x the diffusion of div(K grad) is a Brownian motion in the
+ * polytope S^{-1} D, and the walk is walk-on-spheres there,
+ * Y_{n+1} = Y_n + dist_y(Y_n) U_n, stopped at dist_y <= eps; the exit point
+ * S Y is classified in x. */
+static int orc_walk_mapped(const orc_instance *I, const double *x0, uint64_t walk,
+                           double *x_exit, uint32_t *nsteps)
+{
+    const int d = I->dom.dim;
+    const int wpu = I->words_per_uniform;
+    const int wps = (d == 2 ? 1 : 2) * wpu;
+    const int G = 4 / wps;
+    const uint32_t key[2] = {(uint32_t)I->seed, (uint32_t)(I->seed >> 32)};
+    double Y[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < d; ++a)
+        for (int b = 0; b < d; ++b)
+            Y[a] += I->Sinv[a * d + b] * x0[b];
+    uint32_t words[4] = {0, 0, 0, 0};
+    for (uint32_t n = 0;; ++n) {
+        double r = INFINITY;
+        for (int f = 0; f < I->n_planes; ++f) {
+            double s = I->plane_d[f];
+            for (int a = 0; a < d; ++a)
+                s -= I->plane_n[f][a] * Y[a];
+            r = fmin(r, s);
+        }
+        if (r <= I->eps || n >= I->step_cap) {
+            double X[3] = {0.0, 0.0, 0.0};
+            for (int a = 0; a < d; ++a)
+                for (int b = 0; b < d; ++b)
+                    X[a] += I->S[a * d + b] * Y[b];
+            for (int a = 0; a < d; ++a)
+                x_exit[a] = X[a];
+            *nsteps = n;
+            return r <= I->eps ? orc_classify(&I->dom, X) : -1;
+        }
+        if (n % (uint32_t)G == 0) {
+            uint32_t ctr[4] = {n / (uint32_t)G, (uint32_t)walk,
+                               (uint32_t)(walk >> 32), I->stream};
+            orc_philox4x32_10(ctr, key, words);
+        }
+        const uint32_t *w = words + (n % (uint32_t)G) * (uint32_t)wps;
+        if (d == 2) {
+            double u = uniform_from_words(w, wpu);
+            Y[0] += r * cos(2.0 * M_PI * u);
+            Y[1] += r * sin(2.0 * M_PI * u);
+        } else {
+            double u1 = uniform_from_words(w, wpu);
+            double u2 = uniform_from_words(w + wpu, wpu);
+            double z = 1.0 - 2.0 * u1;
+            double sr = sqrt(fmax(0.0, 1.0 - z * z));
+            Y[0] += r * sr * cos(2.0 * M_PI * u2);
+            Y[1] += r * sr * sin(2.0 * M_PI * u2);
+            Y[2] += r * z;
+        }
+    }
+}
+
 int orc_walk(const orc_instance *I, const double *x0, uint64_t walk,
              double *x_exit, uint32_t *nsteps)
 {
+    if (I->mapped)
+        return orc_walk_mapped(I, x0, walk, x_exit, nsteps);
     const int d = I->dom.dim;
     const int wpu = I->words_per_uniform;
     const int wps = (d == 2 ? 1 : 2) * wpu;

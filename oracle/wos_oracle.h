@@ -11,6 +11,7 @@
 
 #define ORC_MAX_VERTS 64
 #define ORC_MAX_HOLES 16
+#define ORC_MAX_PLANES 64
 
 enum { ORC_OUTER_SPHERE = 1, ORC_OUTER_BOX = 2, ORC_OUTER_POLYGON = 3 };
 
@@ -53,6 +54,13 @@ typedef struct {
     uint32_t N;         /* walks per point (walk id = i * N + k) */
     uint32_t step_cap;  /* walks reaching it are left unterminated */
     int32_t words_per_uniform; /* 1: 24-bit, 2: 53-bit uniforms */
+    /* mapped = 1: walk-on-spheres in y = S^{-1} x, whose domain S^{-1} D is a
+     * convex polytope: dist_y(y) = min_f (plane_d[f] - plane_n[f] . y) */
+    int32_t mapped;
+    int32_t n_planes;
+    double plane_n[ORC_MAX_PLANES][3];
+    double plane_d[ORC_MAX_PLANES];
+    double Sinv[9];     /* row-major d x d */
 } orc_instance;
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],

@@ -76,6 +76,7 @@ class Instance:
     fp64: bool = False
     step_cap: int = 1_000_000
     nu: np.ndarray | None = None  # default 1/sqrt(M_D) (Sec. 5.2)
+    mapped: bool = False  # walk-on-spheres in y = S^{-1} x (boxes, convex polygons)
 
     @property
     def dim(self) -> int:
