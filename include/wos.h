@@ -128,6 +128,13 @@ typedef struct {
     void *kernel_events[2]; /* optional cudaEvent_t pair (caller-created):
                                recorded on `stream` right before and after
                                the walk kernel, to time it alone */
+    int32_t mapped;      /* 1: walk-on-spheres in y = S^{-1} x with the exact
+                            distance to the polytope S^{-1} D (larger steps
+                            than the paper's ellipsoids inside the Euclidean
+                            ball, Sec. 4.2); stop at dist_y <= eps (then
+                            dist_x <= eps); exits classified in x.  Boxes and
+                            convex counter-clockwise polygons of at most 8
+                            edges without holes, else WOS_INVALID_ARG */
 } wos_opts;
 
 /* Per-build statistics (filled after the build's device work finished). */

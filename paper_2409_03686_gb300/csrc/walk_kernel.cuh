@@ -38,11 +38,13 @@ namespace wos {
 
 // Kernel kinds: any domain; a disc / ball; a box; a disc / ball with holes;
 // a disc / ball with one concentric hole (annulus, spherical shell: both
-// boundary distances come from one radius).
+// boundary distances come from one radius); mapped walks (walk-on-spheres in
+// y = S^{-1} x, the domain a convex polytope given by its faces).
 enum KernelKind : int {
-    kGeneric = 0, kSphereOnly = 1, kBoxOnly = 2, kSphereHoles = 3, kAnnulus = 4
+    kGeneric = 0, kSphereOnly = 1, kBoxOnly = 2, kSphereHoles = 3, kAnnulus = 4,
+    kMapped = 5
 };
-constexpr int kNumKinds = 5;
+constexpr int kNumKinds = 6;
 
 // One instance of the operator build.
 template <typename Real> struct WalkInst {
@@ -98,6 +100,23 @@ __device__ __forceinline__ Real walk_dist(const Geom<Real> &g, const Real *x)
             r = w_min(r, hole_dist<Real, DIM>(g, h, x));
         return r;
     }
+    if (KIND == kMapped) {  // exact distance to the polytope S^{-1} D
+        Real r = g.pd[0];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a)
+            r = fma(-g.pn[0][a], x[a], r);
+#pragma unroll
+        for (int f = 1; f < kMaxPlanes; ++f) {
+            if (f < g.np) {
+                Real s = g.pd[f];
+#pragma unroll
+                for (int a = 0; a < DIM; ++a)
+                    s = fma(-g.pn[f][a], x[a], s);
+                r = w_min(r, s);
+            }
+        }
+        return r;
+    }
     if (KIND == kAnnulus) {  // |x - c| once: the same values as the two distances
         Real s = Real(0);
 #pragma unroll
@@ -121,6 +140,8 @@ __device__ __forceinline__ int32_t walk_classify(const Geom<Real> &g, const Real
         return outer_box_cell<Real, DIM>(g, x);
     if (KIND == kSphereHoles || KIND == kAnnulus)
         return sphere_holes_cell<Real, DIM>(g, x);
+    if (KIND == kMapped && g.vn == 0 && g.n_holes == 0 && g.outer_kind == kBox)
+        return outer_box_cell<Real, DIM>(g, x);
     return classify<Real, DIM>(g, x);
 }
 
@@ -295,6 +316,19 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
                     for (int a = 0; a < DIM; ++a)
                         tile_x[a] = T.points_r ? T.points_r[size_t(ti) * DIM + a]
                                                : Real(T.points[size_t(ti) * DIM + a]);
+                    if (KIND == kMapped) {  // the walk runs in y = S^{-1} x
+                        Real y[DIM];
+#pragma unroll
+                        for (int a = 0; a < DIM; ++a) {
+                            y[a] = Real(0);
+#pragma unroll
+                            for (int b = 0; b < DIM; ++b)
+                                y[a] = fma(T.g.mSinv[a * DIM + b], tile_x[b], y[a]);
+                        }
+#pragma unroll
+                        for (int a = 0; a < DIM; ++a)
+                            tile_x[a] = y[a];
+                    }
                     if (p.nslot > 0) {
                         int32_t s = (p.nslot == 2) ? (slot_cur ^ 1) : 0;
                         int32_t old_pt = s ? pt1 : pt0;
@@ -376,6 +410,20 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
         const unsigned fin_mask = __ballot_sync(FULL, fin);
         if (fin_mask == 0u)
             continue;
+        if (KIND == kMapped && fin) {  // exit point back in x = S y
+            const WalkInst<Real> &I = inst(linst);
+            Real xo[DIM];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                xo[a] = Real(0);
+#pragma unroll
+                for (int b = 0; b < DIM; ++b)
+                    xo[a] = fma(I.g.mS[a * DIM + b], X[b], xo[a]);
+            }
+#pragma unroll
+            for (int a = 0; a < DIM; ++a)
+                X[a] = xo[a];
+        }
 
         // ---- queue the finished walks; tally 32 at a time (Eq. (WoE_matrix_MC))
         const unsigned cap_mask = __ballot_sync(FULL, fin && capped);

@@ -37,13 +37,16 @@ const void *pick_walk_kernel(int kind)
     if (kind == kBoxOnly) return walk_kernel_ptr<Real, DIM, kBoxOnly, MULTI>();
     if (kind == kSphereHoles) return walk_kernel_ptr<Real, DIM, kSphereHoles, MULTI>();
     if (kind == kAnnulus) return walk_kernel_ptr<Real, DIM, kAnnulus, MULTI>();
+    if (kind == kMapped) return walk_kernel_ptr<Real, DIM, kMapped, MULTI>();
     return walk_kernel_ptr<Real, DIM, kGeneric, MULTI>();
 }
 
 // Kernel kind: specialised distance for a plain disc / ball, a box, a disc /
 // ball with holes, or a disc / ball with one hole of the same centre.
-inline int walk_kind(const wos_domain &d, const wos_partition &part)
+inline int walk_kind(const wos_domain &d, const wos_partition &part, bool mapped = false)
 {
+    if (mapped)
+        return kMapped;
     if (part.voronoi_n <= 0 && d.outer_kind == WOS_OUTER_SPHERE) {
         if (d.n_holes == 0)
             return kSphereOnly;
@@ -63,12 +66,17 @@ template <typename Real>
 void fill_inst(const wos_domain &d, const wos_partition &part, const double *S,
                const double *points, int32_t M_D, uint32_t N, double eps,
                uint32_t stream_id, uint32_t k0, uint32_t k1, uint32_t step_cap,
-               uint32_t *counts, uint32_t *unterm, WalkInst<Real> *I)
+               uint32_t *counts, uint32_t *unterm, WalkInst<Real> *I, bool mapped = false)
 {
     std::memset(I, 0, sizeof(*I));
     fill_geom(d, part, I->g);
     for (int i = 0; i < 9; ++i)
         I->S[i] = i < d.dim * d.dim ? Real(S[i]) : Real(0);
+    if (mapped) {  // isotropic steps in y = S^{-1} x
+        set_mapped(d, S, I->g);
+        for (int i = 0; i < 9; ++i)
+            I->S[i] = (i < d.dim * d.dim && i % (d.dim + 1) == 0) ? Real(1) : Real(0);
+    }
     I->eps = Real(eps);
     I->stream_id = stream_id;
     I->N = N;

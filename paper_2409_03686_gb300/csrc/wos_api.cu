@@ -385,6 +385,134 @@ double fp32_floor(const wos_domain &d)
     return 128.0 * std::ldexp(1.0, -24) * m;
 }
 
+// Faces a.x <= c of the box or convex polygon D (outward unit a).
+static int polytope_faces(const wos_domain &d, double (*a)[3], double *c)
+{
+    int nf = 0;
+    if (d.outer_kind == WOS_OUTER_BOX) {
+        for (int ax = 0; ax < d.dim; ++ax)
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+                for (int b = 0; b < 3; ++b)
+                    a[nf][b] = b == ax ? double(sgn) : 0.0;
+                c[nf++] = sgn * d.center[ax] + d.half[ax];
+            }
+        return nf;
+    }
+    const int nv = d.n_vertices;
+    for (int e = 0; e < nv; ++e) {
+        const double *v0 = d.vertices + 2 * e, *v1 = d.vertices + 2 * ((e + 1) % nv);
+        const double tx = v1[0] - v0[0], ty = v1[1] - v0[1], L = std::hypot(tx, ty);
+        a[nf][0] = ty / L;
+        a[nf][1] = -tx / L;
+        a[nf][2] = 0.0;
+        c[nf++] = a[e][0] * v0[0] + a[e][1] * v0[1];
+    }
+    return nf;
+}
+
+bool mapped_supported(const wos_domain &d)
+{
+    if (d.n_holes != 0)
+        return false;
+    if (d.outer_kind == WOS_OUTER_BOX)
+        return true;
+    if (d.outer_kind != WOS_OUTER_POLYGON || d.dim != 2 || d.n_vertices > kMaxPlanes)
+        return false;
+    const int nv = d.n_vertices;
+    for (int e = 0; e < nv; ++e) {  // convex, counter-clockwise: left turns only
+        const double *p0 = d.vertices + 2 * e, *p1 = d.vertices + 2 * ((e + 1) % nv),
+                     *p2 = d.vertices + 2 * ((e + 2) % nv);
+        const double cr = (p1[0] - p0[0]) * (p2[1] - p1[1]) - (p1[1] - p0[1]) * (p2[0] - p1[0]);
+        if (!(cr > 0.0))
+            return false;
+    }
+    return true;
+}
+
+// Inverse of a symmetric positive definite d x d matrix (d <= 3), by
+// cofactors.
+static void inverse(int dim, const double *S, double *Si)
+{
+    if (dim == 2) {
+        const double det = S[0] * S[3] - S[1] * S[2];
+        Si[0] = S[3] / det; Si[1] = -S[1] / det; Si[2] = -S[2] / det; Si[3] = S[0] / det;
+        return;
+    }
+    double cof[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+            cof[i * 3 + j] = S[i1 * 3 + j1] * S[i2 * 3 + j2] - S[i1 * 3 + j2] * S[i2 * 3 + j1];
+        }
+    const double det = S[0] * cof[0] + S[1] * cof[1] + S[2] * cof[2];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            Si[i * 3 + j] = cof[j * 3 + i] / det;
+}
+
+// A face a.x <= c becomes (S a).y <= c in y = S^{-1} x (S symmetric),
+// normalised to a unit normal.
+template <typename Real>
+void set_mapped(const wos_domain &d, const double *S, Geom<Real> &g)
+{
+    const int dim = d.dim;
+    double a[kMaxPlanes][3], c[kMaxPlanes], Si[9] = {0};
+    const int nf = polytope_faces(d, a, c);
+    inverse(dim, S, Si);
+    g.mapped = 1;
+    g.np = nf;
+    for (int f = 0; f < kMaxPlanes; ++f) {
+        double m[3] = {0.0, 0.0, 0.0}, L = 0.0;
+        if (f < nf) {
+            for (int i = 0; i < dim; ++i) {
+                for (int j = 0; j < dim; ++j)
+                    m[i] += S[i * dim + j] * a[f][j];
+                L += m[i] * m[i];
+            }
+            L = std::sqrt(L);
+        }
+        for (int i = 0; i < 3; ++i)
+            g.pn[f][i] = f < nf ? Real(m[i] / L) : Real(0);
+        g.pd[f] = f < nf ? Real(c[f] / L) : Real(0);
+    }
+    for (int i = 0; i < 9; ++i) {
+        g.mS[i] = i < dim * dim ? Real(S[i]) : Real(0);
+        g.mSinv[i] = i < dim * dim ? Real(Si[i]) : Real(0);
+    }
+}
+
+template void set_mapped<float>(const wos_domain &, const double *, Geom<float> &);
+template void set_mapped<double>(const wos_domain &, const double *, Geom<double> &);
+
+// The floor of the unmapped walks over the coordinates y = S^{-1} x of D's
+// corners (the walk's own coordinates).
+double fp32_floor_mapped(const wos_domain &d, const double *S)
+{
+    const int dim = d.dim;
+    double Si[9] = {0}, m = 0.0;
+    inverse(dim, S, Si);
+    auto corner = [&](const double *x) {
+        for (int i = 0; i < dim; ++i) {
+            double y = 0.0;
+            for (int j = 0; j < dim; ++j)
+                y += Si[i * dim + j] * x[j];
+            m = std::max(m, std::fabs(y));
+        }
+    };
+    if (d.outer_kind == WOS_OUTER_BOX) {
+        for (int q = 0; q < (1 << dim); ++q) {
+            double x[3];
+            for (int a = 0; a < dim; ++a)
+                x[a] = d.center[a] + (((q >> a) & 1) ? d.half[a] : -d.half[a]);
+            corner(x);
+        }
+    } else {
+        for (int v = 0; v < d.n_vertices; ++v)
+            corner(d.vertices + 2 * v);
+    }
+    return 128.0 * std::ldexp(1.0, -24) * m;
+}
+
 }  // namespace wos
 
 extern "C" wos_status wos_conductivity_sqrt(int32_t dim, const double *K, double *S)
@@ -533,9 +661,9 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
     const int dim = d.dim;
     wos_opts o = o_in;
     apply_tuning(ctx, sizeof(Real) == sizeof(double) ? WOS_FP64 : WOS_FP32, dim,
-                 walk_kind(d, part), &o);
+                 walk_kind(d, part, o.mapped != 0), &o);
     fill_inst<Real>(d, part, S, points, M_D, N, eps, o.stream_id, o.k0, o.k1, o.step_cap,
-                    counts, unterm, &p.one);
+                    counts, unterm, &p.one, o.mapped != 0);
     philox_round_keys(seed, p.rk);
     p.trace_elem = o.trace_elem;
     p.trace_steps = o.trace_steps;
@@ -544,7 +672,8 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
 
     const uint64_t per_point = uint64_t(p.one.k1 - p.one.k0);
     WalkPlan plan;
-    wos_status pst = plan_walk_any<Real>(dim, walk_kind(d, part), M, o, ctx->sm_count,
+    wos_status pst = plan_walk_any<Real>(dim, walk_kind(d, part, o.mapped != 0), M, o,
+                                         ctx->sm_count,
                                          ctx->max_smem_optin, per_point, M_D, &plan);
     if (pst != WOS_OK) {
         delete pp;
@@ -679,7 +808,10 @@ extern "C" wos_status wos_build_operator(wos_context *ctx, const wos_domain *dom
     st = setup_S(domain->dim, K, S);
     if (st != WOS_OK)
         return st;
-    if (o.precision == WOS_FP32 && eps < fp32_floor(*domain))
+    if (o.mapped != 0 && (o.mapped != 1 || !mapped_supported(*domain)))
+        return WOS_INVALID_ARG;
+    if (o.precision == WOS_FP32 &&
+        eps < (o.mapped ? fp32_floor_mapped(*domain, S) : fp32_floor(*domain)))
         return WOS_EPS_BELOW_FP32_FLOOR;
     cudaSetDevice(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);

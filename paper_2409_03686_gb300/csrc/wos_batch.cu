@@ -47,12 +47,13 @@ wos_status launch_class(wos_context *ctx, const std::vector<int> &idx,
 {
     const int n = int(idx.size());
     // kernel kind shared by the whole class, else the generic kernel
-    int kind = walk_kind(*probs[idx[0]].domain, *probs[idx[0]].partition);
+    const bool mapped = o_in.mapped != 0;
+    int kind = walk_kind(*probs[idx[0]].domain, *probs[idx[0]].partition, mapped);
     int32_t max_M = 0;
     uint64_t total = 0;
     for (int q = 0; q < n; ++q) {
         const wos_problem &pb = probs[idx[q]];
-        if (walk_kind(*pb.domain, *pb.partition) != kind)
+        if (walk_kind(*pb.domain, *pb.partition, mapped) != kind)
             kind = kGeneric;
         max_M = std::max(max_M, num_elements(*pb.domain, *pb.partition));
         const uint32_t k1 = pb.k1 ? pb.k1 : pb.N;
@@ -110,7 +111,7 @@ wos_status launch_class(wos_context *ctx, const std::vector<int> &idx,
         WalkInst<Real> &I = recs[q];
         fill_inst<Real>(*pb.domain, *pb.partition, S[idx[q]].data(), pb.points, pb.M_D, pb.N,
                         pb.eps, pb.stream_id, pb.k0, pb.k1, pb.step_cap, pb.counts,
-                        pb.unterminated, &I);
+                        pb.unterminated, &I, mapped);
         if (pb.partition->voronoi_n > 0) {
             const size_t ns = size_t(pb.partition->voronoi_n) * DIM;
             for (size_t k = 0; k < ns; ++k)
@@ -222,9 +223,14 @@ extern "C" wos_status wos_build_operators_batched(wos_context *ctx, int32_t n,
         st = setup_S(pb.domain->dim, pb.K, S[q].data());
         if (st != WOS_OK)
             return st;
-        if (o.precision == WOS_FP32 && pb.eps < fp32_floor(*pb.domain))
+        if (o.mapped != 0 && (o.mapped != 1 || !mapped_supported(*pb.domain)))
+            return WOS_INVALID_ARG;
+        if (o.precision == WOS_FP32 &&
+            pb.eps < (o.mapped ? fp32_floor_mapped(*pb.domain, S[q].data())
+                               : fp32_floor(*pb.domain)))
             return WOS_EPS_BELOW_FP32_FLOOR;
-        by_class[pb.domain->dim - 2][walk_kind(*pb.domain, *pb.partition)].push_back(q);
+        by_class[pb.domain->dim - 2][walk_kind(*pb.domain, *pb.partition, o.mapped != 0)]
+            .push_back(q);
     }
     cudaSetDevice(ctx_device(ctx));
     cudaStream_t s = static_cast<cudaStream_t>(stream);

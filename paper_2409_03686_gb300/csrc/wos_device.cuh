@@ -29,6 +29,7 @@ namespace wos {
 
 constexpr int kMaxVerts = 64;
 constexpr int kMaxHoles = 16;
+constexpr int kMaxPlanes = 8;  // faces of a mapped polytope
 
 enum OuterKind : int32_t { kSphere = 1, kBox = 2, kPolygon = 3 };
 
@@ -101,6 +102,11 @@ template <typename Real> struct Geom {
     int32_t hole_m[kMaxHoles], hole_off[kMaxHoles];
     int32_t hole_nb[kMaxHoles], hole_ns[kMaxHoles];
     Real hole_t0[kMaxHoles]; // theta0 / (2 pi)
+    // mapped walks: the polytope S^{-1} D, dist(y) = min_f (pd[f] - pn[f] . y)
+    int32_t mapped;
+    int32_t np;
+    Real pn[kMaxPlanes][3], pd[kMaxPlanes];
+    Real mS[9], mSinv[9];    // S and S^{-1}, row-major DIM x DIM
 };
 
 // Index of the cell of t in [0, 1) split into m equal cells (clamped).

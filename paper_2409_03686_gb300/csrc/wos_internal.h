@@ -24,6 +24,13 @@ template <typename Real>
 void fill_geom(const wos_domain &d, const wos_partition &p, Geom<Real> &g);
 wos_status setup_S(int d, const double *K, double *S);
 double fp32_floor(const wos_domain &d);
+// Mapped walks: whether the domain is a polytope the kernel can map (box,
+// convex counter-clockwise polygon of <= kMaxPlanes edges, no holes); its
+// faces in y = S^{-1} x, S and S^{-1}; the FP32 floor in y.
+bool mapped_supported(const wos_domain &d);
+template <typename Real>
+void set_mapped(const wos_domain &d, const double *S, Geom<Real> &g);
+double fp32_floor_mapped(const wos_domain &d, const double *S);
 
 // Points the geometry at a Voronoi candidate grid already on the device.
 template <typename Real, typename Grid>

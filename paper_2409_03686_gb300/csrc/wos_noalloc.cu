@@ -79,9 +79,9 @@ wos_status build_noalloc(wos_context *ctx, unsigned char *scratch, const wos_dom
     const int dim = d.dim;
     wos_opts o = o_in;
     apply_tuning(ctx, sizeof(Real) == sizeof(double) ? WOS_FP64 : WOS_FP32, dim,
-                 walk_kind(d, part), &o);
+                 walk_kind(d, part, o.mapped != 0), &o);
     fill_inst<Real>(d, part, S, points, M_D, N, eps, o.stream_id, o.k0, o.k1, o.step_cap,
-                    counts, unterm, &p.one);  // points_r stays null: converted per walk
+                    counts, unterm, &p.one, o.mapped != 0);  // points_r null: per walk
     philox_round_keys(seed, p.rk);
     p.trace_elem = o.trace_elem;
     p.trace_steps = o.trace_steps;
@@ -89,7 +89,8 @@ wos_status build_noalloc(wos_context *ctx, unsigned char *scratch, const wos_dom
     const int32_t M = p.one.g.M_tot;
 
     WalkPlan plan;
-    wos_status pst = plan_walk_any<Real>(dim, walk_kind(d, part), M, o, ctx_sm_count(ctx),
+    wos_status pst = plan_walk_any<Real>(dim, walk_kind(d, part, o.mapped != 0), M, o,
+                                         ctx_sm_count(ctx),
                                          ctx_max_smem(ctx), uint64_t(p.one.k1 - p.one.k0),
                                          M_D, &plan);
     if (pst != WOS_OK)
@@ -188,7 +189,10 @@ extern "C" wos_status wos_build_operator_noalloc(
     st = setup_S(domain->dim, K, S);
     if (st != WOS_OK)
         return st;
-    if (o.precision == WOS_FP32 && eps < fp32_floor(*domain))
+    if (o.mapped != 0 && (o.mapped != 1 || !mapped_supported(*domain)))
+        return WOS_INVALID_ARG;
+    if (o.precision == WOS_FP32 &&
+        eps < (o.mapped ? fp32_floor_mapped(*domain, S) : fp32_floor(*domain)))
         return WOS_EPS_BELOW_FP32_FLOOR;
     const int dev = ctx_device(ctx);
     if (cudaSetDevice(dev) != cudaSuccess)

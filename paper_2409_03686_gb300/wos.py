@@ -90,6 +90,7 @@ class WosOpts(ctypes.Structure):
         ("trace_steps", ctypes.c_void_p),
         ("trace_x", ctypes.c_void_p),
         ("kernel_events", ctypes.c_void_p * 2),
+        ("mapped", ctypes.c_int32),
     ]
 
 
@@ -408,7 +409,7 @@ def make_opts(precision: int = 0, step_cap: int = 0, stream_id: int = 0, k0: int
               blocks_per_sm: int = 0, tile_walks: int = 0, hist_slots: int = 0,
               refill_min: int = 0, tiles_per_warp: int = 0,
               trace_elem=None, trace_steps=None, trace_x=None,
-              kernel_events=None) -> WosOpts:
+              kernel_events=None, mapped: bool = False) -> WosOpts:
     o = WosOpts()
     o.precision = precision
     o.step_cap = step_cap
@@ -427,6 +428,7 @@ def make_opts(precision: int = 0, step_cap: int = 0, stream_id: int = 0, k0: int
     if kernel_events is not None:
         for q, ev in enumerate(kernel_events):
             o.kernel_events[q] = ev.cuda_event
+    o.mapped = int(mapped)
     return o
 
 
@@ -523,6 +525,8 @@ def wos_build_operators_batched(ctx: Context, insts, seed: int, points=None,
         pb.step_cap = 0 if inst.step_cap == 1_000_000 else int(inst.step_cap)
         pb.counts = counts[q].data_ptr()
         pb.unterminated = unterminated[q].data_ptr()
+    if opts is None and any(getattr(i, "mapped", False) for i in insts):
+        opts = make_opts(mapped=True)
     st = WosStats() if stats else None
     code = L.wos_build_operators_batched(ctx.h, len(insts), ctypes.byref(probs), int(seed),
                                          ctypes.byref(opts) if opts is not None else None,
@@ -712,7 +716,7 @@ def solve_instance(ctx: Context, inst, uD, u0, r: int, points=None, sigma=None,
                                 dtype=torch.float64, device=dev)
     if opts is None:
         opts = make_opts(precision=1 if inst.fp64 else 0, stream_id=inst.stream,
-                         step_cap=inst.step_cap)
+                         step_cap=inst.step_cap, mapped=getattr(inst, "mapped", False))
     counts, unterm, st = wos_build_operator(ctx, inst.domain, inst.K, points,
                                             inst.partition, inst.N, inst.eps, inst.seed,
                                             opts=opts, stats=stats, stream=stream)

@@ -32,7 +32,8 @@ def gpu_build(inst, trace=True, trace_steps=False, trace_x=False, **kw):
     opts = wos.make_opts(precision=1 if inst.fp64 else 0, stream_id=inst.stream,
                          step_cap=inst.step_cap if inst.step_cap != 1_000_000 else 0,
                          k0=k0, k1=k1 if k1 != inst.N or k0 else 0,
-                         trace_elem=tr, trace_steps=ts, trace_x=tx, **kw)
+                         trace_elem=tr, trace_steps=ts, trace_x=tx,
+                         mapped=getattr(inst, "mapped", False), **kw)
     c, u, st = wos.wos_build_operator(ctx(), inst.domain, inst.K, pts, inst.partition,
                                       inst.N, inst.eps, inst.seed, opts=opts,
                                       counts=counts, unterminated=unterm)

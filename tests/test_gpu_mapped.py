@@ -1,0 +1,64 @@
+"""Mapped walks on the GPU (walk-on-spheres in y = S^{-1} x, exact distance to
+the polytope S^{-1} D): exits agree walk by walk with the oracle's mapped
+chain, batched equals lone, the chain needs far fewer steps than the paper's
+for anisotropic K, and unsupported domains are rejected."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import ctx, gpu_build, oracle_walks
+from paper_2409_03686_gb300 import workloads as W
+from paper_2409_03686_gb300 import wos
+from test_oracle_mapped import K_RAND3, _hexagon
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "square": lambda: W.square_config(N=600, grid=8),
+    "cube_diag": lambda: W.cube_config(N=400, n_points=40),
+    "cube_rand": lambda: W.cube_config(N=400, n_points=40, K=K_RAND3),
+    "hexagon": lambda: _hexagon(N=600).replace(eps=1e-4),
+    "square64": lambda: W.square_config(N=300, grid=4).replace(fp64=True, eps=1e-8),
+    "cube64": lambda: W.cube_config(N=200, n_points=16, K=K_RAND3).replace(fp64=True,
+                                                                            eps=1e-8),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mapped_walks_match_oracle(name):
+    inst = CASES[name]().replace(mapped=True)
+    r = gpu_build(inst, trace_steps=True)
+    assert (r["counts"].sum(1) + r["unterm"] == inst.N).all()
+    el, ns, _ = oracle_walks(inst)
+    agree = (r["trace"] == el).mean()
+    assert agree >= 0.999, (name, agree)
+    assert (r["steps"] == ns).mean() >= 0.999
+
+
+def test_mapped_batch_equals_lone_builds():
+    insts = [CASES["square"]().replace(mapped=True, stream=1, seed=7),
+             CASES["cube_rand"]().replace(mapped=True, stream=2, seed=7),
+             CASES["hexagon"]().replace(mapped=True, stream=3, seed=7)]
+    counts, _, _ = wos.wos_build_operators_batched(ctx(), insts, seed=7)
+    torch.cuda.synchronize()
+    for q, inst in enumerate(insts):
+        lone = gpu_build(inst, trace=False)
+        np.testing.assert_array_equal(counts[q].cpu().numpy().astype(np.int64),
+                                      lone["counts"], err_msg=inst.name)
+
+
+def test_mapped_chain_takes_fewer_steps():
+    for make in (lambda: W.square_config(N=20_000, grid=8),
+                 lambda: W.cube_config(N=5_000, n_points=64)):
+        inst = make()
+        a = gpu_build(inst, trace=False)["stats"]
+        b = gpu_build(inst.replace(mapped=True), trace=False)["stats"]
+        assert b["steps"] < 0.6 * a["steps"], (inst.name, a["steps"], b["steps"])
+
+
+def test_unsupported_domains_are_rejected():
+    for inst in (W.annulus_config(N=100, grid=2), W.lshape_config(N=100, n_points=4),
+                 W.square_hole_config(N=100, eps=1e-5, n_points=4, fp64=False)):
+        with pytest.raises(wos.WosError) as e:
+            gpu_build(inst.replace(mapped=True), trace=False)
+        assert e.value.code == 1
