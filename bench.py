@@ -150,18 +150,21 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # CPU oracle (the baseline and the reference arm)
 # ----------------------------------------------------------------------------
-def oracle_sample(insts, n_points: int, n_walks: int):
+def oracle_sample(insts, n_points: int, n_walks: int, passes: int = 1):
     """Times the oracle's MC-REM on the first n_points points with n_walks
-    walks each, for every instance; returns (walks, steps, seconds)."""
+    walks each, for every instance, `passes` times with independent walks
+    (another Philox stream per pass); returns (walks, steps, seconds)."""
     from oracle import oracle as O
     O.build()
     walks = steps = 0
     t0 = time.perf_counter()
-    for inst in insts:
-        sub = inst.replace(points=inst.points[:n_points], N=n_walks)
-        C, U, s = O.build_counts(sub)
-        walks += sub.M_D * sub.N
-        steps += s
+    for ps in range(passes):
+        for inst in insts:
+            sub = inst.replace(points=inst.points[:n_points], N=n_walks,
+                               stream=inst.stream + 1000 * ps)
+            C, U, s = O.build_counts(sub)
+            walks += sub.M_D * sub.N
+            steps += s
     return walks, steps, time.perf_counter() - t0
 
 
@@ -477,12 +480,14 @@ def run_gpu(args, rank: int, world: int, dist):
         "clocks": clk,
     }
     if not args.no_cpu_baseline and world == 1:
-        n_pts, n_walks = 32, 100_000
-        w, s, dt = oracle_sample([p["inst"] for p in prep], n_pts, n_walks)
+        insts = [p["inst"] for p in prep]
+        n_pts, n_walks = insts[0].M_D, insts[0].N
+        w, s, dt = oracle_sample(insts, n_pts, n_walks, passes=2)
         line["cpu_baseline"] = {
             "value": w / dt, "unit": "walks/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"first {n_pts} points x {n_walks} walks of each instance "
-                      f"({w} walks, {dt:.1f} s, FP64 C oracle)"}
+            "sample": f"the whole workload (all {n_pts} points x {n_walks} walks of both "
+                      f"instances) twice with independent walks: {w} walks, {dt:.1f} s, "
+                      f"FP64 C oracle on {os.cpu_count()} threads"}
     print(json.dumps(line))
 
 
