@@ -255,6 +255,11 @@ def run_gpu(args, rank: int, world: int, dist):
 
     streams = [torch.cuda.Stream(device=dev) for _ in prep]
     build_stream = torch.cuda.Stream(device=dev)
+    # the project's autotuner picks the launch configuration of each
+    # instance's class (precision, dimension, kernel kind) on a bounded sample
+    # of its walks, before anything is timed; later builds use it
+    tunings = {inst_p["inst"].name: wos.wos_autotune(ctx, inst_p["inst"])
+               for inst_p in prep}
     # warm-up: truncation ranks from the spectra, step counts from stats
     steps_per_inst = []
     for p in prep:
@@ -474,6 +479,9 @@ def run_gpu(args, rank: int, world: int, dist):
         "device_ms_per_step": {"walk_kernels": walk_ms_sum, "jacobi_kernel": jac_ms,
                                "svd_call": svd_ms_sum},
         "gpu_launches": int(launches),
+        "autotuned": {k: {f: v[f] for f in ("block_size", "blocks_per_sm", "tiles_per_warp",
+                                             "hist_slots", "refill_min", "best_ms",
+                                             "default_ms")} for k, v in tunings.items()},
         "wall_s_timed": wall,
         "e2e": {"value": e2e_value, "unit": "walks/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},

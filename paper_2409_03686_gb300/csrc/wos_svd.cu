@@ -30,6 +30,11 @@ namespace {
 
 constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr double kTol = 1e-15;
+// A sweep whose pairs all had |cos| = |w_p . w_q| / (|w_p| |w_q|) <= kLast
+// rotated by angles that small; the cyclic sweep's quadratic convergence
+// leaves every cosine at O(kLast^2) = 1e-18 after it, below kTol, so no
+// verifying sweep without rotations follows it.
+constexpr double kLast = 1e-9;
 constexpr int kMaxSweeps = 80;
 constexpr int kPairThreads = 128;
 static_assert(kPairThreads == 128, "the partial sums below assume four warps");
@@ -40,7 +45,8 @@ struct SvdWork {
     int m, n;         // worked orientation, m >= n
     int n_pad;        // n rounded up to even (a dummy column when odd)
     unsigned *bar;    // [0] arrive count, [1] generation, [2..4] rotation
-                      // counters of sweeps mod 3, [5] status, [6] sweeps
+                      // counters of sweeps mod 3, [5] status, [6] sweeps,
+                      // [8..13] largest cos^2 of sweeps mod 3 (3 x uint64)
     unsigned *ver;    // n_pad column versions (rounds finished per column)
 };
 
@@ -184,10 +190,14 @@ __device__ void jacobi_body(const SvdWork &w, const int bid, const int nblk)
     const int half = w.n_pad / 2;
     const int m = w.m, n = w.n;
     unsigned *status = w.bar + 5;
+    unsigned long long *maxcos = reinterpret_cast<unsigned long long *>(w.bar + 8);
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
         unsigned *rot = w.bar + 2 + (sweep % 3);
-        if (bid == 0 && tid == 0)
+        if (bid == 0 && tid == 0) {
             w.bar[2 + ((sweep + 1) % 3)] = 0u;
+            maxcos[(sweep + 1) % 3] = 0ull;
+        }
+        double my_cos2 = 0.0;  // largest cos^2 this CTA met in the sweep (thread 0)
         for (int r = 0; r < w.n_pad - 1; ++r) {
             const unsigned R = unsigned(sweep) * unsigned(w.n_pad - 1) + unsigned(r);
             for (int pr = bid; pr < half; pr += nblk) {
@@ -245,6 +255,7 @@ __device__ void jacobi_body(const SvdWork &w, const int bid, const int nblk)
                         if (al != 0.0 && be != 0.0 && ga * ga > (kTol * kTol) * (al * be)) {
                             jacobi_rotation(al, be, ga, c, sn);
                             rot_flag = 1;
+                            my_cos2 = fmax(my_cos2, (ga * ga) / (al * be));
                         }
                         cs[0] = c;
                         cs[1] = sn;
@@ -292,9 +303,13 @@ __device__ void jacobi_body(const SvdWork &w, const int bid, const int nblk)
                 }
             }
         }
+        if (tid == 0 && my_cos2 > 0.0)  // non-negative doubles order like their bits
+            atomicMax(maxcos + (sweep % 3), __double_as_longlong(my_cos2));
         if (!grid_barrier(w.bar, unsigned(nblk)))
             return;
-        bool done = *(volatile unsigned *)rot == 0u;
+        const double sweep_cos2 =
+            __longlong_as_double(*(volatile long long *)(maxcos + (sweep % 3)));
+        bool done = *(volatile unsigned *)rot == 0u || sweep_cos2 <= kLast * kLast;
         if (bid == 0 && tid == 0)
             w.bar[6] = unsigned(sweep + 1);
         if (done)
