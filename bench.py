@@ -258,8 +258,8 @@ def run_gpu(args, rank: int, world: int, dist):
     # the project's autotuner picks the launch configuration of each
     # instance's class (precision, dimension, kernel kind) on a bounded sample
     # of its walks, before anything is timed; later builds use it
-    tunings = {inst_p["inst"].name: wos.wos_autotune(ctx, inst_p["inst"])
-               for inst_p in prep}
+    tunings = ({inst_p["inst"].name: wos.wos_autotune(ctx, inst_p["inst"])
+                for inst_p in prep} if not args.no_autotune else {})
     # warm-up: truncation ranks from the spectra, step counts from stats
     steps_per_inst = []
     for p in prep:
@@ -761,6 +761,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="square-annulus")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="default launch configuration (profiling: no trial launches)")
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="walks-per-point scale of the batch workload")
     ap.add_argument("--serve-requests", type=int, default=128,
