@@ -203,6 +203,15 @@ def run_reference(args, rank: int, world: int):
 # ----------------------------------------------------------------------------
 # the GPU arm
 # ----------------------------------------------------------------------------
+SVD_PATHS = {"auto": 0, "grid": 1}
+
+
+def qr_flop(m: int, n: int) -> int:
+    """FP64 flop of the Householder QR of an m x n matrix (m >= n): 2mn^2 -
+    2n^3/3 (the column-pivoting norm updates are O(mn))."""
+    return 2 * m * n * n - (2 * n ** 3) // 3
+
+
 def jacobi_flop(m: int, n: int, sweeps: int) -> int:
     """FP64 flop of the Jacobi sweeps of one SVD of an m x n worked matrix
     (m >= n) as the library runs it (on X = R^T, n x n, when n >= 32): every
@@ -233,6 +242,7 @@ def run_gpu(args, rank: int, world: int, dist):
     from paper_2409_03686_gb300 import build as B
     B.build()
     ctx = wos.Context(local)
+    wos.wos_set_svd_path(ctx, SVD_PATHS[args.svd_path])
     stream = torch.cuda.current_stream()
     insts = workload(args.workload)
     prep = []
@@ -424,19 +434,24 @@ def run_gpu(args, rank: int, world: int, dist):
     svd_ms_sum = float(np.mean([sum(a.elapsed_time(b) for (a, b) in row) for row in sev]))
     jac_ms = float(np.mean([a.elapsed_time(b) for (a, b) in jev]))
     walk_ms_sum = float(np.mean([sum(a.elapsed_time(b) for (a, b) in row) for row in kev]))
-    flop = sum(jacobi_flop(p["svd_mn"][0], p["svd_mn"][1], p["sweeps"]) for p in prep)
+    flop = sum(jacobi_flop(p["svd_mn"][0], p["svd_mn"][1], p["sweeps"]) +
+               (qr_flop(*p["svd_mn"]) if p["svd_mn"][1] >= 32 else 0) for p in prep)
     svd_achieved = flop / (jac_ms / 1e3) / 1e9
-    svd_roof = {"kernel": "jacobi_kernel", "bound": "fp64", "achieved": svd_achieved,
+    svd_roof = {"kernel": ("svd_cluster_kernel" if args.svd_path == "auto" and
+                           all(p["svd_mn"][1] <= 256 for p in prep)
+                           else "qrcp_kernel + jacobi_kernel"),
+                "bound": "fp64", "achieved": svd_achieved,
                 "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "frac": svd_achieved / FP64_PEAK_GFLOPS, "traffic": None,
                 "peak_source": "152 SMs x 2 FP64 FMA/clk (ncu dfma peak_sustained 304 "
                                "per chip) x 2 flop x 2070 MHz",
-                "unit_of_work": "one pair visit of a sweep: 12 l + 6n flop (l = rows of the "
-                                "matrix Jacobi works on: n after the QR preconditioning, m "
-                                "without; every visit counted as rotated)",
+                "unit_of_work": "one factorisation: the pivoted Householder QR (2mn^2 - "
+                                "2n^3/3 flop, n >= 32) and every pair visit of every sweep "
+                                "(12 l + 6n flop, l = rows of the matrix Jacobi works on: n "
+                                "after the QR, m without; every visit counted as rotated)",
                 "sweeps": [p["sweeps"] for p in prep],
                 "problems_per_launch": len(prep),
-                "ms_per_launch": jac_ms,
+                "ms_per_step": jac_ms,
                 "svd_call_ms": svd_ms_sum}
     # the kernel with the larger device time per step is the dominant one
     if jac_ms > walk_ms_sum:
@@ -476,7 +491,7 @@ def run_gpu(args, rank: int, world: int, dist):
         "truncation_r": [p["r"] for p in prep],
         "roofline": roof,
         "roofline_secondary": roof2,
-        "device_ms_per_step": {"walk_kernels": walk_ms_sum, "jacobi_kernel": jac_ms,
+        "device_ms_per_step": {"walk_kernels": walk_ms_sum, "svd_factorisation": jac_ms,
                                "svd_call": svd_ms_sum},
         "gpu_launches": int(launches),
         "autotuned": {k: {f: v[f] for f in ("block_size", "blocks_per_sm", "tiles_per_warp",
@@ -513,6 +528,7 @@ def run_batch(args, rank: int, world: int, dist):
     dev = torch.device("cuda", local)
     B.build()
     ctx = wos.Context(local)
+    wos.wos_set_svd_path(ctx, SVD_PATHS[args.svd_path])
     insts = W.mixed_batch(64, scale=args.batch_scale)
     pts = [torch.as_tensor(i.points, dtype=torch.float64, device=dev) for i in insts]
     walks = sum(i.M_D * i.N for i in insts)
@@ -618,6 +634,7 @@ def run_serve(args, rank: int, world: int, dist):
     dev = torch.device("cuda", local)
     B.build()
     ctx = wos.Context(local)
+    wos.wos_set_svd_path(ctx, SVD_PATHS[args.svd_path])
     reqs = W.serve_stream(first=args.serve_requests)
     seed = reqs[0].inst.seed
     meas = [W.measurements(r.inst, noise=r.noise, seed=r.index) for r in reqs]
@@ -753,6 +770,72 @@ def run_serve(args, rank: int, world: int, dist):
     }))
 
 
+def run_svd(args, rank: int, world: int, dist):
+    """The FP64 SVD alone (QR preconditioning + Jacobi on R^T + left vectors)
+    on seeded operator-shaped count matrices of the two operator sizes of
+    the paper's 2-D experiments (M_D x M_1 = 256 x 128 and 1024 x 768),
+    one wos_op_svd call per shape per step.  factorisation = the QR with
+    pivoting and the Jacobi sweeps (the cluster kernel, or the grid-wide
+    QR, X and Jacobi launches)."""
+    import torch
+    from paper_2409_03686_gb300 import build as B
+    from paper_2409_03686_gb300 import workloads as W
+    from paper_2409_03686_gb300 import wos
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    ctx = wos.Context(local)
+    wos.wos_set_svd_path(ctx, SVD_PATHS[args.svd_path])
+    N = 100_000
+    shapes = [(256, 256, 128), (1024, 1536, 768)]
+    probs = []
+    for M_D, M_tot, M_1 in shapes:
+        C = torch.as_tensor(W.synthetic_counts(M_D, M_tot, N, seed=M_D).astype(np.int32),
+                            device=dev)
+        g1 = np.zeros(M_tot, np.uint8)
+        g1[:M_1] = 1
+        sg = torch.full((M_tot,), 2 * np.pi / M_tot, dtype=torch.float64, device=dev)
+        probs.append((C, N, g1, sg))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in probs]
+    for e in evs:  # create the events; the library re-records e[1], e[2]
+        for x in e:
+            x.record()
+    res = [dict(call=[], jac=[], sweeps=0) for _ in probs]
+    for it in range(args.warmup + args.steps):
+        for q, pb in enumerate(probs):
+            e = evs[q]
+            torch.cuda.synchronize()
+            e[0].record()
+            out = wos.wos_op_svd_batched(ctx, [pb], jacobi_events=(e[1], e[2]))
+            e[3].record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                res[q]["call"].append(e[0].elapsed_time(e[3]))
+                res[q]["jac"].append(e[1].elapsed_time(e[2]))
+            res[q]["sweeps"] = out[0][3]
+    if rank != 0:
+        return
+    per = []
+    for (M_D, M_tot, M_1), r in zip(shapes, res):
+        call, jac = float(np.median(r["call"])), float(np.median(r["jac"]))
+        fl = jacobi_flop(M_D, M_1, r["sweeps"]) + qr_flop(M_D, M_1)
+        per.append({"shape": f"{M_D}x{M_1}", "ms_per_call": call, "factorisation_ms": jac,
+                    "sweeps": r["sweeps"], "factorisation_gflops": fl / jac / 1e6,
+                    "factorisation_frac_fp64_peak": fl / jac / 1e6 / FP64_PEAK_GFLOPS})
+    total = sum(p["ms_per_call"] for p in per)
+    print(json.dumps({
+        "metric": "fp64_svd_ms", "value": total, "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "svd_path": args.svd_path,
+        "config": {"workload": "FP64 SVD of seeded operator-shaped counts, 256x128 and "
+                               "1024x768 (M_D x M_1), N = 1e5, one call per shape per step"},
+        "per_shape": per,
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -761,6 +844,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="square-annulus")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--svd-path", choices=list(SVD_PATHS), default="auto",
+                    help="SVD factorisation kernels: auto (cluster kernel when the "
+                         "operator fits it) or grid (grid-wide kernels)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default launch configuration (profiling: no trial launches)")
     ap.add_argument("--batch-scale", type=float, default=1.0,
@@ -786,6 +872,8 @@ def main():
         run_batch(args, rank, world, dist)
     elif args.workload == "serve":
         run_serve(args, rank, world, dist)
+    elif args.workload == "svd":
+        run_svd(args, rank, world, dist)
     else:
         run_gpu(args, rank, world, dist)
     if dist is not None:

@@ -135,6 +135,12 @@ typedef struct {
                             dist_x <= eps); exits classified in x.  Boxes and
                             convex counter-clockwise polygons of at most 8
                             edges without holes, else WOS_INVALID_ARG */
+    int32_t group_blocks; /* Philox blocks per group of steps (0 = about 16
+                            steps, at most 16 blocks): a group is
+                            group_blocks x (4 / words per step) steps, the
+                            lanes whose walk ended are refilled once per
+                            group; results do not depend on it (the counter
+                            of step n is n / steps per block) */
 } wos_opts;
 
 /* Per-build statistics (filled after the build's device work finished). */
@@ -283,6 +289,7 @@ wos_status wos_build_operators_batched(wos_context *ctx, int32_t n,
 /* A launch configuration chosen by wos_autotune. */
 typedef struct {
     int32_t block_size, blocks_per_sm, tiles_per_warp, hist_slots, refill_min;
+    int32_t group_blocks;
     int32_t trials;        /* configurations timed */
     float best_ms;         /* walk-kernel time of the sample, best config */
     float default_ms;      /* the same with the built-in defaults */
@@ -427,7 +434,27 @@ wos_status wos_op_svd_batched(wos_context *ctx, int32_t n,
                               const wos_svd_problem *problems, int32_t *sweeps,
                               void *stream, void *const *jacobi_events);
 /* jacobi_events: NULL, or two cudaEvent_t recorded on the stream before the
- * first and after the last Jacobi launch (for profiling). */
+ * first and after the last factorisation launch (the QR with pivoting and
+ * the Jacobi sweeps; for profiling). */
+
+/* Which kernels factor an SVD problem (a setting of the context, read by
+ * wos_op_svd, wos_op_svd_batched and the serving queue):
+ *   WOS_SVD_AUTO     the cluster kernel when the worked matrix fits it (at
+ *                    most 256 columns and the shared memory of the cluster),
+ *                    else the grid-wide kernels (default);
+ *   WOS_SVD_GRID     always the grid-wide kernels (cooperative QR and Jacobi
+ *                    launches synchronised through global memory);
+ *   WOS_SVD_CLUSTER  as AUTO (a problem that does not fit still runs on the
+ *                    grid-wide kernels).
+ * The cluster kernel factors one problem in one thread-block cluster of up
+ * to 16 CTAs: the matrix stays in distributed shared memory and the Jacobi
+ * rounds are ordered by cluster barriers.  Both compute the same
+ * factorisation (QR with column pivoting, then one-sided Jacobi on R^T in
+ * the same round-robin order) with different summation orders, so their
+ * results agree to rounding, not bit for bit; each is deterministic.
+ * Errors: WOS_INVALID_ARG (unknown path or NULL ctx). */
+enum { WOS_SVD_AUTO = 0, WOS_SVD_GRID = 1, WOS_SVD_CLUSTER = 2 };
+wos_status wos_set_svd_path(wos_context *ctx, int32_t path);
 
 /* r-TSVD reconstruction (paper Sec. 2, Eq. (u1r); Sec. 4.3, Eq.
  * (u_omega_M1_r_MC A); Sec. 5.1, Rem. (b and u0 simulations), Eq. (tsvd

@@ -1,0 +1,459 @@
+// svd_cluster.cuh -- the SVD of one small operator inside one thread-block
+// cluster (included by wos_svd.cu after SvdWork, QrWork and the Jacobi
+// helpers).
+//
+// Same mathematics as the grid-wide kernels of wos_svd.cu (Householder QR
+// with column pivoting, Drmac & Veselic's preconditioning, one-sided
+// Jacobi in the round-robin order with the relative rotation test and the
+// early stop after a sweep of tiny angles), but the whole factorisation
+// lives in the distributed shared memory of a cluster of up to 16 CTAs (one
+// SM each): columns move between CTAs with shared::cluster stores and the
+// rounds are ordered by hardware cluster barriers, so a round costs shared-
+// memory latencies instead of L2 round trips, a release fence and flag
+// polling.  Used when the worked matrix fits (n <= 256 columns).
+//
+//  * QR (preconditioned path): CTA c owns the physical columns j = c (mod
+//    CL).  Per pivot k every CTA pushes its largest remaining squared norm to
+//    every CTA (double buffered by pivot parity), one cluster barrier, every
+//    CTA takes the same argmax pc (lowest index on ties), reads column pc from
+//    its owner and forms the same reflector (xLARFG's beta, tau, v) in the
+//    same arithmetic order; it then applies it to its own columns (one warp
+//    per column) and downdates their norms (xLAQP2's test).  The owner writes
+//    the reflector into column pc only after the next barrier, when nobody
+//    reads the raw column any more.
+//  * X = R^T goes to the Jacobi buffers: column i of X (row i of R) starts at
+//    round-robin position i.
+//  * Jacobi: one warp per pair; CTA c holds the pairs [c PP, (c + 1) PP) of
+//    the round, each pair's two columns (X and V_X rows) in a slot of a
+//    double-buffered array.  After rotating, the warp stores each column into
+//    the slot of the position it takes in the next round (the circle method
+//    moves every column but the first by one position), then the cluster
+//    barrier.  Sweep statistics (rotations, and whether a rotated pair had
+//    cos^2 > kLast^2: a comparison, no division on the FP64 pipe, which a
+//    warp instruction occupies for 64 cycles whatever its active lanes) are
+//    stored by every warp in its own CTA and read by every warp of the
+//    cluster after the sweep's last barrier.
+#pragma once
+
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
+constexpr int kClThreads = 256;
+constexpr int kClWarps = kClThreads / 32;
+constexpr int kClMaxCtas = 16;
+constexpr int kClMaxN = 2 * kClMaxCtas * kClWarps;  // 256 columns
+
+struct ClusterJob {
+    double *A;       // m x n column-major: W on entry; (pre) R and reflectors
+    int m, n;        // worked orientation, m >= n
+    int pre;         // 1: QR with pivoting, Jacobi on X = R^T
+    double *tau;     // n reflector scalars (pre)
+    int *perm;       // n: physical column of pivot k (pre)
+    double *X;       // out: final columns of the matrix Jacobi worked on
+                     // (n x n when pre, else m x n; may alias A when not pre)
+    double *V;       // out: n x n accumulated rotations
+    unsigned *bar;   // [5] status, [6] sweeps
+};
+
+// Shared-memory layout of one CTA (bytes, 16-byte aligned pieces).
+struct ClLayout {
+    int CL, PP, cpc, nX, n_pad, half;
+    size_t small, qcol, vbuf, jb, total;
+};
+
+__host__ __device__ inline size_t cl_align(size_t b) { return (b + 15) / 16 * 16; }
+
+__host__ __device__ inline ClLayout cl_layout(int m, int n, int pre, int CL)
+{
+    ClLayout L;
+    L.CL = CL;
+    L.n_pad = n + (n & 1) < 2 ? 2 : n + (n & 1);
+    L.half = L.n_pad / 2;
+    L.PP = (L.half + CL - 1) / CL;
+    L.cpc = pre ? (n + CL - 1) / CL : 0;
+    L.nX = pre ? n : m;
+    // small: pub_val[2][16] double, pub_idx[2][16] int, tau_all[n] double,
+    // perm_all[n] int, cn[cpc], cn0[cpc] double, flags[cpc] int (done, or
+    // pivot position + 1), sweep statistics of the warps [2][kClWarps],
+    // block-sum scratch
+    size_t s = 0;
+    s += cl_align(2 * 16 * 8) + cl_align(2 * 16 * 4);
+    s += cl_align(size_t(n) * 8) + cl_align(size_t(n) * 4);
+    s += 2 * cl_align(size_t(L.cpc) * 8) + cl_align(size_t(L.cpc) * 4);
+    s += cl_align(2 * kClWarps * 4) + cl_align(64 * 8);
+    L.small = s;
+    L.qcol = pre ? cl_align(size_t(L.cpc) * m * 8) : 0;
+    L.vbuf = pre ? cl_align(size_t(m) * 8) : 0;
+    L.jb = cl_align(size_t(2) * 2 * L.PP * (L.nX + n) * 8);
+    L.total = L.small + L.qcol + L.vbuf + L.jb;
+    return L;
+}
+
+// CTA and slot of round-robin position pos: pair pr = pos (top) or
+// n_pad - 1 - pos (bottom); CTA pr / PP, slot 2 (pr mod PP) + (bottom).
+__device__ __forceinline__ void cl_where(int pos, const ClLayout &L, int &cta, int &slot)
+{
+    const bool top = pos < L.half;
+    const int pr = top ? pos : L.n_pad - 1 - pos;
+    cta = pr / L.PP;
+    slot = 2 * (pr - cta * L.PP) + (top ? 0 : 1);
+}
+
+// Position in the next round of the column at position pos (circle method:
+// position 0 fixed, 1 -> n_pad - 1, every other one down by one).
+__device__ __forceinline__ int cl_next(int pos, int n_pad)
+{
+    return pos == 0 ? 0 : (pos == 1 ? n_pad - 1 : pos - 1);
+}
+
+// Sum over the block, the same value (and the same arithmetic order) in
+// every thread.
+__device__ double cl_block_sum(double v, double *red)
+{
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+        red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kClWarps; ++q)
+        s += red[q];
+    return s;
+}
+
+__global__ void __launch_bounds__(kClThreads)
+svd_cluster_kernel(const ClusterJob *jobs, int CL)
+{
+    cg::cluster_group cluster = cg::this_cluster();
+    const ClusterJob J = jobs[blockIdx.x / CL];
+    const int c = int(cluster.block_rank());
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int m = J.m, n = J.n, pre = J.pre;
+    const ClLayout L = cl_layout(m, n, pre, CL);
+    extern __shared__ __align__(16) unsigned char cl_smem[];
+    unsigned char *sp = cl_smem;
+    auto carve = [&](size_t b) { unsigned char *r = sp; sp += cl_align(b); return r; };
+    double *pub_val = reinterpret_cast<double *>(carve(2 * 16 * 8));
+    int *pub_idx = reinterpret_cast<int *>(carve(2 * 16 * 4));
+    double *tau_all = reinterpret_cast<double *>(carve(size_t(n) * 8));
+    int *perm_all = reinterpret_cast<int *>(carve(size_t(n) * 4));
+    double *cn = reinterpret_cast<double *>(carve(size_t(L.cpc) * 8));
+    double *cn0 = reinterpret_cast<double *>(carve(size_t(L.cpc) * 8));
+    int *cflag = reinterpret_cast<int *>(carve(size_t(L.cpc) * 4));
+    unsigned *swstat = reinterpret_cast<unsigned *>(carve(2 * kClWarps * 4));
+    double *red = reinterpret_cast<double *>(carve(64 * 8));
+    sp = cl_smem + L.small;
+    double *qcol = reinterpret_cast<double *>(sp);
+    double *vbuf = reinterpret_cast<double *>(sp + L.qcol);
+    double *jb = reinterpret_cast<double *>(sp + L.qcol + L.vbuf);
+    const int slot_len = L.nX + n;
+    const size_t buf_len = size_t(2) * L.PP * slot_len;
+
+    // ---- QR with column pivoting ------------------------------------------
+    if (pre) {
+        const int nown = c < n ? (n - c + CL - 1) / CL : 0;
+        for (int t = warp; t < nown; t += kClWarps) {
+            const double *g = J.A + size_t(c + t * CL) * m;
+            double *col = qcol + size_t(t) * m;
+            double s = 0.0;
+            for (int i = lane; i < m; i += 32) {
+                const double v = g[i];
+                col[i] = v;
+                s = fma(v, v, s);
+            }
+            s = warp_sum(s);
+            if (lane == 0) {
+                cn[t] = s;
+                cn0[t] = s;
+                cflag[t] = 0;
+            }
+        }
+        __syncthreads();
+        int pend_t = -1, pend_k = 0;  // owner's reflector still to be stored
+        double pend_beta = 0.0;
+        for (int k = 0; k < n; ++k) {
+            // push this CTA's largest remaining norm to every CTA
+            if (tid < CL) {
+                double bv = -1.0;
+                int bi = -1;
+                for (int t = 0; t < nown; ++t)
+                    if (cflag[t] == 0 && cn[t] > bv) {
+                        bv = cn[t];
+                        bi = c + t * CL;
+                    }
+                double *rv = cluster.map_shared_rank(pub_val, tid);
+                int *ri = cluster.map_shared_rank(pub_idx, tid);
+                rv[(k & 1) * 16 + c] = bv;
+                ri[(k & 1) * 16 + c] = bi;
+            }
+            cluster.sync();
+            if (pend_t >= 0) {  // the previous pivot's reflector, now unread
+                double *col = qcol + size_t(pend_t) * m;
+                for (int i = pend_k + 1 + tid; i < m; i += kClThreads)
+                    col[i] = vbuf[i];
+                if (tid == 0)
+                    col[pend_k] = pend_beta;
+                pend_t = -1;
+                __syncthreads();
+            }
+            // the same argmax in every CTA (largest norm, lowest column on ties)
+            double bv = -1.0;
+            int pc = 0x7fffffff;
+            if (lane < CL) {
+                const int i = pub_idx[(k & 1) * 16 + lane];
+                const double v = pub_val[(k & 1) * 16 + lane];
+                if (i >= 0) {
+                    bv = v;
+                    pc = i;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(FULL, bv, o);
+                const int oi = __shfl_xor_sync(FULL, pc, o);
+                if (ov > bv || (ov == bv && oi < pc)) {
+                    bv = ov;
+                    pc = oi;
+                }
+            }
+            if (pc < 0 || pc >= n)
+                pc = 0;  // unreachable: n - k columns remain
+            const int owner = pc % CL, tp = pc / CL;
+            const double *src = cluster.map_shared_rank(qcol + size_t(tp) * m, owner);
+            for (int i = k + tid; i < m; i += kClThreads)
+                vbuf[i] = src[i];
+            __syncthreads();
+            // reflector of rows k..m-1 (xLARFG), identical in every CTA
+            double xn2 = 0.0;
+            for (int i = k + 1 + tid; i < m; i += kClThreads)
+                xn2 = fma(vbuf[i], vbuf[i], xn2);
+            xn2 = cl_block_sum(xn2, red);
+            const double alpha = vbuf[k];
+            double tau = 0.0, beta = alpha;
+            if (xn2 > 0.0) {
+                beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
+                tau = (beta - alpha) / beta;
+                const double scal = 1.0 / (alpha - beta);
+                for (int i = k + 1 + tid; i < m; i += kClThreads)
+                    vbuf[i] *= scal;
+            }
+            if (tid == 0) {
+                tau_all[k] = tau;
+                perm_all[k] = pc;
+            }
+            if (owner == c) {
+                if (tid == 0)
+                    cflag[tp] = k + 1;  // pivot k + 1 (>= 1: done)
+                pend_t = tp;
+                pend_k = k;
+                pend_beta = beta;
+            }
+            __syncthreads();
+            // apply H_k = I - tau v v^T (v_k = 1) to the remaining own columns
+            for (int t = warp; t < nown; t += kClWarps) {
+                if (cflag[t] != 0)
+                    continue;
+                double *col = qcol + size_t(t) * m;
+                if (tau != 0.0) {
+                    double w = 0.0;
+                    for (int i = k + 1 + lane; i < m; i += 32)
+                        w = fma(vbuf[i], col[i], w);
+                    w = warp_sum(w) + col[k];
+                    const double tw = tau * w;
+                    for (int i = k + 1 + lane; i < m; i += 32)
+                        col[i] = fma(-tw, vbuf[i], col[i]);
+                    __syncwarp();
+                    if (lane == 0)
+                        col[k] -= tw;
+                    __syncwarp();
+                }
+                // norm of rows k+1..m-1: downdate, or recompute when
+                // cancellation has eaten half the digits (xLAQP2's test)
+                const double r = col[k], cv = cn[t];
+                double f = 0.0;
+                bool recompute = false;
+                if (cv > 0.0) {
+                    f = fmax(1.0 - (r * r) / cv, 0.0);
+                    recompute = f * (cv / cn0[t]) <= kTol3z;
+                }
+                if (recompute) {
+                    double s = 0.0;
+                    for (int i = k + 1 + lane; i < m; i += 32)
+                        s = fma(col[i], col[i], s);
+                    s = warp_sum(s);
+                    if (lane == 0) {
+                        cn[t] = s;
+                        cn0[t] = s;
+                    }
+                } else if (lane == 0) {
+                    cn[t] = cv * f;
+                }
+                __syncwarp();
+            }
+            __syncthreads();
+        }
+        cluster.sync();
+        if (pend_t >= 0) {
+            double *col = qcol + size_t(pend_t) * m;
+            for (int i = pend_k + 1 + tid; i < m; i += kClThreads)
+                col[i] = vbuf[i];
+            if (tid == 0)
+                col[pend_k] = pend_beta;
+        }
+        __syncthreads();
+        // factors out (R and reflectors in place, tau, perm)
+        for (int t = warp; t < nown; t += kClWarps) {
+            double *g = J.A + size_t(c + t * CL) * m;
+            const double *col = qcol + size_t(t) * m;
+            for (int i = lane; i < m; i += 32)
+                g[i] = col[i];
+        }
+        if (c == 0)
+            for (int k = tid; k < n; k += kClThreads) {
+                J.tau[k] = tau_all[k];
+                J.perm[k] = perm_all[k];
+            }
+        // X = R^T into buffer 0: own column j (pivot kj) is row kj of X's
+        // columns: X[kj][i] = R[i][kj] = A[i][j] for i <= kj, else 0
+        for (int t = warp; t < nown; t += kClWarps) {
+            const int kj = cflag[t] - 1;
+            const double *col = qcol + size_t(t) * m;
+            for (int i = lane; i < n; i += 32) {
+                int cta, slot;
+                cl_where(i, L, cta, slot);
+                double *dst = cluster.map_shared_rank(jb + size_t(slot) * slot_len, cta);
+                dst[kj] = i <= kj ? col[i] : 0.0;
+            }
+        }
+    }
+    // own slots: V = I (and X = W on the direct path; zeros for the dummy)
+    for (int s = warp; s < 2 * L.PP; s += kClWarps) {
+        const int pr = c * L.PP + (s >> 1);
+        if (pr >= L.half)
+            continue;
+        const int pos = (s & 1) ? L.n_pad - 1 - pr : pr;  // = column at round 0
+        double *x = jb + size_t(s) * slot_len;
+        if (!pre)
+            for (int i = lane; i < L.nX; i += 32)
+                x[i] = pos < n ? J.A[size_t(pos) * m + i] : 0.0;
+        else if (pos >= n)
+            for (int i = lane; i < L.nX; i += 32)
+                x[i] = 0.0;
+        for (int i = lane; i < n; i += 32)
+            x[L.nX + i] = (i == pos) ? 1.0 : 0.0;
+    }
+    cluster.sync();
+
+    // ---- one-sided Jacobi ---------------------------------------------------
+    const int pr = c * L.PP + warp;
+    const bool has_pair = warp < L.PP && pr < L.half;
+    const int pos_t = pr, pos_b = L.n_pad - 1 - pr;
+    int cta_t = 0, slot_t = 0, cta_b = 0, slot_b = 0;
+    if (has_pair) {
+        cl_where(cl_next(pos_t, L.n_pad), L, cta_t, slot_t);
+        cl_where(cl_next(pos_b, L.n_pad), L, cta_b, slot_b);
+    }
+    int cur = 0, sweeps = 0;
+    bool converged = false;
+    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+        unsigned my_rot = 0;
+        bool my_big = false;  // a rotated pair had cos^2 > kLast^2
+        for (int r = 0; r < L.n_pad - 1; ++r) {
+            if (has_pair) {
+                const double *xt = jb + cur * buf_len + size_t(2 * warp) * slot_len;
+                const double *xb = xt + slot_len;
+                const int a = pos_t == 0 ? 0 : 1 + (pos_t - 1 + r) % (L.n_pad - 1);
+                const int b = 1 + (pos_b - 1 + r) % (L.n_pad - 1);
+                const bool real = (a < n) && (b < n);
+                double tt = 0.0, bb = 0.0, tb = 0.0;
+                if (real)
+                    for (int i = lane; i < L.nX; i += 32) {
+                        const double x = xt[i], y = xb[i];
+                        tt = fma(x, x, tt);
+                        bb = fma(y, y, bb);
+                        tb = fma(x, y, tb);
+                    }
+                const double red3 = warp_sum3(tt, bb, tb, lane);
+                tt = __shfl_sync(FULL, red3, 0);
+                bb = __shfl_sync(FULL, red3, 8);
+                tb = __shfl_sync(FULL, red3, 16);
+                // p = the lower column index of the pair
+                const bool top_is_p = a < b;
+                const double al = top_is_p ? tt : bb, be = top_is_p ? bb : tt;
+                double cs = 1.0, sn = 0.0;
+                const double ab = al * be, g2 = tb * tb;
+                bool rotate = real && al != 0.0 && be != 0.0 && g2 > (kTol * kTol) * ab;
+                if (rotate) {
+                    jacobi_rotation(al, be, tb, cs, sn);
+                    my_big = my_big || g2 > (kLast * kLast) * ab;  // no division
+                    ++my_rot;
+                }
+                // x_p' = c x_p - s x_q, x_q' = s x_p + c x_q, written to the
+                // slots the two columns take in the next round
+                const double ss = top_is_p ? sn : -sn;
+                double *dt = cluster.map_shared_rank(
+                    jb + (cur ^ 1) * buf_len + size_t(slot_t) * slot_len, cta_t);
+                double *db = cluster.map_shared_rank(
+                    jb + (cur ^ 1) * buf_len + size_t(slot_b) * slot_len, cta_b);
+                for (int i = lane; i < slot_len; i += 32) {
+                    const double x = xt[i], y = xb[i];
+                    if (rotate) {
+                        dt[i] = cs * x - ss * y;
+                        db[i] = ss * x + cs * y;
+                    } else {
+                        dt[i] = x;
+                        db[i] = y;
+                    }
+                }
+            }
+            cur ^= 1;
+            cluster.sync();
+        }
+        // every warp publishes its rotations and flag in its own CTA (plain
+        // stores, double buffered by sweep parity); after the barrier every
+        // warp reads all CTAs' entries and takes the same decision
+        if (lane == 0)
+            swstat[(sweep & 1) * kClWarps + warp] = (my_rot & 0x7fffffffu) |
+                                                    (my_big ? 0x80000000u : 0u);
+        cluster.sync();
+        unsigned nrot = 0u, big = 0u;
+        for (int e = lane; e < CL * kClWarps; e += 32) {
+            const unsigned v = *cluster.map_shared_rank(
+                swstat + (sweep & 1) * kClWarps + (e % kClWarps), e / kClWarps);
+            nrot += v & 0x7fffffffu;
+            big |= v >> 31;
+        }
+        nrot = __reduce_add_sync(FULL, nrot);
+        big = __reduce_or_sync(FULL, big);
+        sweeps = sweep + 1;
+        if (nrot == 0u || big == 0u) {
+            converged = true;
+            break;
+        }
+    }
+
+    // ---- results: position i holds column i at the start of a sweep --------
+    for (int s = warp; s < 2 * L.PP; s += kClWarps) {
+        const int p2 = c * L.PP + (s >> 1);
+        if (p2 >= L.half)
+            continue;
+        const int pos = (s & 1) ? L.n_pad - 1 - p2 : p2;
+        if (pos >= n)
+            continue;
+        const double *x = jb + cur * buf_len + size_t(s) * slot_len;
+        for (int i = lane; i < L.nX; i += 32)
+            J.X[size_t(pos) * L.nX + i] = x[i];
+        for (int i = lane; i < n; i += 32)
+            J.V[size_t(pos) * n + i] = x[L.nX + i];
+    }
+    if (c == 0 && tid == 0) {
+        J.bar[6] = unsigned(sweeps);
+        if (!converged)
+            J.bar[5] = unsigned(WOS_NO_CONVERGENCE);
+    }
+    // no CTA may leave while others can still read its shared memory
+    cluster.sync();
+}

@@ -12,12 +12,14 @@
 //    One launch serves one instance (its record in the constant bank) or a
 //    batch of instances of one precision and dimension (records in global
 //    memory, each lane reading its own walk's record through L1).
-//  * Every lane owns one walk at a time.  Walks advance in groups of G steps
-//    that share one Philox4x32-10 block (G = 4 words / words per step), so all
-//    lanes call Philox together; a lane whose walk stops mid-group idles to
-//    the group's end.  At a group boundary the finished lanes are refilled
-//    from the warp's tile (warp-level refill: ballot + popc ranks), so warps
-//    stay full despite geometric walk lengths.
+//  * Every lane owns one walk at a time.  Walks advance in groups of
+//    group_blocks x G steps, G steps per Philox4x32-10 block (G = 4 words /
+//    words per step), so all lanes call Philox together; a lane whose walk
+//    stops mid-group idles to the group's end.  At a group boundary the
+//    finished lanes are refilled from the warp's tile (warp-level refill:
+//    ballot + popc ranks), so warps stay full despite geometric walk
+//    lengths.  Longer groups spread the refill and queue bookkeeping over
+//    more steps at the price of more idle lane-steps after a walk stops.
 //  * The Philox counter of step n of walk w is (n / G, w lo, w hi, stream):
 //    results do not depend on scheduling or on the batch a walk runs in.
 //  * A finished lane only pushes its stopped point into a per-warp queue in
@@ -79,6 +81,7 @@ template <typename Real> struct WalkParams {
     int32_t nslot;               // 0 (global tally), 1 or 2
     int32_t hist_words;          // ceil(M_tot / 2), max over a batch
     int32_t refill_min;          // refill when >= this many lanes need a walk
+    int32_t group_blocks;        // Philox blocks per group of steps (>= 1)
 };
 
 template <typename Real, int DIM> struct Steps {
@@ -377,32 +380,41 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
         bool stop = false, capped = false;
         {
             const WalkInst<Real> &I = inst(linst);
+            const uint32_t nb = uint32_t(p.group_blocks);
+            const uint32_t blk0 = nstep / G;  // a group starts on a block boundary
             uint32_t w[4];
-            philox4x32_10(nstep / G, wlo, whi, I.stream_id, p.rk, w);
-            if (!active || nstep + uint32_t(G) <= I.step_cap) {
+            if (!active || nstep + uint32_t(G) * nb <= I.step_cap) {
+#pragma unroll 1
+                for (uint32_t b = 0; b < nb; ++b) {
+                    philox4x32_10(blk0 + b, wlo, whi, I.stream_id, p.rk, w);
 #pragma unroll
-                for (int s = 0; s < G; ++s) {
-                    const Real r = walk_dist<Real, DIM, KIND>(I.g, X);
-                    const bool go = !stop && !(r <= I.eps);
-                    stop = !go;
-                    Real U[DIM];
-                    direction<Real, DIM>(w + s * WPS, U);
-                    step_move<Real, DIM>(I.S, U, go ? r : Real(0), X);
-                    nstep += go ? 1u : 0u;
+                    for (int s = 0; s < G; ++s) {
+                        const Real r = walk_dist<Real, DIM, KIND>(I.g, X);
+                        const bool go = !stop && !(r <= I.eps);
+                        stop = !go;
+                        Real U[DIM];
+                        direction<Real, DIM>(w + s * WPS, U);
+                        step_move<Real, DIM>(I.S, U, go ? r : Real(0), X);
+                        nstep += go ? 1u : 0u;
+                    }
                 }
             } else {
+#pragma unroll 1
+                for (uint32_t b = 0; b < nb; ++b) {
+                    philox4x32_10(blk0 + b, wlo, whi, I.stream_id, p.rk, w);
 #pragma unroll
-                for (int s = 0; s < G; ++s) {
-                    const Real r = walk_dist<Real, DIM, KIND>(I.g, X);
-                    const bool at_eps = r <= I.eps;
-                    const bool at_cap = nstep >= I.step_cap;
-                    const bool go = !stop && !at_eps && !at_cap;
-                    capped = capped || (!stop && !at_eps && at_cap);
-                    stop = stop || !go;
-                    Real U[DIM];
-                    direction<Real, DIM>(w + s * WPS, U);
-                    step_move<Real, DIM>(I.S, U, go ? r : Real(0), X);
-                    nstep += go ? 1u : 0u;
+                    for (int s = 0; s < G; ++s) {
+                        const Real r = walk_dist<Real, DIM, KIND>(I.g, X);
+                        const bool at_eps = r <= I.eps;
+                        const bool at_cap = nstep >= I.step_cap;
+                        const bool go = !stop && !at_eps && !at_cap;
+                        capped = capped || (!stop && !at_eps && at_cap);
+                        stop = stop || !go;
+                        Real U[DIM];
+                        direction<Real, DIM>(w + s * WPS, U);
+                        step_move<Real, DIM>(I.S, U, go ? r : Real(0), X);
+                        nstep += go ? 1u : 0u;
+                    }
                 }
             }
         }

@@ -30,6 +30,7 @@ struct wos_context {
     int device = 0;
     int sm_count = 0;
     int max_smem_optin = 0;
+    std::atomic<int> svd_path{WOS_SVD_AUTO};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
@@ -48,13 +49,14 @@ int ctx_device(const wos_context *c) { return c->device; }
 void count_launches(wos_context *c, int n) { c->launches += uint64_t(n); }
 int ctx_sm_count(const wos_context *c) { return c->sm_count; }
 int ctx_max_smem(const wos_context *c) { return c->max_smem_optin; }
+int ctx_svd_path(const wos_context *c) { return c->svd_path.load(); }
 
 static int tune_key(int precision, int dim, int kind) { return (precision << 8) | (dim << 4) | kind; }
 
 void apply_tuning(const wos_context *c, int precision, int dim, int kind, wos_opts *o)
 {
     if (o->block_size || o->blocks_per_sm || o->tile_walks || o->hist_slots ||
-        o->refill_min || o->tiles_per_warp)
+        o->refill_min || o->tiles_per_warp || o->group_blocks)
         return;
     wos_context *cc = const_cast<wos_context *>(c);
     std::lock_guard<std::mutex> lock(cc->tune_mu);
@@ -66,6 +68,7 @@ void apply_tuning(const wos_context *c, int precision, int dim, int kind, wos_op
     o->tiles_per_warp = it->second.tiles_per_warp;
     o->hist_slots = it->second.hist_slots;
     o->refill_min = it->second.refill_min;
+    o->group_blocks = it->second.group_blocks;
 }
 
 }  // namespace wos
@@ -110,6 +113,14 @@ extern "C" wos_status wos_destroy(wos_context *c)
 extern "C" uint64_t wos_kernel_launches(const wos_context *c)
 {
     return c ? c->launches.load() : 0;
+}
+
+extern "C" wos_status wos_set_svd_path(wos_context *c, int32_t path)
+{
+    if (!c || path < WOS_SVD_AUTO || path > WOS_SVD_CLUSTER)
+        return WOS_INVALID_ARG;
+    c->svd_path.store(path);
+    return WOS_OK;
 }
 
 extern "C" const char *wos_status_string(wos_status s)
@@ -681,6 +692,7 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
     }
     apply_plan(plan, &p);
     p.refill_min = refill_min_of(o);
+    p.group_blocks = group_blocks_of<Real>(o, dim);
     const void *kfn = plan.kfn;
     const int grid = plan.grid, block = plan.block, nslot = plan.nslot;
     const size_t smem = plan.smem;
@@ -892,6 +904,7 @@ extern "C" wos_status wos_autotune(wos_context *ctx, const wos_problem *sp, uint
     best.block_size = 256;
     best.tiles_per_warp = 16;
     best.refill_min = 1;
+    best.group_blocks = 0;  // the default for the class
     float best_ms = 0.f, ms = 0.f;
     int trials = 0;
     st = trial(best, &ms);  // warm-up
@@ -904,7 +917,8 @@ extern "C" wos_status wos_autotune(wos_context *ctx, const wos_problem *sp, uint
             return;
         wos_opts c = best;
         int *f = field == 0 ? &c.block_size : field == 1 ? &c.blocks_per_sm
-               : field == 2 ? &c.tiles_per_warp : field == 3 ? &c.hist_slots : &c.refill_min;
+               : field == 2 ? &c.tiles_per_warp : field == 3 ? &c.hist_slots
+               : field == 4 ? &c.refill_min : &c.group_blocks;
         if (*f == value)
             return;
         *f = value;
@@ -926,6 +940,7 @@ extern "C" wos_status wos_autotune(wos_context *ctx, const wos_problem *sp, uint
     for (int v : {4, 64}) consider(2, v);
     for (int v : {-1}) consider(3, v);
     for (int v : {4, 8}) consider(4, v);
+    for (int v : {2, 4, 8}) consider(5, v);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != WOS_OK)
@@ -936,6 +951,7 @@ extern "C" wos_status wos_autotune(wos_context *ctx, const wos_problem *sp, uint
     out->tiles_per_warp = best.tiles_per_warp;
     out->hist_slots = best.hist_slots;
     out->refill_min = best.refill_min;
+    out->group_blocks = best.group_blocks;
     out->trials = trials;
     out->best_ms = best_ms;
     out->default_ms = default_ms;

@@ -171,6 +171,7 @@ wos_status launch_class(wos_context *ctx, const std::vector<int> &idx,
     pp->nslot = plan.nslot;
     pp->hist_words = (max_M + 1) / 2;
     pp->refill_min = refill_min_of(o);
+    pp->group_blocks = group_blocks_of<Real>(o, DIM);
     if (o.kernel_events[0])
         cudaEventRecord(static_cast<cudaEvent_t>(o.kernel_events[0]), stream);
     void *args[] = {pp};

@@ -476,9 +476,20 @@ template <typename Real, int DIM>
 __device__ __forceinline__ void direction(const uint32_t *w, Real *U)
 {
     if (DIM == 2) {
-        Real u = Uniform<Real>::get(w);
         Real s, c;
-        w_sincospi(Real(2) * u, &s, &c);
+        if constexpr (sizeof(Real) == 4) {
+            // 2u - 1 = (w >> 8) 2^-23 - 1 in one exact FMA (the same value as
+            // Uniform<float>::get doubled, less one); then the SFU path of
+            // w_sincospi
+            const float t = fmaf(float(w[0] >> 8), 0x1p-23f, -1.0f);
+            float ss, cc;
+            __sincosf(3.14159265358979f * t, &ss, &cc);
+            s = -ss;
+            c = -cc;
+        } else {
+            Real u = Uniform<Real>::get(w);
+            w_sincospi(Real(2) * u, &s, &c);
+        }
         U[0] = c;
         U[1] = s;
     } else {

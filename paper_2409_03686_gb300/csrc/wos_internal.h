@@ -13,6 +13,7 @@ int ctx_device(const wos_context *c);
 int ctx_sm_count(const wos_context *c);
 void count_launches(wos_context *c, int n);
 int ctx_max_smem(const wos_context *c);
+int ctx_svd_path(const wos_context *c);  // WOS_SVD_AUTO / _GRID / _CLUSTER
 // Launch fields of opts replaced by the context's tuned configuration for the
 // class (precision, dim, kind) when they are all zero.
 void apply_tuning(const wos_context *c, int precision, int dim, int kind, wos_opts *o);

@@ -97,6 +97,7 @@ wos_status build_noalloc(wos_context *ctx, unsigned char *scratch, const wos_dom
         return pst;
     apply_plan(plan, &p);
     p.refill_min = refill_min_of(o);
+    p.group_blocks = group_blocks_of<Real>(o, dim);
     const void *kfn = plan.kfn;
     const int grid = plan.grid, block = plan.block, nslot = plan.nslot;
     const size_t smem = plan.smem;

@@ -817,6 +817,8 @@ __global__ void finalize_kernel(SvdWork w, const double *sv, int transposed,
     }
 }
 
+#include "svd_cluster.cuh"
+
 // ---------------------------------------------------------------------------
 // TSVD pieces
 // ---------------------------------------------------------------------------
@@ -900,6 +902,7 @@ struct SvdProb {
     double *U, *S, *V;
     Lists L;
     bool pre;
+    int cl;          // cluster size of the cluster kernel, 0 = grid-wide kernels
     SvdWork w, wj;   // W itself, and the matrix Jacobi works on (W or X = R^T)
     QrWork q;
     double *sv, *Lb;
@@ -958,8 +961,53 @@ cudaError_t launch_groups(const void *kfn, int threads, int budget, const std::v
     return cudaSuccess;
 }
 
+// Whether a cluster of CL CTAs with smem bytes of dynamic shared memory each
+// can be resident at all.
+bool cluster_launchable(int CL, size_t smem)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(CL));
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = unsigned(CL);
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, svd_cluster_kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return nc >= 1;
+}
+
+// Cluster size of the cluster kernel for an m x n worked matrix, or 0 when
+// it does not fit (more than 256 columns, or more shared memory than a CTA
+// may have).
+int cluster_fit(const wos_context *ctx, int m, int n, int pre)
+{
+    if (n < 1 || n > kClMaxN)
+        return 0;
+    const int n_pad = std::max(2, n + (n & 1));
+    const int CL = std::min(kClMaxCtas, n_pad / 2);
+    const ClLayout L = cl_layout(m, n, pre, CL);
+    if (L.PP > kClWarps || L.total > size_t(wos::ctx_max_smem(ctx)))
+        return 0;
+    // every launch may use up to the opt-in maximum (set once, so that
+    // concurrent callers never see a smaller limit)
+    cudaFuncSetAttribute(svd_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(svd_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         wos::ctx_max_smem(ctx));
+    return cluster_launchable(CL, L.total) ? CL : 0;
+}
+
 // The whole SVD pipeline for a batch of problems (one stream): per-problem
-// small kernels, batched cooperative QR and Jacobi launches.
+// small kernels, then the factorisations -- one cluster launch per cluster
+// size for the problems that fit a cluster, batched cooperative QR and
+// Jacobi launches for the others -- then the left vectors and the outputs.
 wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
                      cudaStream_t st, void *const *jacobi_events = nullptr)
 {
@@ -982,6 +1030,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         w.n = b.transposed ? b.M_D : b.M_1;
         w.n_pad = std::max(2, w.n + (w.n & 1));
         b.pre = w.n >= kPrecondMinN;
+        b.cl = wos::ctx_svd_path(ctx) == WOS_SVD_GRID ? 0 : cluster_fit(ctx, w.m, w.n, b.pre);
         b.qgrid = b.pre ? std::max(1, std::min({w.n, 2 * sms, qbudget})) : 0;
         Off &o = O[p];
         o.W = take(size_t(w.m) * w.n * 8);
@@ -1005,6 +1054,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     }
     const size_t o_jrec = take(sizeof(SvdWork) * np), o_qrec = take(sizeof(QrWork) * np);
     const size_t o_left = take(sizeof(LeftJob) * np);
+    const size_t o_cjob = take(sizeof(ClusterJob) * np);
     const size_t o_begin = take(sizeof(int) * (2 * np + 2));
     char *base = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&base), off, st);
@@ -1013,7 +1063,8 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     int launches = 0;
     std::vector<SvdWork> jrecs(np);
     std::vector<QrWork> qrecs(np);
-    std::vector<int> qidx, jgrids(np, 0), qgrids(np, 0);
+    std::vector<int> qidx, pidx, jgrids(np, 0), qgrids(np, 0);
+    std::vector<ClusterJob> cjobs(np);
     for (int p = 0; p < np; ++p) {
         SvdProb &b = P[p];
         const Off &o = O[p];
@@ -1051,9 +1102,23 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
             b.Lb = reinterpret_cast<double *>(base + o.L);
             qrecs[p] = q;
             qgrids[p] = b.qgrid;
-            qidx.push_back(p);
+            pidx.push_back(p);
+            if (!b.cl)
+                qidx.push_back(p);
         }
         jrecs[p] = b.wj;
+        if (b.cl) {
+            ClusterJob &J = cjobs[p];
+            J.A = w.W;
+            J.m = w.m;
+            J.n = w.n;
+            J.pre = b.pre ? 1 : 0;
+            J.tau = b.pre ? b.q.tau : nullptr;
+            J.perm = b.pre ? b.q.perm : nullptr;
+            J.X = b.wj.W;
+            J.V = b.wj.Vw;
+            J.bar = w.bar;
+        }
     }
     QrWork *dq = reinterpret_cast<QrWork *>(base + o_qrec);
     SvdWork *dj = reinterpret_cast<SvdWork *>(base + o_jrec);
@@ -1066,16 +1131,47 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
             for (int p : qidx)
                 qgrids[p] = std::max(1, int(qgrids[p] * (long long)qbudget / want));
     }
-    if (!qidx.empty())
+    if (jacobi_events && jacobi_events[0])
+        cudaEventRecord(static_cast<cudaEvent_t>(jacobi_events[0]), st);
+    // cluster kernel: one launch per cluster size, one cluster per problem
+    size_t cjobs_used = 0;
+    for (int CL = 1; e == cudaSuccess && CL <= kClMaxCtas; ++CL) {
+        std::vector<ClusterJob> jobs;
+        size_t smem = 0;
+        for (int p = 0; p < np; ++p)
+            if (P[p].cl == CL) {
+                jobs.push_back(cjobs[p]);
+                smem = std::max(smem, cl_layout(P[p].w.m, P[p].w.n, P[p].pre, CL).total);
+            }
+        if (jobs.empty())
+            continue;
+        ClusterJob *dj2 = reinterpret_cast<ClusterJob *>(base + o_cjob) + cjobs_used;
+        cjobs_used += jobs.size();
+        cudaMemcpyAsync(dj2, jobs.data(), sizeof(ClusterJob) * jobs.size(),
+                        cudaMemcpyHostToDevice, st);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(CL * int(jobs.size())));
+        cfg.blockDim = dim3(kClThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = unsigned(CL);
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, svd_cluster_kernel, const_cast<const ClusterJob *>(dj2), CL);
+        ++launches;
+    }
+    if (e == cudaSuccess && !qidx.empty())
         e = launch_groups(reinterpret_cast<const void *>(qrcp_kernel), kQrThreads, qbudget,
                           qidx, qgrids, qrecs, dq, dbegin, st, &launches);
     for (int p = 0; e == cudaSuccess && p < np; ++p)
-        if (P[p].pre) {
+        if (P[p].pre && !P[p].cl) {
             build_x_kernel<<<sms * 4, 256, 0, st>>>(P[p].q, P[p].wj.W, P[p].wj.Vw);
             ++launches;
         }
-    if (jacobi_events && jacobi_events[0])
-        cudaEventRecord(static_cast<cudaEvent_t>(jacobi_events[0]), st);
     // Jacobi: one cooperative launch per class of rows per thread (and per
     // group of co-resident problems); the CTAs are shared in proportion to
     // the pairs when the batch is larger than the GPU
@@ -1084,7 +1180,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
             break;
         std::vector<int> idx;
         for (int p = 0; p < np; ++p)
-            if (rpt_of(P[p].wj.m) == rpt)
+            if (!P[p].cl && rpt_of(P[p].wj.m) == rpt)
                 idx.push_back(p);
         if (idx.empty())
             continue;
@@ -1105,10 +1201,10 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     }
     if (jacobi_events && jacobi_events[1])
         cudaEventRecord(static_cast<cudaEvent_t>(jacobi_events[1]), st);
-    if (e == cudaSuccess && !qidx.empty()) {  // left vectors of every preconditioned problem
+    if (e == cudaSuccess && !pidx.empty()) {  // left vectors of every preconditioned problem
         std::vector<LeftJob> jobs;
         int ncols = 0;
-        for (int p : qidx) {
+        for (int p : pidx) {
             jobs.push_back(LeftJob{P[p].q, P[p].wj.Vw, P[p].Lb, ncols});
             ncols += P[p].w.n;
         }

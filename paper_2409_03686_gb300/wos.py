@@ -91,6 +91,7 @@ class WosOpts(ctypes.Structure):
         ("trace_x", ctypes.c_void_p),
         ("kernel_events", ctypes.c_void_p * 2),
         ("mapped", ctypes.c_int32),
+        ("group_blocks", ctypes.c_int32),
     ]
 
 
@@ -119,6 +120,7 @@ class WosTuning(ctypes.Structure):
         ("tiles_per_warp", ctypes.c_int32),
         ("hist_slots", ctypes.c_int32),
         ("refill_min", ctypes.c_int32),
+        ("group_blocks", ctypes.c_int32),
         ("trials", ctypes.c_int32),
         ("best_ms", ctypes.c_float),
         ("default_ms", ctypes.c_float),
@@ -232,6 +234,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.wos_destroy.argtypes = [vp]
     L.wos_kernel_launches.restype = u64
     L.wos_kernel_launches.argtypes = [vp]
+    L.wos_set_svd_path.argtypes = [vp, i32]
     L.wos_status_string.restype = ctypes.c_char_p
     L.wos_status_string.argtypes = [ctypes.c_int]
     L.wos_conductivity_sqrt.argtypes = [i32, vp, vp]
@@ -409,7 +412,8 @@ def make_opts(precision: int = 0, step_cap: int = 0, stream_id: int = 0, k0: int
               blocks_per_sm: int = 0, tile_walks: int = 0, hist_slots: int = 0,
               refill_min: int = 0, tiles_per_warp: int = 0,
               trace_elem=None, trace_steps=None, trace_x=None,
-              kernel_events=None, mapped: bool = False) -> WosOpts:
+              kernel_events=None, mapped: bool = False,
+              group_blocks: int = 0) -> WosOpts:
     o = WosOpts()
     o.precision = precision
     o.step_cap = step_cap
@@ -429,6 +433,7 @@ def make_opts(precision: int = 0, step_cap: int = 0, stream_id: int = 0, k0: int
         for q, ev in enumerate(kernel_events):
             o.kernel_events[q] = ev.cuda_event
     o.mapped = int(mapped)
+    o.group_blocks = group_blocks
     return o
 
 
@@ -563,6 +568,15 @@ def wos_autotune(ctx: Context, inst, seed: int | None = None, sample_walks: int 
 
 def wos_autotune_reset(ctx: Context) -> None:
     _check(load().wos_autotune_reset(ctx.h), "wos_autotune_reset", False)
+
+
+SVD_AUTO, SVD_GRID, SVD_CLUSTER = 0, 1, 2
+
+
+def wos_set_svd_path(ctx: Context, path: int) -> None:
+    """Kernels that factor SVD problems: SVD_AUTO (cluster kernel when the
+    worked matrix fits it), SVD_GRID (grid-wide kernels) or SVD_CLUSTER."""
+    _check(load().wos_set_svd_path(ctx.h, int(path)), "wos_set_svd_path", False)
 
 
 def wos_op_svd(ctx: Context, counts, N: int, gamma1: np.ndarray, sigma, nu=None,

@@ -64,14 +64,19 @@ int main(void) {
          sizeof(wos_queue_opts), sizeof(wos_queue_stats), offsetof(wos_problem, k1),
          offsetof(wos_request, r_used), offsetof(wos_queue_opts, side_streams),
          offsetof(wos_queue_stats, queued));
+  printf("%zu %zu %zu %zu\\n", offsetof(wos_opts, group_blocks), sizeof(wos_tuning),
+         offsetof(wos_tuning, group_blocks), offsetof(wos_tuning, best_ms));
   return 0;
 }
 """)
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", str(ROOT / "include"), str(src), "-o", str(exe)],
                    check=True)
-    a, b, sp, c = subprocess.run([str(exe)], capture_output=True, text=True,
-                                 check=True).stdout.split("\n")[:4]
+    a, b, sp, c, t = subprocess.run([str(exe)], capture_output=True, text=True,
+                                    check=True).stdout.split("\n")[:5]
+    assert [int(x) for x in t.split()] == [
+        wos.WosOpts.group_blocks.offset, ctypes.sizeof(wos.WosTuning),
+        wos.WosTuning.group_blocks.offset, wos.WosTuning.best_ms.offset]
     assert [int(x) for x in sp.split()] == [ctypes.sizeof(wos.WosSvdProblem),
                                             wos.WosSvdProblem.V.offset]
     sizes = [int(x) for x in a.split()]

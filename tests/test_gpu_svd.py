@@ -20,6 +20,15 @@ pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
 
 
+@pytest.fixture(params=[wos.SVD_AUTO, wos.SVD_GRID], ids=["cluster", "grid"])
+def svd_path(request):
+    """Both factorisation kernels: the cluster kernel (taken by every problem
+    here that fits it: at most 256 columns) and the grid-wide kernels."""
+    wos.wos_set_svd_path(ctx(), request.param)
+    yield request.param
+    wos.wos_set_svd_path(ctx(), wos.SVD_AUTO)
+
+
 def _svd_pair(C, N, gamma1, sigma, nu):
     Ct = torch.as_tensor(C.astype(np.int32), device=DEV)
     sg = torch.as_tensor(sigma, device=DEV)
@@ -46,7 +55,7 @@ def _gaps(so, max_r):
     lambda: W.annulus_config(N=1000, grid=6, m_each=32),
     lambda: W.perforated_disc_config(N=1000, eps=1e-6, n_points=20, m_outer=20, m_hole=8),
 ])
-def test_svd_matches_oracle_on_oracle_counts(make):
+def test_svd_matches_oracle_on_oracle_counts(make, svd_path):
     inst = make()
     C, _, _ = O.build_counts(inst)
     sigma = O.element_measures(inst.domain, inst.partition)
@@ -66,7 +75,7 @@ def test_svd_matches_oracle_on_oracle_counts(make):
 
 
 @pytest.mark.parametrize("shape", [(256, 256, 128), (96, 300, 200), (1024, 1536, 768)])
-def test_svd_matches_oracle_at_benchmark_shapes(shape):
+def test_svd_matches_oracle_at_benchmark_shapes(shape, svd_path):
     M_D, M_tot, M_1 = shape
     N = 100_000
     C = W.synthetic_counts(M_D, M_tot, N, seed=M_D)
@@ -107,7 +116,7 @@ def test_reconstruction_matches_oracle():
 
 
 @pytest.mark.parametrize("transposed", [False, True])
-def test_rank_deficient_operator(transposed):
+def test_rank_deficient_operator(transposed, svd_path):
     """Zero Gamma_1 columns and repeated rows (rank deficiency) on the
     preconditioned path (n >= 32): singular values as the oracle's, B
     reproduced, singular vectors of the non-zero singular values
@@ -132,7 +141,7 @@ def test_rank_deficient_operator(transposed):
 
 
 @pytest.mark.parametrize("shape", [(256, 256, 128), (300, 1536, 768)])
-def test_svd_is_deterministic(shape):
+def test_svd_is_deterministic(shape, svd_path):
     """Repeated SVDs of the same counts are bit-identical (the preconditioned
     path's cooperative QR and the Jacobi dataflow take the same decisions
     whatever the CTA timing)."""
@@ -153,7 +162,7 @@ def test_svd_is_deterministic(shape):
             assert torch.equal(a, b), rep
 
 
-def test_batched_svd_equals_single_calls():
+def test_batched_svd_equals_single_calls(svd_path):
     """wos_op_svd_batched: problems of different shapes and orientations
     (direct path n < 32 and preconditioned n >= 32), and a batch larger than
     the co-resident CTAs of one launch, give each problem's single-call
@@ -175,3 +184,47 @@ def test_batched_svd_equals_single_calls():
         for a, b in zip(r[:3], g[:3]):
             assert torch.equal(a, b), q
         assert r[3] == g[3]
+
+
+@pytest.mark.parametrize("shape", [(32, 48, 16), (20, 48, 30), (256, 256, 128), (96, 300, 200),
+                                   (300, 400, 256), (33, 40, 33)])
+def test_cluster_and_grid_kernels_agree(shape):
+    """The cluster kernel and the grid-wide kernels factor the same problems
+    (direct path n < 32, preconditioned path, transposed orientation, odd n,
+    the largest n the cluster takes): the same singular values to rounding,
+    B reproduced by both, the same singular subspaces at gaps; on the
+    preconditioned path the cluster kernel is the one taken (fewer launches:
+    no separate QR, X and Jacobi launches)."""
+    M_D, M_tot, M_1 = shape
+    N = 80_000
+    C = W.synthetic_counts(M_D, M_tot, N, seed=M_D + M_1)
+    g1 = np.zeros(M_tot, np.uint8)
+    g1[:M_1] = 1
+    Ct = torch.as_tensor(C.astype(np.int32), device=DEV)
+    sg = torch.full((M_tot,), 2 * np.pi / M_tot, dtype=torch.float64, device=DEV)
+    c = ctx()
+    out = {}
+    launches = {}
+    for path in (wos.SVD_AUTO, wos.SVD_GRID):
+        wos.wos_set_svd_path(c, path)
+        torch.cuda.synchronize()
+        l0 = c.kernel_launches()
+        U, S, V, sw = wos.wos_op_svd(c, Ct, N, g1, sg)
+        torch.cuda.synchronize()
+        launches[path] = c.kernel_launches() - l0
+        out[path] = (U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy(), sw)
+    wos.wos_set_svd_path(c, wos.SVD_AUTO)
+    if min(M_D, M_1) >= 32:  # preconditioned: QR, X and Jacobi are one launch
+        assert launches[wos.SVD_AUTO] < launches[wos.SVD_GRID]
+    Ua, sa, Va, swa = out[wos.SVD_AUTO]
+    Ug, sg_, Vg, swg = out[wos.SVD_GRID]
+    _check_sv(sa, sg_)
+    B = O.operator_B(C, N, g1, np.full(M_D, 1 / np.sqrt(M_D)), np.full(M_tot, 2 * np.pi / M_tot))
+    for U, s, V in ((Ua, sa, Va), (Ug, sg_, Vg)):
+        np.testing.assert_allclose(U @ np.diag(s) @ V.T, B, atol=1e-13 * s[0])
+        k = len(s)
+        np.testing.assert_allclose(U.T @ U, np.eye(k), atol=1e-12)
+        np.testing.assert_allclose(V.T @ V, np.eye(k), atol=1e-12)
+    for r in _gaps(sg_, 16):
+        np.testing.assert_allclose(Ua[:, :r] @ Ua[:, :r].T, Ug[:, :r] @ Ug[:, :r].T, atol=1e-8)
+    assert abs(swa - swg) <= 2

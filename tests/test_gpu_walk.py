@@ -96,6 +96,27 @@ def test_schedule_does_not_change_results():
         np.testing.assert_array_equal(gpu_build(inst, trace=False, **kw)["counts"], ref)
 
 
+@pytest.mark.parametrize("make", [
+    lambda: W.square_config(N=1000, grid=6),
+    lambda: W.annulus_config(N=800, grid=4),
+    lambda: W.ball_config(N=600, n_points=24),
+    lambda: W.square_config(N=400, grid=4).replace(fp64=True, eps=1e-8),
+    lambda: W.square_config(N=500, grid=4).replace(step_cap=13),
+])
+def test_group_length_does_not_change_results(make):
+    """Walks advance group_blocks Philox blocks per refill; the counter of
+    step n is n / (steps per block) whatever the group, so counts, the
+    unterminated tallies (with a step cap inside a group) and every exit
+    are the same for every group length."""
+    inst = make()
+    ref = gpu_build(inst, group_blocks=1)
+    for nb in (2, 3, 5, 16):
+        got = gpu_build(inst, group_blocks=nb)
+        np.testing.assert_array_equal(got["counts"], ref["counts"])
+        np.testing.assert_array_equal(got["unterm"], ref["unterm"])
+        np.testing.assert_array_equal(got["trace"], ref["trace"])
+
+
 def test_resume_is_bit_identical():
     inst = W.annulus_config(N=1500, grid=4)
     full = gpu_build(inst, trace=False)
