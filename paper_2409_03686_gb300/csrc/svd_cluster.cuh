@@ -43,6 +43,7 @@ constexpr int kClThreads = 256;
 constexpr int kClWarps = kClThreads / 32;
 constexpr int kClMaxCtas = 16;
 constexpr int kClMaxN = 2 * kClMaxCtas * kClWarps;  // 256 columns
+constexpr int kClChunk = 4;                          // rows per lane per chunk
 
 struct ClusterJob {
     double *A;       // m x n column-major: W on entry; (pre) R and reflectors
@@ -107,24 +108,7 @@ __device__ __forceinline__ int cl_next(int pos, int n_pad)
     return pos == 0 ? 0 : (pos == 1 ? n_pad - 1 : pos - 1);
 }
 
-// Sum over the block, the same value (and the same arithmetic order) in
-// every thread.
-__device__ double cl_block_sum(double v, double *red)
-{
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0)
-        red[wid] = v;
-    __syncthreads();
-    double s = 0.0;
-#pragma unroll
-    for (int q = 0; q < kClWarps; ++q)
-        s += red[q];
-    return s;
-}
-
-__global__ void __launch_bounds__(kClThreads)
+__global__ void __launch_bounds__(kClThreads, 1)
 svd_cluster_kernel(const ClusterJob *jobs, int CL)
 {
     cg::cluster_group cluster = cg::this_cluster();
@@ -226,20 +210,39 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
             for (int i = k + tid; i < m; i += kClThreads)
                 vbuf[i] = src[i];
             __syncthreads();
-            // reflector of rows k..m-1 (xLARFG), identical in every CTA
-            double xn2 = 0.0;
-            for (int i = k + 1 + tid; i < m; i += kClThreads)
-                xn2 = fma(vbuf[i], vbuf[i], xn2);
-            xn2 = cl_block_sum(xn2, red);
-            const double alpha = vbuf[k];
-            double tau = 0.0, beta = alpha;
-            if (xn2 > 0.0) {
-                beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
-                tau = (beta - alpha) / beta;
-                const double scal = 1.0 / (alpha - beta);
+            // reflector of rows k..m-1 (xLARFG), identical in every CTA.  A
+            // warp instruction holds the FP64 pipe of its SM sub-partition
+            // for 64 cycles whatever its active lanes, so the scalars are
+            // formed by two warps (on two sub-partitions: warp 0 tau, warp 1
+            // the scale), not by every thread.
+            if (warp < 2) {
+                double xn2 = 0.0;
+                for (int i = k + 1 + lane; i < m; i += 32)
+                    xn2 = fma(vbuf[i], vbuf[i], xn2);
+                xn2 = warp_sum(xn2);
+                const double alpha = vbuf[k];
+                double tau = 0.0, beta = alpha, scal = 1.0;
+                if (xn2 > 0.0) {
+                    beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
+                    if (warp == 0)
+                        tau = (beta - alpha) / beta;
+                    else
+                        scal = 1.0 / (alpha - beta);
+                }
+                if (lane == 0) {
+                    if (warp == 0) {
+                        red[0] = tau;
+                        red[1] = beta;
+                    } else {
+                        red[2] = scal;
+                    }
+                }
+            }
+            __syncthreads();
+            const double tau = red[0], beta = red[1], scal = red[2];
+            if (tau != 0.0)
                 for (int i = k + 1 + tid; i < m; i += kClThreads)
                     vbuf[i] *= scal;
-            }
             if (tid == 0) {
                 tau_all[k] = tau;
                 perm_all[k] = pc;
@@ -270,14 +273,16 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
                         col[k] -= tw;
                     __syncwarp();
                 }
-                // norm of rows k+1..m-1: downdate, or recompute when
-                // cancellation has eaten half the digits (xLAQP2's test)
+                // norm of rows k+1..m-1: downdate |x|^2 - r^2, or recompute
+                // when cancellation has eaten half the digits (xLAQP2's test
+                // (1 - r^2/|x|^2) |x|^2 / |x_0|^2 <= tol3z, multiplied out:
+                // no division on the FP64 pipe)
                 const double r = col[k], cv = cn[t];
                 double f = 0.0;
                 bool recompute = false;
                 if (cv > 0.0) {
-                    f = fmax(1.0 - (r * r) / cv, 0.0);
-                    recompute = f * (cv / cn0[t]) <= kTol3z;
+                    f = fmax(fma(-r, r, cv), 0.0);
+                    recompute = f <= kTol3z * cn0[t];
                 }
                 if (recompute) {
                     double s = 0.0;
@@ -289,7 +294,7 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
                         cn0[t] = s;
                     }
                 } else if (lane == 0) {
-                    cn[t] = cv * f;
+                    cn[t] = f;
                 }
                 __syncwarp();
             }
@@ -368,13 +373,24 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
                 const int a = pos_t == 0 ? 0 : 1 + (pos_t - 1 + r) % (L.n_pad - 1);
                 const int b = 1 + (pos_b - 1 + r) % (L.n_pad - 1);
                 const bool real = (a < n) && (b < n);
+                // rows in chunks of four per lane, loads first (one warp per
+                // sub-partition: nothing else hides the shared-memory latency)
                 double tt = 0.0, bb = 0.0, tb = 0.0;
                 if (real)
-                    for (int i = lane; i < L.nX; i += 32) {
-                        const double x = xt[i], y = xb[i];
-                        tt = fma(x, x, tt);
-                        bb = fma(y, y, bb);
-                        tb = fma(x, y, tb);
+                    for (int i0 = lane; i0 < L.nX; i0 += 32 * kClChunk) {
+                        double x[kClChunk], y[kClChunk];
+#pragma unroll
+                        for (int u = 0; u < kClChunk; ++u) {
+                            const int i = i0 + 32 * u;
+                            x[u] = i < L.nX ? xt[i] : 0.0;
+                            y[u] = i < L.nX ? xb[i] : 0.0;
+                        }
+#pragma unroll
+                        for (int u = 0; u < kClChunk; ++u) {
+                            tt = fma(x[u], x[u], tt);
+                            bb = fma(y[u], y[u], bb);
+                            tb = fma(x[u], y[u], tb);
+                        }
                     }
                 const double red3 = warp_sum3(tt, bb, tb, lane);
                 tt = __shfl_sync(FULL, red3, 0);
@@ -398,14 +414,29 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
                     jb + (cur ^ 1) * buf_len + size_t(slot_t) * slot_len, cta_t);
                 double *db = cluster.map_shared_rank(
                     jb + (cur ^ 1) * buf_len + size_t(slot_b) * slot_len, cta_b);
-                for (int i = lane; i < slot_len; i += 32) {
-                    const double x = xt[i], y = xb[i];
+                for (int i0 = lane; i0 < slot_len; i0 += 32 * kClChunk) {
+                    double x[kClChunk], y[kClChunk];
+#pragma unroll
+                    for (int u = 0; u < kClChunk; ++u) {
+                        const int i = i0 + 32 * u;
+                        x[u] = i < slot_len ? xt[i] : 0.0;
+                        y[u] = i < slot_len ? xb[i] : 0.0;
+                    }
                     if (rotate) {
-                        dt[i] = cs * x - ss * y;
-                        db[i] = ss * x + cs * y;
-                    } else {
-                        dt[i] = x;
-                        db[i] = y;
+#pragma unroll
+                        for (int u = 0; u < kClChunk; ++u) {
+                            const double a2 = cs * x[u] - ss * y[u];
+                            y[u] = ss * x[u] + cs * y[u];
+                            x[u] = a2;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kClChunk; ++u) {
+                        const int i = i0 + 32 * u;
+                        if (i < slot_len) {
+                            dt[i] = x[u];
+                            db[i] = y[u];
+                        }
                     }
                 }
             }
