@@ -37,13 +37,9 @@
 
 #include <cooperative_groups.h>
 
-namespace cg = cooperative_groups;
+#include "svd_cluster_layout.h"
 
-constexpr int kClThreads = 256;
-constexpr int kClWarps = kClThreads / 32;
-constexpr int kClMaxCtas = 16;
-constexpr int kClMaxN = 2 * kClMaxCtas * kClWarps;  // 256 columns
-constexpr int kClChunk = 4;                          // rows per lane per chunk
+namespace cg = cooperative_groups;
 
 struct ClusterJob {
     double *A;       // m x n column-major: W on entry; (pre) R and reflectors
@@ -56,57 +52,6 @@ struct ClusterJob {
     double *V;       // out: n x n accumulated rotations
     unsigned *bar;   // [5] status, [6] sweeps
 };
-
-// Shared-memory layout of one CTA (bytes, 16-byte aligned pieces).
-struct ClLayout {
-    int CL, PP, cpc, nX, n_pad, half;
-    size_t small, qcol, vbuf, jb, total;
-};
-
-__host__ __device__ inline size_t cl_align(size_t b) { return (b + 15) / 16 * 16; }
-
-__host__ __device__ inline ClLayout cl_layout(int m, int n, int pre, int CL)
-{
-    ClLayout L;
-    L.CL = CL;
-    L.n_pad = n + (n & 1) < 2 ? 2 : n + (n & 1);
-    L.half = L.n_pad / 2;
-    L.PP = (L.half + CL - 1) / CL;
-    L.cpc = pre ? (n + CL - 1) / CL : 0;
-    L.nX = pre ? n : m;
-    // small: pub_val[2][16] double, pub_idx[2][16] int, tau_all[n] double,
-    // perm_all[n] int, cn[cpc], cn0[cpc] double, flags[cpc] int (done, or
-    // pivot position + 1), sweep statistics of the warps [2][kClWarps],
-    // block-sum scratch
-    size_t s = 0;
-    s += cl_align(2 * 16 * 8) + cl_align(2 * 16 * 4);
-    s += cl_align(size_t(n) * 8) + cl_align(size_t(n) * 4);
-    s += 2 * cl_align(size_t(L.cpc) * 8) + cl_align(size_t(L.cpc) * 4);
-    s += cl_align(2 * kClWarps * 4) + cl_align(64 * 8);
-    L.small = s;
-    L.qcol = pre ? cl_align(size_t(L.cpc) * m * 8) : 0;
-    L.vbuf = pre ? cl_align(size_t(m) * 8) : 0;
-    L.jb = cl_align(size_t(2) * 2 * L.PP * (L.nX + n) * 8);
-    L.total = L.small + L.qcol + L.vbuf + L.jb;
-    return L;
-}
-
-// CTA and slot of round-robin position pos: pair pr = pos (top) or
-// n_pad - 1 - pos (bottom); CTA pr / PP, slot 2 (pr mod PP) + (bottom).
-__device__ __forceinline__ void cl_where(int pos, const ClLayout &L, int &cta, int &slot)
-{
-    const bool top = pos < L.half;
-    const int pr = top ? pos : L.n_pad - 1 - pos;
-    cta = pr / L.PP;
-    slot = 2 * (pr - cta * L.PP) + (top ? 0 : 1);
-}
-
-// Position in the next round of the column at position pos (circle method:
-// position 0 fixed, 1 -> n_pad - 1, every other one down by one).
-__device__ __forceinline__ int cl_next(int pos, int n_pad)
-{
-    return pos == 0 ? 0 : (pos == 1 ? n_pad - 1 : pos - 1);
-}
 
 __global__ void __launch_bounds__(kClThreads, 1)
 svd_cluster_kernel(const ClusterJob *jobs, int CL)
@@ -370,8 +315,8 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
             if (has_pair) {
                 const double *xt = jb + cur * buf_len + size_t(2 * warp) * slot_len;
                 const double *xb = xt + slot_len;
-                const int a = pos_t == 0 ? 0 : 1 + (pos_t - 1 + r) % (L.n_pad - 1);
-                const int b = 1 + (pos_b - 1 + r) % (L.n_pad - 1);
+                const int a = cl_column(pos_t, r, L.n_pad);
+                const int b = cl_column(pos_b, r, L.n_pad);
                 const bool real = (a < n) && (b < n);
                 // rows in chunks of four per lane, loads first (one warp per
                 // sub-partition: nothing else hides the shared-memory latency)

@@ -1211,7 +1211,10 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         LeftJob *dl = reinterpret_cast<LeftJob *>(base + o_left);
         cudaMemcpyAsync(dl, jobs.data(), sizeof(LeftJob) * jobs.size(), cudaMemcpyHostToDevice,
                         st);
-        form_left_kernel<<<std::max(1, std::min((ncols + 7) / 8, sms * 8)), 256, 0, st>>>(
+        // two warps (columns) per block: the columns spread over the SMs'
+        // sub-partitions (each warp's dependent FP64 chain of n reflectors
+        // holds its sub-partition's FP64 unit; two per SM would queue)
+        form_left_kernel<<<std::max(1, std::min((ncols + 1) / 2, sms * 16)), 64, 0, st>>>(
             dl, int(jobs.size()), ncols);
         ++launches;
     }
