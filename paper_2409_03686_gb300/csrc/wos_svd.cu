@@ -1190,7 +1190,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         const int budget = std::max(1, bps) * sms;
         long long want = 0;
         for (int p : idx) {
-            jgrids[p] = std::min({P[p].wj.n_pad / 2, 2 * sms, budget});
+            jgrids[p] = std::min(P[p].wj.n_pad / 2, budget);  // a CTA per pair if they fit
             want += jgrids[p];
         }
         if (want > budget)
