@@ -60,6 +60,7 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
     const ClusterJob J = jobs[blockIdx.x / CL];
     const int c = int(cluster.block_rank());
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int T = int(blockDim.x), nw = T >> 5;  // 128 or 256 threads
     const int m = J.m, n = J.n, pre = J.pre;
     const ClLayout L = cl_layout(m, n, pre, CL);
     extern __shared__ __align__(16) unsigned char cl_smem[];
@@ -84,7 +85,7 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
     // ---- QR with column pivoting ------------------------------------------
     if (pre) {
         const int nown = c < n ? (n - c + CL - 1) / CL : 0;
-        for (int t = warp; t < nown; t += kClWarps) {
+        for (int t = warp; t < nown; t += nw) {
             const double *g = J.A + size_t(c + t * CL) * m;
             double *col = qcol + size_t(t) * m;
             double s = 0.0;
@@ -121,7 +122,7 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
             cluster.sync();
             if (pend_t >= 0) {  // the previous pivot's reflector, now unread
                 double *col = qcol + size_t(pend_t) * m;
-                for (int i = pend_k + 1 + tid; i < m; i += kClThreads)
+                for (int i = pend_k + 1 + tid; i < m; i += T)
                     col[i] = vbuf[i];
                 if (tid == 0)
                     col[pend_k] = pend_beta;
@@ -152,7 +153,7 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
                 pc = 0;  // unreachable: n - k columns remain
             const int owner = pc % CL, tp = pc / CL;
             const double *src = cluster.map_shared_rank(qcol + size_t(tp) * m, owner);
-            for (int i = k + tid; i < m; i += kClThreads)
+            for (int i = k + tid; i < m; i += T)
                 vbuf[i] = src[i];
             __syncthreads();
             // reflector of rows k..m-1 (xLARFG), identical in every CTA.  A
@@ -186,7 +187,7 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
             __syncthreads();
             const double tau = red[0], beta = red[1], scal = red[2];
             if (tau != 0.0)
-                for (int i = k + 1 + tid; i < m; i += kClThreads)
+                for (int i = k + 1 + tid; i < m; i += T)
                     vbuf[i] *= scal;
             if (tid == 0) {
                 tau_all[k] = tau;
@@ -201,7 +202,7 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
             }
             __syncthreads();
             // apply H_k = I - tau v v^T (v_k = 1) to the remaining own columns
-            for (int t = warp; t < nown; t += kClWarps) {
+            for (int t = warp; t < nown; t += nw) {
                 if (cflag[t] != 0)
                     continue;
                 double *col = qcol + size_t(t) * m;
@@ -248,27 +249,27 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
         cluster.sync();
         if (pend_t >= 0) {
             double *col = qcol + size_t(pend_t) * m;
-            for (int i = pend_k + 1 + tid; i < m; i += kClThreads)
+            for (int i = pend_k + 1 + tid; i < m; i += T)
                 col[i] = vbuf[i];
             if (tid == 0)
                 col[pend_k] = pend_beta;
         }
         __syncthreads();
         // factors out (R and reflectors in place, tau, perm)
-        for (int t = warp; t < nown; t += kClWarps) {
+        for (int t = warp; t < nown; t += nw) {
             double *g = J.A + size_t(c + t * CL) * m;
             const double *col = qcol + size_t(t) * m;
             for (int i = lane; i < m; i += 32)
                 g[i] = col[i];
         }
         if (c == 0)
-            for (int k = tid; k < n; k += kClThreads) {
+            for (int k = tid; k < n; k += T) {
                 J.tau[k] = tau_all[k];
                 J.perm[k] = perm_all[k];
             }
         // X = R^T into buffer 0: own column j (pivot kj) is row kj of X's
         // columns: X[kj][i] = R[i][kj] = A[i][j] for i <= kj, else 0
-        for (int t = warp; t < nown; t += kClWarps) {
+        for (int t = warp; t < nown; t += nw) {
             const int kj = cflag[t] - 1;
             const double *col = qcol + size_t(t) * m;
             for (int i = lane; i < n; i += 32) {
@@ -280,7 +281,7 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
         }
     }
     // own slots: V = I (and X = W on the direct path; zeros for the dummy)
-    for (int s = warp; s < 2 * L.PP; s += kClWarps) {
+    for (int s = warp; s < 2 * L.PP; s += nw) {
         const int pr = c * L.PP + (s >> 1);
         if (pr >= L.half)
             continue;
@@ -396,9 +397,9 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
                                                     (my_big ? 0x80000000u : 0u);
         cluster.sync();
         unsigned nrot = 0u, big = 0u;
-        for (int e = lane; e < CL * kClWarps; e += 32) {
+        for (int e = lane; e < CL * nw; e += 32) {
             const unsigned v = *cluster.map_shared_rank(
-                swstat + (sweep & 1) * kClWarps + (e % kClWarps), e / kClWarps);
+                swstat + (sweep & 1) * kClWarps + (e % nw), e / nw);
             nrot += v & 0x7fffffffu;
             big |= v >> 31;
         }
@@ -412,7 +413,7 @@ svd_cluster_kernel(const ClusterJob *jobs, int CL)
     }
 
     // ---- results: position i holds column i at the start of a sweep --------
-    for (int s = warp; s < 2 * L.PP; s += kClWarps) {
+    for (int s = warp; s < 2 * L.PP; s += nw) {
         const int p2 = c * L.PP + (s >> 1);
         if (p2 >= L.half)
             continue;

@@ -1138,10 +1138,13 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     for (int CL = 1; e == cudaSuccess && CL <= kClMaxCtas; ++CL) {
         std::vector<ClusterJob> jobs;
         size_t smem = 0;
+        int pp = 1;
         for (int p = 0; p < np; ++p)
             if (P[p].cl == CL) {
                 jobs.push_back(cjobs[p]);
-                smem = std::max(smem, cl_layout(P[p].w.m, P[p].w.n, P[p].pre, CL).total);
+                const ClLayout L = cl_layout(P[p].w.m, P[p].w.n, P[p].pre, CL);
+                smem = std::max(smem, L.total);
+                pp = std::max(pp, L.PP);
             }
         if (jobs.empty())
             continue;
@@ -1151,7 +1154,10 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
                         cudaMemcpyHostToDevice, st);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(unsigned(CL * int(jobs.size())));
-        cfg.blockDim = dim3(kClThreads);
+        // a warp per pair of a round, at least four (the QR's two scalar
+        // warps and the column warps); fewer threads leave room on the SMs
+        // for other work (the next walk launch) beside the cluster
+        cfg.blockDim = dim3(pp <= 4 ? 128u : unsigned(kClThreads));
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
         cudaLaunchAttribute at[1];
