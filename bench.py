@@ -275,6 +275,8 @@ def run_gpu(args, rank: int, world: int, dist):
     # of its walks, before anything is timed; later builds use it
     tunings = ({inst_p["inst"].name: wos.wos_autotune(ctx, inst_p["inst"])
                 for inst_p in prep} if not args.no_autotune else {})
+    # measured pipe throughputs of this GPU (microbenchmark kernels, a few ms)
+    pipes = wos.wos_measure_pipes(ctx)
     # warm-up: truncation ranks from the spectra, step counts from stats
     steps_per_inst = []
     for p in prep:
@@ -450,6 +452,8 @@ def run_gpu(args, rank: int, world: int, dist):
     walk_roof = {"kernel": "walk_kernel", "bound": "alu", "achieved": achieved,
                  "peak": ALU_PEAK_GOPS, "unit": "Gop/s", "frac": achieved / ALU_PEAK_GOPS,
                  "traffic": traffic,
+                 "measured_issue_peak": pipes["issue"] / 1e9,
+                 "frac_of_measured_issue": achieved / (pipes["issue"] / 1e9),
                  "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz "
                                 "(recipe unit counts and max clock)",
                  "unit_of_work": "one step of the chain: 42 (box) / 46 (annulus) "
@@ -544,6 +548,9 @@ def run_gpu(args, rank: int, world: int, dist):
         "e2e": {"value": e2e_value, "unit": "walks/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "clocks": clk,
+        "pipe_peaks": {"unit": "lane-ops/s (measured; per SM per clock at 2070 MHz beside)",
+                       **{k: v for k, v in pipes.items()},
+                       "per_sm_clk": {k: v / (sms * 2.07e9) for k, v in pipes.items()}},
     }
     if not args.no_cpu_baseline and world == 1:
         insts = [p["inst"] for p in prep]

@@ -456,6 +456,26 @@ wos_status wos_op_svd_batched(wos_context *ctx, int32_t n,
 enum { WOS_SVD_AUTO = 0, WOS_SVD_GRID = 1, WOS_SVD_CLUSTER = 2 };
 wos_status wos_set_svd_path(wos_context *ctx, int32_t path);
 
+/* Measured throughput of the execution pipes the kernels lean on, from
+ * microbenchmark kernels on the context's device (a few milliseconds; SMs x
+ * 8 CTAs of 256 threads, eight independent chains of one PTX operation per
+ * thread, CUDA events around a launch after a warm-up launch):
+ *   out[WOS_PIPE_FFMA]       fma.rn.f32 per second (lanes)
+ *   out[WOS_PIPE_MUFU]       sin.approx.f32 and cos.approx.f32 per second
+ *   out[WOS_PIPE_IMAD_WIDE]  mul.wide.u32 (each followed by the xor of its
+ *                            halves: a Philox half-round) per second
+ *   out[WOS_PIPE_LOP3]       lop3.b32 per second
+ *   out[WOS_PIPE_DFMA]       fma.rn.f64 per second
+ *   out[WOS_PIPE_ISSUE]      instructions per second of an fma.rn.f32 /
+ *                            lop3.b32 alternation (two pipes: the issue limit)
+ * out: host, WOS_PIPE_COUNT doubles; stream as elsewhere (the call waits).
+ * Errors: WOS_INVALID_ARG, WOS_OOM, WOS_CUDA_ERROR. */
+enum {
+    WOS_PIPE_FFMA = 0, WOS_PIPE_MUFU = 1, WOS_PIPE_IMAD_WIDE = 2, WOS_PIPE_LOP3 = 3,
+    WOS_PIPE_DFMA = 4, WOS_PIPE_ISSUE = 5, WOS_PIPE_COUNT = 6
+};
+wos_status wos_measure_pipes(wos_context *ctx, double *out, void *stream);
+
 /* r-TSVD reconstruction (paper Sec. 2, Eq. (u1r); Sec. 4.3, Eq.
  * (u_omega_M1_r_MC A); Sec. 5.1, Rem. (b and u0 simulations), Eq. (tsvd
  * solution simulations)):

@@ -16,7 +16,7 @@ CSRC = PKG / "csrc"
 OUT = PKG / "_lib"
 LIB = OUT / "libwos.so"
 SOURCES = ["wos_api.cu", "wos_svd.cu", "wos_noalloc.cu", "wos_batch.cu", "wos_serve.cu",
-           "wos_spectral.cu"]
+           "wos_spectral.cu", "wos_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -235,6 +235,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     L.wos_kernel_launches.restype = u64
     L.wos_kernel_launches.argtypes = [vp]
     L.wos_set_svd_path.argtypes = [vp, i32]
+    L.wos_measure_pipes.argtypes = [vp, vp, vp]
     L.wos_status_string.restype = ctypes.c_char_p
     L.wos_status_string.argtypes = [ctypes.c_int]
     L.wos_conductivity_sqrt.argtypes = [i32, vp, vp]
@@ -571,6 +572,15 @@ def wos_autotune_reset(ctx: Context) -> None:
 
 
 SVD_AUTO, SVD_GRID, SVD_CLUSTER = 0, 1, 2
+PIPES = ("ffma", "mufu", "imad_wide", "lop3", "dfma", "issue")
+
+
+def wos_measure_pipes(ctx: Context, stream=None) -> dict:
+    """Measured lane-operations per second of each pipe (see wos.h)."""
+    out = (ctypes.c_double * len(PIPES))()
+    _check(load().wos_measure_pipes(ctx.h, ctypes.byref(out), _stream(stream)),
+           "wos_measure_pipes", False)
+    return {k: float(out[q]) for q, k in enumerate(PIPES)}
 
 
 def wos_set_svd_path(ctx: Context, path: int) -> None:
