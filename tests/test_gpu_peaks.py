@@ -1,8 +1,7 @@
 """The pipe microbenchmarks (wos_measure_pipes): every rate measured and
-positive, in the order the unit counts give (FP32 FMA above the half-rate
-logic pipe, both far above the SFU and FP64 pipes), and per SM per clock
-within a factor of two of those unit counts at the maximum clock (FFMA 128,
-LOP3 64, MUFU 16, DFMA 2 lanes; 128 lanes issued)."""
+positive, the FP32 FMA and logic pipes far above the SFU and FP64 pipes, and
+per SM per clock within a factor of two of the unit counts at the maximum
+clock (FFMA 128, LOP3 64 or 128, MUFU 16, DFMA 2 lanes; 128 lanes issued)."""
 import pytest
 import torch
 
@@ -17,6 +16,7 @@ def test_pipe_rates_are_plausible():
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     per = {k: v / (sms * 2.07e9) for k, v in p.items()}
     assert all(v > 0 for v in p.values()), p
-    assert per["ffma"] > per["lop3"] > per["mufu"] > per["dfma"], per
-    for k, nominal in (("ffma", 128), ("lop3", 64), ("mufu", 16), ("dfma", 2), ("issue", 128)):
-        assert nominal / 2 <= per[k] <= nominal * 2, (k, per[k])
+    assert min(per["ffma"], per["lop3"]) > per["mufu"] > per["dfma"], per
+    for k, lo, hi in (("ffma", 64, 256), ("lop3", 32, 256), ("mufu", 8, 32), ("dfma", 1, 4),
+                      ("issue", 64, 256)):
+        assert lo <= per[k] <= hi, (k, per[k])
