@@ -266,9 +266,10 @@ def run_gpu(args, rank: int, world: int, dist):
     # the SVD stream runs at high priority: when a step's walk launch drains,
     # the block scheduler places the SVD's clusters before the next step's
     # walk blocks, which fill the rest of the GPU (steps pipeline)
-    # two SVD streams, alternated by step, so that consecutive steps' SVDs
-    # (each a latency-bound cluster launch on a few SMs) overlap each other too
-    streams = [torch.cuda.Stream(device=dev, priority=-1) for _ in range(2)]
+    # several SVD streams (three by default), taken in turn by the steps, so
+    # that consecutive steps' SVDs (each a latency-bound cluster launch on a
+    # few SMs) overlap each other too
+    streams = [torch.cuda.Stream(device=dev, priority=-1) for _ in range(args.svd_streams)]
     build_stream = torch.cuda.Stream(device=dev)
     # the project's autotuner picks the launch configuration of each
     # instance's class (precision, dimension, kernel kind) on a bounded sample
@@ -528,8 +529,8 @@ def run_gpu(args, rank: int, world: int, dist):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "schedule": "pipelined: step k+1's walk launches (build stream) overlap step k's "
-                    "SVD and reconstructions (two high-priority SVD streams, alternated by "
-                    "step); L2 flushed before every step's walks",
+                    "SVD and reconstructions (%d high-priority SVD streams taken in turn); "
+                    "L2 flushed before every step's walks" % args.svd_streams,
         "step_latency_ms": step_latency_ms,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": describe(args.workload),
@@ -897,6 +898,8 @@ def main():
     ap.add_argument("--svd-path", choices=list(SVD_PATHS), default="auto",
                     help="SVD factorisation kernels: auto (cluster kernel when the "
                          "operator fits it) or grid (grid-wide kernels)")
+    ap.add_argument("--svd-streams", type=int, default=3,
+                    help="SVD streams the pipelined steps alternate over")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default launch configuration (profiling: no trial launches)")
     ap.add_argument("--batch-scale", type=float, default=1.0,
