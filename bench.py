@@ -8,10 +8,14 @@ points, N = 1e5 walks per point, eps = 1e-5, FP32 walks): the Monte Carlo
 operator build (MC-REM), the FP64 one-sided Jacobi SVD of the Gamma_1 block
 and the TSVD reconstruction from measurements with 1 % Gaussian noise.
 
-Prints one JSON line (metric, value = walks/s over all GPUs, roofline of the
-walk kernel, CPU baseline = the FP64 oracle on the host cores, e2e = the same
-through the public API with host buffers).  ``--impl reference`` times the
-CPU oracle on a bounded sample of the same workload instead.
+The timed steps pipeline: step k + 1's walk launches overlap step k's SVD
+and reconstructions, which run on high-priority SVD streams taken in turn;
+``step_latency_ms`` is one step alone.  Prints one JSON line (metric, value =
+walks/s over all GPUs, roofline of the walk kernel and of the SVD
+factorisation, measured pipe rates, CPU baseline = the FP64 oracle on the
+host cores, e2e = the same steps through the public API with host buffers).
+``--impl reference`` times the CPU oracle on a bounded sample of the same
+workload instead.
 """
 from __future__ import annotations
 

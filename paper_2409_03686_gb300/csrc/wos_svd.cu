@@ -996,8 +996,8 @@ int cluster_fit(const wos_context *ctx, int m, int n, int pre)
     const ClLayout L = cl_layout(m, n, pre, CL);
     if (L.PP > kClWarps || L.total > size_t(wos::ctx_max_smem(ctx)))
         return 0;
-    // every launch may use up to the opt-in maximum (set once, so that
-    // concurrent callers never see a smaller limit)
+    // every launch may use up to the opt-in maximum (always the same value,
+    // so that concurrent callers never see a smaller limit)
     cudaFuncSetAttribute(svd_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute(svd_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          wos::ctx_max_smem(ctx));

@@ -228,3 +228,34 @@ def test_cluster_and_grid_kernels_agree(shape):
     for r in _gaps(sg_, 16):
         np.testing.assert_allclose(Ua[:, :r] @ Ua[:, :r].T, Ug[:, :r] @ Ug[:, :r].T, atol=1e-8)
     assert abs(swa - swg) <= 2
+
+
+@pytest.mark.parametrize("shape", [(1, 3, 1), (2, 3, 1), (1, 4, 3), (3, 5, 2), (5, 7, 5),
+                                   (31, 40, 31), (2, 40, 33)])
+def test_degenerate_shapes(shape, svd_path):
+    """One row, one column, square, n just below and above the QR threshold
+    (31, 33), a wide operator with two points: singular values as LAPACK's,
+    B reproduced, orthonormal vectors."""
+    M_D, M_tot, M_1 = shape
+    N = 5000
+    C = W.synthetic_counts(M_D, M_tot, N, seed=sum(shape))
+    g1 = np.zeros(M_tot, np.uint8)
+    g1[:M_1] = 1
+    sigma = np.full(M_tot, 2 * np.pi / M_tot)
+    nu = np.full(M_D, 1 / np.sqrt(M_D))
+    (U, s, V, sweeps), (Uo, so, Vo), _ = _svd_pair(C, N, g1, sigma, nu)
+    B = O.operator_B(C, N, g1, nu, sigma)
+    ref = np.linalg.svd(B, compute_uv=False)
+    np.testing.assert_allclose(s, ref, rtol=1e-12, atol=1e-15 * ref[0])
+    np.testing.assert_allclose(U @ np.diag(s) @ V.T, B, atol=1e-13 * ref[0])
+    k = len(s)
+    np.testing.assert_allclose(U.T @ U, np.eye(k), atol=1e-12)
+    np.testing.assert_allclose(V.T @ V, np.eye(k), atol=1e-12)
+
+
+def test_svd_path_setting_is_checked():
+    for bad in (-1, 3, 100):
+        with pytest.raises(wos.WosError) as e:
+            wos.wos_set_svd_path(ctx(), bad)
+        assert e.value.code == 1
+    wos.wos_set_svd_path(ctx(), wos.SVD_AUTO)
