@@ -29,8 +29,8 @@
  * Chain specification shared (as a specification, not as code) with the GPU:
  *   key     = (seed & 0xffffffff, seed >> 32)
  *   counter = (b, walk & 0xffffffff, walk >> 32, stream), walk = i*N + k
- *   a step uses wps = (d == 2 ? 1 : 2) * wpu words, wpu = 1 (24-bit
- *   uniforms u = (w >> 8) 2^-24) or 2 (53-bit u = (w0 2^21 + (w1 >> 11))
+ *   a step uses wps = (d == 2 ? 1 : 2) * wpu words, wpu = 1 (23-bit
+ *   uniforms u = (w >> 9) 2^-23) or 2 (53-bit u = (w0 2^21 + (w1 >> 11))
  *   2^-53); Philox block b serves steps b*G .. b*G+G-1 with G = 4 / wps.
  *   d = 2: U = (cos 2 pi u, sin 2 pi u)
  *   d = 3: z = 1 - 2 u1, phi = 2 pi u2, U = (s cos phi, s sin phi, z),
@@ -79,11 +79,11 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* Uniform on [0, 1) from one word (24 bits) or two words (53 bits). */
+/* Uniform on [0, 1) from one word (23 bits) or two words (53 bits). */
 static double uniform_from_words(const uint32_t *w, int wpu)
 {
     if (wpu == 1)
-        return (double)(w[0] >> 8) * 0x1p-24;
+        return (double)(w[0] >> 9) * 0x1p-23;
     uint64_t m = ((uint64_t)w[0] << 21) | (uint64_t)(w[1] >> 11);
     return (double)m * 0x1p-53;
 }

@@ -53,7 +53,7 @@ typedef struct {
     uint32_t stream;    /* fourth Philox counter word */
     uint32_t N;         /* walks per point (walk id = i * N + k) */
     uint32_t step_cap;  /* walks reaching it are left unterminated */
-    int32_t words_per_uniform; /* 1: 24-bit, 2: 53-bit uniforms */
+    int32_t words_per_uniform; /* 1: 23-bit, 2: 53-bit uniforms */
     /* mapped = 1: walk-on-spheres in y = S^{-1} x, whose domain S^{-1} D is a
      * convex polytope: dist_y(y) = min_f (plane_d[f] - plane_n[f] . y) */
     int32_t mapped;

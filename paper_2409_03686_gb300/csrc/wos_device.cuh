@@ -439,14 +439,17 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1,
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-// Uniform on [0, 1): 24 bits of one word (FP32 walks) or 53 bits of two
-// words (FP64 walks).
+// Uniform on [0, 1): 23 bits of one word (FP32 walks) or 53 bits of two
+// words (FP64 walks).  The FP32 uniform is built from the bits, not by a
+// conversion: 1 + (w >> 9) 2^-23 has exponent 0 and those 23 bits as its
+// mantissa, so subtracting 1 leaves (w >> 9) 2^-23 exactly (a logic op and
+// an add on the FMA pipe instead of an I2F on the conversion unit).
 template <typename Real> struct Uniform;
 template <> struct Uniform<float> {
     static constexpr int kWords = 1;
     __device__ __forceinline__ static float get(const uint32_t *w)
     {
-        return float(w[0] >> 8) * 0x1p-24f;
+        return __uint_as_float(0x3f800000u | (w[0] >> 9)) - 1.0f;
     }
 };
 template <> struct Uniform<double> {
@@ -478,10 +481,9 @@ __device__ __forceinline__ void direction(const uint32_t *w, Real *U)
     if (DIM == 2) {
         Real s, c;
         if constexpr (sizeof(Real) == 4) {
-            // 2u - 1 = (w >> 8) 2^-23 - 1 in one exact FMA (the same value as
-            // Uniform<float>::get doubled, less one); then the SFU path of
-            // w_sincospi
-            const float t = fmaf(float(w[0] >> 8), 0x1p-23f, -1.0f);
+            // 2u - 1 straight from the bits: 2 + (w >> 9) 2^-22 less 3
+            // (exact); then the SFU path of w_sincospi
+            const float t = __uint_as_float(0x40000000u | (w[0] >> 9)) - 3.0f;
             float ss, cc;
             __sincosf(3.14159265358979f * t, &ss, &cc);
             s = -ss;

@@ -29,13 +29,13 @@ def test_philox_known_answers(ctr, key, expect):
 
 
 def test_philox_uniformity_and_independence():
-    # 24-bit uniforms from 4 * 20000 words: chi^2 over 64 bins, and lag-1
-    # correlation between consecutive counters.
+    # 23-bit uniforms (the FP32 walks' map) from 4 * 20000 words: chi^2 over
+    # 64 bins, and lag-1 correlation between consecutive counters.
     words = []
     for b in range(20000):
         words.extend(O.philox([b, 7, 0, 0], [123, 456]))
     w = np.array(words, dtype=np.uint64)
-    u = (w >> np.uint64(8)).astype(np.float64) * 2.0 ** -24
+    u = (w >> np.uint64(9)).astype(np.float64) * 2.0 ** -23
     assert u.min() >= 0.0 and u.max() < 1.0
     h, _ = np.histogram(u, bins=64, range=(0, 1))
     e = len(u) / 64
@@ -58,15 +58,15 @@ def _first_step_by_hand(inst, i, k):
         if inst.fp64:
             u = ((words[0] << 21) | (words[1] >> 11)) * 2.0 ** -53
         else:
-            u = (words[0] >> 8) * 2.0 ** -24
+            u = (words[0] >> 9) * 2.0 ** -23
         U = np.array([math.cos(2 * math.pi * u), math.sin(2 * math.pi * u)])
     else:
         if inst.fp64:
             u1 = ((words[0] << 21) | (words[1] >> 11)) * 2.0 ** -53
             u2 = ((words[2] << 21) | (words[3] >> 11)) * 2.0 ** -53
         else:
-            u1 = (words[0] >> 8) * 2.0 ** -24
-            u2 = (words[1] >> 8) * 2.0 ** -24
+            u1 = (words[0] >> 9) * 2.0 ** -23
+            u2 = (words[1] >> 9) * 2.0 ** -23
         z = 1 - 2 * u1
         s = math.sqrt(1 - z * z)
         U = np.array([s * math.cos(2 * math.pi * u2), s * math.sin(2 * math.pi * u2), z])
