@@ -22,6 +22,11 @@
 //    more steps at the price of more idle lane-steps after a walk stops.
 //  * The Philox counter of step n of walk w is (n / G, w lo, w hi, stream):
 //    results do not depend on scheduling or on the batch a walk runs in.
+//  * Kinds whose distance depends on x - c only (disc / ball, box, annulus /
+//    shell) walk in coordinates relative to the centre c: the start point is
+//    shifted once per tile and the exit point back once per walk, which
+//    takes a subtraction per coordinate off every step (the same bits when
+//    c = 0; otherwise a rounding of the sum in another place).
 //  * A finished lane only pushes its stopped point into a per-warp queue in
 //    shared memory; once 32 are queued the whole warp classifies them (pi of
 //    App. A) and tallies them at full lane efficiency.
@@ -93,10 +98,20 @@ template <typename Real, int DIM> struct Steps {
 template <typename Real, int DIM, int KIND>
 __device__ __forceinline__ Real walk_dist(const Geom<Real> &g, const Real *x)
 {
-    if (KIND == kSphereOnly)
-        return sphere_dist<Real, DIM>(g, x);
-    if (KIND == kBoxOnly)
-        return box_dist_value<Real, DIM>(g, x);
+    if (KIND == kSphereOnly) {  // x relative to the centre
+        Real s = x[0] * x[0];
+#pragma unroll
+        for (int a = 1; a < DIM; ++a)
+            s = fma(x[a], x[a], s);
+        return g.R - w_sqrt(s);
+    }
+    if (KIND == kBoxOnly) {  // x relative to the centre
+        Real best = g.h[0] - w_fabs(x[0]);
+#pragma unroll
+        for (int a = 1; a < DIM; ++a)
+            best = w_min(best, g.h[a] - w_fabs(x[a]));
+        return best;
+    }
     if (KIND == kSphereHoles) {
         Real r = sphere_dist<Real, DIM>(g, x);
         for (int h = 0; h < g.n_holes; ++h)
@@ -124,8 +139,7 @@ __device__ __forceinline__ Real walk_dist(const Geom<Real> &g, const Real *x)
         Real s = Real(0);
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-            Real d = x[a] - g.c[a];
-            s += d * d;
+            s += x[a] * x[a];  // x relative to the centre
         }
         const Real rho = w_sqrt(s);
         return w_min(g.R - rho, rho - g.hr[0]);
@@ -319,6 +333,11 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
                     for (int a = 0; a < DIM; ++a)
                         tile_x[a] = T.points_r ? T.points_r[size_t(ti) * DIM + a]
                                                : Real(T.points[size_t(ti) * DIM + a]);
+                    if (KIND == kSphereOnly || KIND == kBoxOnly || KIND == kAnnulus) {
+#pragma unroll
+                        for (int a = 0; a < DIM; ++a)
+                            tile_x[a] -= T.g.c[a];  // walk relative to the centre
+                    }
                     if (KIND == kMapped) {  // the walk runs in y = S^{-1} x
                         Real y[DIM];
 #pragma unroll
@@ -422,6 +441,12 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
         const unsigned fin_mask = __ballot_sync(FULL, fin);
         if (fin_mask == 0u)
             continue;
+        if ((KIND == kSphereOnly || KIND == kBoxOnly || KIND == kAnnulus) && fin) {
+            const WalkInst<Real> &I = inst(linst);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a)
+                X[a] += I.g.c[a];  // exit point back in x
+        }
         if (KIND == kMapped && fin) {  // exit point back in x = S y
             const WalkInst<Real> &I = inst(linst);
             Real xo[DIM];
