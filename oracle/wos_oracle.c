@@ -29,9 +29,12 @@
  * Chain specification shared (as a specification, not as code) with the GPU:
  *   key     = (seed & 0xffffffff, seed >> 32)
  *   counter = (b, walk & 0xffffffff, walk >> 32, stream), walk = i*N + k
- *   a step uses wps = (d == 2 ? 1 : 2) * wpu words, wpu = 1 (23-bit
- *   uniforms u = (w >> 9) 2^-23) or 2 (53-bit u = (w0 2^21 + (w1 >> 11))
- *   2^-53); Philox block b serves steps b*G .. b*G+G-1 with G = 4 / wps.
+ *   FP32 2-D walks (wpu = 1, d = 2): G = 5 steps per Philox block, step j
+ *   of the block takes u = ((B >> 23 j) mod 2^23) 2^-23 from the 128-bit
+ *   B = w0 + 2^32 w1 + 2^64 w2 + 2^96 w3.  Otherwise a step uses
+ *   wps = (d == 2 ? 1 : 2) * wpu words, wpu = 1 (23-bit uniforms
+ *   u = (w >> 9) 2^-23) or 2 (53-bit u = (w0 2^21 + (w1 >> 11)) 2^-53), and
+ *   G = 4 / wps.  Philox block b serves steps b*G .. b*G+G-1.
  *   d = 2: U = (cos 2 pi u, sin 2 pi u)
  *   d = 3: z = 1 - 2 u1, phi = 2 pi u2, U = (s cos phi, s sin phi, z),
  *          s = sqrt(1 - z^2).
@@ -77,6 +80,23 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
         c0 = n0; c1 = n1; c2 = n2; c3 = n3;
     }
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Steps served by one Philox block (see the chain specification above). */
+static int steps_per_block(int d, int wpu)
+{
+    return (d == 2 && wpu == 1) ? 5 : 4 / ((d == 2 ? 1 : 2) * wpu);
+}
+
+/* The 23-bit window j (bits 23 j .. 23 j + 22) of the 128-bit block, as a
+ * uniform on [0, 1). */
+static double window23_uniform(const uint32_t *w, int j)
+{
+    const int off = 23 * j, q = off / 32, r = off % 32;
+    uint64_t pair = (uint64_t)w[q];
+    if (q + 1 < 4)
+        pair |= (uint64_t)w[q + 1] << 32;
+    return (double)((pair >> r) & 0x7FFFFFu) * 0x1p-23;
 }
 
 /* Uniform on [0, 1) from one word (23 bits) or two words (53 bits). */
@@ -368,7 +388,8 @@ static int orc_walk_mapped(const orc_instance *I, const double *x0, uint64_t wal
     const int d = I->dom.dim;
     const int wpu = I->words_per_uniform;
     const int wps = (d == 2 ? 1 : 2) * wpu;
-    const int G = 4 / wps;
+    const int G = steps_per_block(d, wpu);
+    const int packed = d == 2 && wpu == 1;
     const uint32_t key[2] = {(uint32_t)I->seed, (uint32_t)(I->seed >> 32)};
     double Y[3] = {0.0, 0.0, 0.0};
     for (int a = 0; a < d; ++a)
@@ -398,9 +419,10 @@ static int orc_walk_mapped(const orc_instance *I, const double *x0, uint64_t wal
                                (uint32_t)(walk >> 32), I->stream};
             orc_philox4x32_10(ctr, key, words);
         }
-        const uint32_t *w = words + (n % (uint32_t)G) * (uint32_t)wps;
+        const uint32_t *w = words + (packed ? 0u : (n % (uint32_t)G) * (uint32_t)wps);
         if (d == 2) {
-            double u = uniform_from_words(w, wpu);
+            double u = packed ? window23_uniform(words, (int)(n % (uint32_t)G))
+                              : uniform_from_words(w, wpu);
             Y[0] += r * cos(2.0 * M_PI * u);
             Y[1] += r * sin(2.0 * M_PI * u);
         } else {
@@ -423,7 +445,8 @@ int orc_walk(const orc_instance *I, const double *x0, uint64_t walk,
     const int d = I->dom.dim;
     const int wpu = I->words_per_uniform;
     const int wps = (d == 2 ? 1 : 2) * wpu;
-    const int G = 4 / wps;
+    const int G = steps_per_block(d, wpu);
+    const int packed = d == 2 && wpu == 1;
     const uint32_t key[2] = {(uint32_t)I->seed, (uint32_t)(I->seed >> 32)};
     double X[3] = {x0[0], x0[1], d == 3 ? x0[2] : 0.0};
     uint32_t words[4] = {0, 0, 0, 0};
@@ -440,10 +463,11 @@ int orc_walk(const orc_instance *I, const double *x0, uint64_t walk,
                                (uint32_t)(walk >> 32), I->stream};
             orc_philox4x32_10(ctr, key, words);
         }
-        const uint32_t *w = words + (n % (uint32_t)G) * (uint32_t)wps;
+        const uint32_t *w = words + (packed ? 0u : (n % (uint32_t)G) * (uint32_t)wps);
         double U[3];
         if (d == 2) {
-            double u = uniform_from_words(w, wpu);
+            double u = packed ? window23_uniform(words, (int)(n % (uint32_t)G))
+                              : uniform_from_words(w, wpu);
             U[0] = cos(2.0 * M_PI * u);
             U[1] = sin(2.0 * M_PI * u);
             U[2] = 0.0;

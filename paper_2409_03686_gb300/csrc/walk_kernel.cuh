@@ -13,7 +13,8 @@
 //    batch of instances of one precision and dimension (records in global
 //    memory, each lane reading its own walk's record through L1).
 //  * Every lane owns one walk at a time.  Walks advance in groups of
-//    group_blocks x G steps, G steps per Philox4x32-10 block (G = 4 words /
+//    group_blocks x G steps, G steps per Philox4x32-10 block (G = 5 for FP32
+//    2-D walks, which take 23-bit windows of the 128 bits, else 4 words /
 //    words per step), so all lanes call Philox together; a lane whose walk
 //    stops mid-group idles to the group's end.  At a group boundary the
 //    finished lanes are refilled from the warp's tile (warp-level refill:
@@ -90,10 +91,24 @@ template <typename Real> struct WalkParams {
 };
 
 template <typename Real, int DIM> struct Steps {
-    // steps served by one Philox block
+    // steps served by one Philox block: five 23-bit windows for FP32 2-D
+    // walks, else whole words (one or two per uniform)
+    static constexpr bool kPacked = DIM == 2 && sizeof(Real) == 4;
     static constexpr int kWordsPerStep = (DIM == 2 ? 1 : 2) * Uniform<Real>::kWords;
-    static constexpr int G = 4 / kWordsPerStep;
+    static constexpr int G = kPacked ? kPacked2dSteps : 4 / kWordsPerStep;
 };
+
+// Direction of step s of a Philox block.
+template <typename Real, int DIM>
+__device__ __forceinline__ void step_direction(const uint32_t *w, int s, Real *U)
+{
+    if constexpr (Steps<Real, DIM>::kPacked) {
+        const uint32_t win = window23(w, s);
+        direction<Real, DIM>(&win, U);
+    } else {
+        direction<Real, DIM>(w + s * Steps<Real, DIM>::kWordsPerStep, U);
+    }
+}
 
 template <typename Real, int DIM, int KIND>
 __device__ __forceinline__ Real walk_dist(const Geom<Real> &g, const Real *x)
@@ -207,7 +222,6 @@ __global__ void __launch_bounds__(256, 4)
 walk_kernel(const __grid_constant__ WalkParams<Real> p)
 {
     constexpr int G = Steps<Real, DIM>::G;
-    constexpr int WPS = Steps<Real, DIM>::kWordsPerStep;
     constexpr unsigned FULL = 0xFFFFFFFFu;
     extern __shared__ uint32_t smem[];
     const WalkInst<Real> *__restrict__ insts = p.insts;
@@ -412,7 +426,7 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
                         const bool go = !stop && !(r <= I.eps);
                         stop = !go;
                         Real U[DIM];
-                        direction<Real, DIM>(w + s * WPS, U);
+                        step_direction<Real, DIM>(w, s, U);
                         step_move<Real, DIM>(I.S, U, go ? r : Real(0), X);
                         nstep += go ? 1u : 0u;
                     }
@@ -430,7 +444,7 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
                         capped = capped || (!stop && !at_eps && at_cap);
                         stop = stop || !go;
                         Real U[DIM];
-                        direction<Real, DIM>(w + s * WPS, U);
+                        step_direction<Real, DIM>(w, s, U);
                         step_move<Real, DIM>(I.S, U, go ? r : Real(0), X);
                         nstep += go ? 1u : 0u;
                     }

@@ -181,7 +181,7 @@ inline int32_t refill_min_of(const wos_opts &o)
     return o.refill_min > 1 ? std::min(o.refill_min, 32) : 1;
 }
 
-// Default group: about 16 steps (4 Philox blocks of 4 steps for FP32 2-D
+// Default group: about 16 steps (3 Philox blocks of 5 steps for FP32 2-D
 // walks, 8 of 2 for FP32 3-D and FP64 2-D, 16 of 1 for FP64 3-D); measured
 // on the square, annulus, ball and cube operator builds, 12-20 steps per
 // group beat 4 by 20-30 % and longer groups lose again.
@@ -192,8 +192,8 @@ inline int32_t group_blocks_of(const wos_opts &o, int dim)
 {
     if (o.group_blocks > 0)
         return std::min(o.group_blocks, 16);
-    const int words = (dim == 2 ? 1 : 2) * Uniform<Real>::kWords;
-    return std::max(1, kDefaultGroupSteps / (4 / words));
+    const int G = dim == 2 ? Steps<Real, 2>::G : Steps<Real, 3>::G;
+    return std::max(1, (kDefaultGroupSteps + G / 2) / G);
 }
 
 }  // namespace wos

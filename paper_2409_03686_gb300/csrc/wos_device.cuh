@@ -473,6 +473,21 @@ __device__ __forceinline__ void w_sincospi(float x, float *s, float *c)
 }
 __device__ __forceinline__ void w_sincospi(double x, double *s, double *c) { sincospi(x, s, c); }
 
+// FP32 2-D walks take five 23-bit uniforms from one Philox block: step j of
+// the block reads bits 23j .. 23j + 22 of the 128-bit number w0 + 2^32 w1 +
+// 2^64 w2 + 2^96 w3 (bits 115..127 are unused), one funnel shift each.
+constexpr int kPacked2dSteps = 5;
+__device__ __forceinline__ uint32_t window23(const uint32_t *w, int j)
+{
+    switch (j) {  // j is a constant once the step loop is unrolled
+    case 0: return w[0];
+    case 1: return __funnelshift_r(w[0], w[1], 23);
+    case 2: return __funnelshift_r(w[1], w[2], 14);
+    case 3: return __funnelshift_r(w[2], w[3], 5);
+    default: return __funnelshift_r(w[2], w[3], 28);
+    }
+}
+
 // U uniform on S^{d-1}: d = 2 (cos 2 pi u, sin 2 pi u); d = 3 Archimedes:
 // z = 1 - 2 u1, (s cos 2 pi u2, s sin 2 pi u2, z), s = sqrt(1 - z^2).
 template <typename Real, int DIM>
@@ -481,9 +496,10 @@ __device__ __forceinline__ void direction(const uint32_t *w, Real *U)
     if (DIM == 2) {
         Real s, c;
         if constexpr (sizeof(Real) == 4) {
-            // 2u - 1 straight from the bits: 2 + (w >> 9) 2^-22 less 3
-            // (exact); then the SFU path of w_sincospi
-            const float t = __uint_as_float(0x40000000u | (w[0] >> 9)) - 3.0f;
+            // w[0] holds the step's 23-bit window in its low bits: 2u - 1 =
+            // 2 + window 2^-22 less 3 (exact, one logic op builds the float);
+            // then the SFU path of w_sincospi
+            const float t = __uint_as_float(0x40000000u | (w[0] & 0x7fffffu)) - 3.0f;
             float ss, cc;
             __sincosf(3.14159265358979f * t, &ss, &cc);
             s = -ss;

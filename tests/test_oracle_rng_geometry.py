@@ -36,6 +36,16 @@ def test_philox_uniformity_and_independence():
         words.extend(O.philox([b, 7, 0, 0], [123, 456]))
     w = np.array(words, dtype=np.uint64)
     u = (w >> np.uint64(9)).astype(np.float64) * 2.0 ** -23
+    # and the five 23-bit windows of each 128-bit block (FP32 2-D walks)
+    blocks = np.array(words, dtype=object).reshape(-1, 4)
+    big = [int(b[0]) | (int(b[1]) << 32) | (int(b[2]) << 64) | (int(b[3]) << 96) for b in blocks]
+    win = np.array([(v >> (23 * j)) & 0x7FFFFF for v in big for j in range(5)],
+                   dtype=np.float64) * 2.0 ** -23
+    hw, _ = np.histogram(win, bins=64, range=(0, 1))
+    ew = len(win) / 64
+    assert float(((hw - ew) ** 2 / ew).sum()) < 63 + 6 * math.sqrt(2 * 63)
+    cw = np.corrcoef(win[:-1], win[1:])[0, 1]  # neighbouring windows of a block
+    assert abs(cw) < 6 / math.sqrt(len(win))
     assert u.min() >= 0.0 and u.max() < 1.0
     h, _ = np.histogram(u, bins=64, range=(0, 1))
     e = len(u) / 64
@@ -57,8 +67,8 @@ def _first_step_by_hand(inst, i, k):
     if inst.dim == 2:
         if inst.fp64:
             u = ((words[0] << 21) | (words[1] >> 11)) * 2.0 ** -53
-        else:
-            u = (words[0] >> 9) * 2.0 ** -23
+        else:  # step 0 of the block: bits 0..22 of the 128-bit block
+            u = (words[0] & 0x7FFFFF) * 2.0 ** -23
         U = np.array([math.cos(2 * math.pi * u), math.sin(2 * math.pi * u)])
     else:
         if inst.fp64:
@@ -86,6 +96,38 @@ def test_chain_counter_layout(make):
         assert el[0] == -1 and ns[0] == 1  # stopped by the cap after one move
         np.testing.assert_allclose(xe[0], _first_step_by_hand(inst, i, k),
                                    rtol=0, atol=1e-15)
+
+
+def _steps_by_hand(inst, i, k, n_steps):
+    """X_n of a FP32 2-D walk (i, k) recomputed step by step: step n takes
+    Philox block n // 5 and its 23-bit window n % 5 (bits 23 j .. 23 j + 22
+    of the 128-bit block)."""
+    S, _ = O.setup_S(inst.K)
+    wid = i * inst.N + k
+    x = np.array(inst.points[i], dtype=np.float64)
+    for n in range(n_steps):
+        words = O.philox([n // 5, wid & 0xFFFFFFFF, wid >> 32, inst.stream],
+                         [inst.seed & 0xFFFFFFFF, inst.seed >> 32])
+        big = words[0] | (words[1] << 32) | (words[2] << 64) | (words[3] << 96)
+        u = ((big >> (23 * (n % 5))) & 0x7FFFFF) * 2.0 ** -23
+        r = O.dist(inst.domain, inst.partition, x)[0]
+        x = x + r * (S @ np.array([math.cos(2 * math.pi * u), math.sin(2 * math.pi * u)]))
+    return x
+
+
+def test_packed_windows_of_fp32_2d_walks():
+    """Every window of a block and the move to the next block: the oracle's
+    walk stopped by a cap of 1..7 steps equals the chain recomputed by hand
+    (square, FP32 walks, anisotropic K)."""
+    inst = W.square_config(N=1000, eps=1e-9).replace(seed=0x1234567890AB, stream=5)
+    for cap in range(1, 8):
+        ic = inst.replace(step_cap=cap)
+        for i, k in [(0, 0), (2, 31)]:
+            xe, el, ns = O.walks(ic, [i], [k])
+            if ns[0] < cap:  # stopped inside the eps shell first
+                continue
+            np.testing.assert_allclose(xe[0], _steps_by_hand(ic, i, k, cap), rtol=0,
+                                       atol=1e-14)
 
 
 def test_setup_S_is_normalised_square_root():
