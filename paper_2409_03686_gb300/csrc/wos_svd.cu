@@ -912,15 +912,23 @@ struct SvdProb {
 
 int rpt_of(int m)
 {
-    return m <= kPairThreads ? 1 : m <= 2 * kPairThreads ? 2 : m <= 4 * kPairThreads ? 4 : 8;
+    // the fewest rows per thread that hold a column (a masked-off row still
+    // costs its warp's FP64 instruction)
+    const int need = (m + kPairThreads - 1) / kPairThreads;
+    return need <= 6 ? (need < 1 ? 1 : need) : 8;
 }
 
 const void *jacobi_kernel_rpt(int rpt)
 {
-    if (rpt == 1) return reinterpret_cast<const void *>(&jacobi_kernel<1>);
-    if (rpt == 2) return reinterpret_cast<const void *>(&jacobi_kernel<2>);
-    if (rpt == 4) return reinterpret_cast<const void *>(&jacobi_kernel<4>);
-    return reinterpret_cast<const void *>(&jacobi_kernel<8>);
+    switch (rpt) {
+    case 1: return reinterpret_cast<const void *>(&jacobi_kernel<1>);
+    case 2: return reinterpret_cast<const void *>(&jacobi_kernel<2>);
+    case 3: return reinterpret_cast<const void *>(&jacobi_kernel<3>);
+    case 4: return reinterpret_cast<const void *>(&jacobi_kernel<4>);
+    case 5: return reinterpret_cast<const void *>(&jacobi_kernel<5>);
+    case 6: return reinterpret_cast<const void *>(&jacobi_kernel<6>);
+    default: return reinterpret_cast<const void *>(&jacobi_kernel<8>);
+    }
 }
 
 // Cooperative launches over groups of problems whose CTAs are co-resident:
@@ -1181,7 +1189,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     // Jacobi: one cooperative launch per class of rows per thread (and per
     // group of co-resident problems); the CTAs are shared in proportion to
     // the pairs when the batch is larger than the GPU
-    for (int rpt : {1, 2, 4, 8}) {
+    for (int rpt : {1, 2, 3, 4, 5, 6, 8}) {
         if (e != cudaSuccess)
             break;
         std::vector<int> idx;
