@@ -437,8 +437,11 @@ __device__ bool wait_at_least(const unsigned *a, unsigned want, unsigned *status
     }
 }
 
-// Sum of one double per thread over the block, returned to every thread (the
-// partial sums are added in the same order by every thread).
+// Sum of one double per thread over the block, returned to every thread.
+// One thread adds the warps' partial sums (a warp FP64 instruction holds its
+// sub-partition's FP64 unit for 64 cycles whatever its active lanes, so the
+// other warps must not repeat the additions) and publishes the total in
+// red[32]; red holds at least 33 doubles.
 __device__ double block_sum(double v, double *red)
 {
     v = warp_sum(v);
@@ -447,10 +450,14 @@ __device__ double block_sum(double v, double *red)
     if (lane == 0)
         red[wid] = v;
     __syncthreads();
-    double s = 0.0;
-    for (int q = 0; q < int(blockDim.x >> 5); ++q)
-        s += red[q];
-    return s;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < int(blockDim.x >> 5); ++q)
+            s += red[q];
+        red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
 }
 
 // Index of the largest value over the block (lowest index on ties), returned
@@ -493,7 +500,7 @@ __device__ int block_argmax(double v, int i, double *red, int *ired)
 // (xLAQP2's test).  Barriers are bounded (WOS_DEVICE_TIMEOUT).
 __device__ void qrcp_body(const QrWork &q, const int b, const int G)
 {
-    __shared__ double red[32];
+    __shared__ double red[36];  // warp partials, [32] a block sum, [33..35] scalars
     __shared__ int ired[32];
     const int tid = threadIdx.x;
     const int m = q.m, n = q.n;
@@ -553,11 +560,22 @@ __device__ void qrcp_body(const QrWork &q, const int b, const int G)
                 xn2 = fma(col[i], col[i], xn2);
             xn2 = block_sum(xn2, red);
             const double alpha = col[k];
+            // the scalars by two threads of two warps (tau, and the scale)
+            if (xn2 > 0.0 && (tid == 0 || tid == 32)) {
+                const double bt = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
+                if (tid == 0) {
+                    red[33] = bt;
+                    red[34] = (bt - alpha) / bt;
+                } else {
+                    red[35] = 1.0 / (alpha - bt);
+                }
+            }
+            __syncthreads();
             double tau = 0.0, beta = alpha;
             if (xn2 > 0.0) {
-                beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
-                tau = (beta - alpha) / beta;
-                const double scal = 1.0 / (alpha - beta);
+                beta = red[33];
+                tau = red[34];
+                const double scal = red[35];
                 for (int i = k + 1 + tid; i < m; i += blockDim.x)
                     col[i] *= scal;
             }
@@ -597,12 +615,15 @@ __device__ void qrcp_body(const QrWork &q, const int b, const int G)
                     col[k] -= tw;
             }
             __syncthreads();
+            // |x|^2 - r^2, or an exact recomputation when cancellation has
+            // eaten half the digits (xLAQP2's test multiplied out: no
+            // division on the FP64 pipe)
             const double r = col[k], cn = q.cn[c];
             double t = 0.0;
             bool recompute = false;
             if (cn > 0.0) {
-                t = fmax(1.0 - (r * r) / cn, 0.0);
-                recompute = t * (cn / q.cn0[c]) <= kTol3z;
+                t = fmax(fma(-r, r, cn), 0.0);
+                recompute = t <= kTol3z * q.cn0[c];
             }
             if (recompute) {
                 double s = 0.0;
@@ -614,7 +635,7 @@ __device__ void qrcp_body(const QrWork &q, const int b, const int G)
                     q.cn0[c] = s;
                 }
             } else if (tid == 0) {
-                q.cn[c] = cn * t;
+                q.cn[c] = t;
             }
             __syncthreads();
         }
