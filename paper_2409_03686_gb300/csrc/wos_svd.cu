@@ -46,7 +46,8 @@ struct SvdWork {
     int n_pad;        // n rounded up to even (a dummy column when odd)
     unsigned *bar;    // [0] arrive count, [1] generation, [2..4] rotation
                       // counters of sweeps mod 3, [5] status, [6] sweeps,
-                      // [8..13] largest cos^2 of sweeps mod 3 (3 x uint64)
+                      // [8..13] per sweep mod 3 (uint64): 1 if a rotated pair
+                      // had cos^2 > kLast^2
     unsigned *ver;    // n_pad column versions (rounds finished per column)
 };
 
@@ -197,7 +198,7 @@ __device__ void jacobi_body(const SvdWork &w, const int bid, const int nblk)
             w.bar[2 + ((sweep + 1) % 3)] = 0u;
             maxcos[(sweep + 1) % 3] = 0ull;
         }
-        double my_cos2 = 0.0;  // largest cos^2 this CTA met in the sweep (thread 0)
+        bool my_big = false;  // a rotated pair had cos^2 > kLast^2 (thread 0)
         for (int r = 0; r < w.n_pad - 1; ++r) {
             const unsigned R = unsigned(sweep) * unsigned(w.n_pad - 1) + unsigned(r);
             for (int pr = bid; pr < half; pr += nblk) {
@@ -252,10 +253,11 @@ __device__ void jacobi_body(const SvdWork &w, const int bid, const int nblk)
                         double c = 1.0, sn = 0.0;
                         int rot_flag = 0;
                         // rotate when |ga| > tol sqrt(al be), tested squared
-                        if (al != 0.0 && be != 0.0 && ga * ga > (kTol * kTol) * (al * be)) {
+                        const double ab = al * be, g2 = ga * ga;
+                        if (al != 0.0 && be != 0.0 && g2 > (kTol * kTol) * ab) {
                             jacobi_rotation(al, be, ga, c, sn);
                             rot_flag = 1;
-                            my_cos2 = fmax(my_cos2, (ga * ga) / (al * be));
+                            my_big = my_big || g2 > (kLast * kLast) * ab;  // no division
                         }
                         cs[0] = c;
                         cs[1] = sn;
@@ -303,13 +305,12 @@ __device__ void jacobi_body(const SvdWork &w, const int bid, const int nblk)
                 }
             }
         }
-        if (tid == 0 && my_cos2 > 0.0)  // non-negative doubles order like their bits
-            atomicMax(maxcos + (sweep % 3), __double_as_longlong(my_cos2));
+        if (tid == 0 && my_big)
+            atomicMax(maxcos + (sweep % 3), 1ull);
         if (!grid_barrier(w.bar, unsigned(nblk)))
             return;
-        const double sweep_cos2 =
-            __longlong_as_double(*(volatile long long *)(maxcos + (sweep % 3)));
-        bool done = *(volatile unsigned *)rot == 0u || sweep_cos2 <= kLast * kLast;
+        const unsigned long long big = *(volatile unsigned long long *)(maxcos + (sweep % 3));
+        bool done = *(volatile unsigned *)rot == 0u || big == 0ull;
         if (bid == 0 && tid == 0)
             w.bar[6] = unsigned(sweep + 1);
         if (done)
