@@ -196,7 +196,11 @@ double wos_fp32_eps_floor(const wos_domain *domain);
  * walk-on-ellipsoids chain X_{n+1} = X_n + dist(X_n, dD) S U_n from X_0 = x_i,
  * S = (K / lambda_max(K))^{1/2}, U_n uniform on the unit sphere drawn from
  * Philox4x32-10 (key = seed, counter = (block, walk lo, walk hi, stream_id),
- * walk = i * N + k), stops at the first n with dist(X_n, dD) <= eps and adds
+ * walk = i * N + k; step n reads block n / G: G = 5 for FP32 2-D walks, whose
+ * step takes the 23-bit window (n mod 5) of the block's 128 bits; G = 2 for
+ * FP32 3-D walks (23-bit uniforms (w >> 9) 2^-23 from two words) and FP64
+ * 2-D walks; G = 1 for FP64 3-D walks (53-bit uniforms from two words)),
+ * stops at the first n with dist(X_n, dD) <= eps and adds
  * 1 to counts[i][j], j the element holding pi(X_n).  Walks reaching
  * opts->step_cap add 1 to unterminated[i] instead, so that
  * sum_j counts[i][j] + unterminated[i] = k1 - k0 exactly (per call).
