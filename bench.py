@@ -40,9 +40,10 @@ METRIC = ("WoS walks/s and steps/s on 1 GB300 (% FP32/SFU roofline); "
 # at the 2070 MHz maximum SM clock (lane-operations per second).
 ALU_PEAK_GOPS = 152 * 4 * 32 * 2.070
 # Algorithmic lane-operations of one step of the chain (FP32, 2-D, full S):
-# Philox4x32-10 share 80/4 = 20, uniform 3, sin/cos 4, move 6, eps and cap
-# tests 3, step counter 1, plus the distance: box 5, disc-minus-disc 9.
-OPS_PER_STEP = {"box": 42, "annulus": 46}
+# Philox4x32-10 share 80/5 = 16 (a block of 80 operations serves five steps,
+# one 23-bit window each), uniform 3, sin/cos 4, move 6, eps and cap tests 3,
+# step counter 1, plus the distance: box 5, disc-minus-disc 9.
+OPS_PER_STEP = {"box": 38, "annulus": 42}
 # FP64 peak of one GB300: 152 SMs x 2 FP64 FMA per clock (ncu:
 # sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 per
 # chip) x 2 flop x 2070 MHz, in GFLOP/s.
@@ -92,7 +93,9 @@ def describe(name: str) -> dict:
                              "N=1e5 walks/point, eps=1e-5, FP32 walks; FP64 Jacobi SVD of "
                              "the 256x128 Gamma_1 block; TSVD of 1% noisy data"),
                 "walks_per_step": 2 * 256 * 100_000,
-                "l2": "flushed between timed steps (256 MiB write)",
+                "l2": ("flushed between consecutive steps' walks (256 MiB write on the "
+                       "walk stream, inside the timed region; also in the e2e and "
+                       "latency steps)"),
                 "parallelism": "replicas (one full workload per GPU)"}
     return {"workload": name}
 
@@ -314,6 +317,10 @@ def run_gpu(args, rank: int, world: int, dist):
             bs.wait_stream(main)
         built = []
         with torch.cuda.stream(bs):
+            # L2 flushed between consecutive steps' walks: the build stream
+            # runs the walks in order, so the write sits after the previous
+            # step's walk launches and before this step's
+            flush.zero_()
             for q, p in enumerate(prep):
                 inst = p["inst"]
                 if host_io:
@@ -372,7 +379,6 @@ def run_gpu(args, rank: int, world: int, dist):
     # latency of one step on its own (nothing overlapped)
     lat_ms = []
     for _ in range(3):
-        flush.zero_()
         l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         l0.record(stream)
         step(start_ev=l0)
@@ -408,7 +414,6 @@ def run_gpu(args, rank: int, world: int, dist):
     pending = []
     t_first.record(stream)
     for it in range(args.steps):
-        flush.zero_()  # L2 flushed before every step's walks
         starts[it].record(stream)
         _, done = step(timing=kev[it], start_ev=starts[it], svd_timing=sev[it],
                        jac_timing=jev[it], join=False, index=it)
@@ -461,7 +466,7 @@ def run_gpu(args, rank: int, world: int, dist):
                  "frac_of_measured_issue": achieved / (pipes["issue"] / 1e9),
                  "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz "
                                 "(recipe unit counts and max clock)",
-                 "unit_of_work": "one step of the chain: 42 (box) / 46 (annulus) "
+                 "unit_of_work": "one step of the chain: 38 (box) / 42 (annulus) "
                                  "algorithmic lane-operations"}
     # the Jacobi launch of a step's batched SVD (both instances): FP64
     # roofline with every pair visit counted as rotated, an upper bound on the
@@ -599,9 +604,11 @@ def run_batch(args, rank: int, world: int, dist):
             out.append(c)
         return out
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     def timed(fn, reps):
         ms = []
         for _ in range(reps):
+            flush.zero_()  # L2 flushed before every timed call
             torch.cuda.synchronize()
             ev0.record()
             r = fn()
@@ -656,7 +663,8 @@ def run_batch(args, rank: int, world: int, dist):
         "data": "synthetic",
         "config": {"workload": f"mixed batch of 64 instances (disc, annulus, square, L-shape, "
                                f"ball, box), {walks:.3g} walks, operator builds only",
-                   "walks_per_step": walks},
+                   "walks_per_step": walks,
+                   "l2": "flushed before every timed call (256 MiB write, outside it)"},
         "sequential_walks_per_s": walks / t_seq, "batched_over_sequential": t_seq / t_bat,
         "batched_equals_sequential": bool(same), "tunings": tunings,
         "small_requests": {"instances": len(small), "walks": swalks,
@@ -857,9 +865,11 @@ def run_svd(args, rank: int, world: int, dist):
         for x in e:
             x.record()
     res = [dict(call=[], jac=[], sweeps=0) for _ in probs]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     for it in range(args.warmup + args.steps):
         for q, pb in enumerate(probs):
             e = evs[q]
+            flush.zero_()  # L2 flushed before every timed call
             torch.cuda.synchronize()
             e[0].record()
             out = wos.wos_op_svd_batched(ctx, [pb], jacobi_events=(e[1], e[2]))
@@ -886,7 +896,8 @@ def run_svd(args, rank: int, world: int, dist):
         "data": "synthetic",
         "svd_path": args.svd_path,
         "config": {"workload": "FP64 SVD of seeded operator-shaped counts, 256x128 and "
-                               "1024x768 (M_D x M_1), N = 1e5, one call per shape per step"},
+                               "1024x768 (M_D x M_1), N = 1e5, one call per shape per step",
+                   "l2": "flushed before every timed call (256 MiB write, outside it)"},
         "per_shape": per,
     }))
 
@@ -894,7 +905,7 @@ def run_svd(args, rank: int, world: int, dist):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="square-annulus")

@@ -417,20 +417,25 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
             const uint32_t blk0 = nstep / G;  // a group starts on a block boundary
             uint32_t w[4];
             if (!active || nstep + uint32_t(G) * nb <= I.step_cap) {
+                // No stop flag: a walk that reached the eps-shell moves by
+                // 0 * S U, keeps X bit for bit (up to the sign of a zero),
+                // so every later distance repeats the same r <= eps and the
+                // walk stays put; the last step's test says whether it stopped.
+                bool go = true;
 #pragma unroll 1
                 for (uint32_t b = 0; b < nb; ++b) {
                     philox4x32_10(blk0 + b, wlo, whi, I.stream_id, p.rk, w);
 #pragma unroll
                     for (int s = 0; s < G; ++s) {
                         const Real r = walk_dist<Real, DIM, KIND>(I.g, X);
-                        const bool go = !stop && !(r <= I.eps);
-                        stop = !go;
+                        go = !(r <= I.eps);
                         Real U[DIM];
                         step_direction<Real, DIM>(w, s, U);
                         step_move<Real, DIM>(I.S, U, go ? r : Real(0), X);
                         nstep += go ? 1u : 0u;
                     }
                 }
+                stop = !go;
             } else {
 #pragma unroll 1
                 for (uint32_t b = 0; b < nb; ++b) {

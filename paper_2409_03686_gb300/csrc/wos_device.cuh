@@ -496,12 +496,15 @@ __device__ __forceinline__ void direction(const uint32_t *w, Real *U)
     if (DIM == 2) {
         Real s, c;
         if constexpr (sizeof(Real) == 4) {
-            // w[0] holds the step's 23-bit window in its low bits: 2u - 1 =
-            // 2 + window 2^-22 less 3 (exact, one logic op builds the float);
-            // then the SFU path of w_sincospi
-            const float t = __uint_as_float(0x40000000u | (w[0] & 0x7fffffu)) - 3.0f;
+            // w[0] holds the step's 23-bit window in its low bits: one logic
+            // op builds f = 2 + window 2^-22 = 2 + 2u in [2, 4); the angle
+            // pi (2u - 1) = pi f - 3 pi is one FMA, rounded once and inside
+            // [-pi, pi]; the float constants move each angle by less than
+            // 4e-7 rad, an offset plus a stretch of 3e-8 relative, below
+            // the SFU sine's own error.  Then the SFU path of w_sincospi
+            const float f = __uint_as_float(0x40000000u | (w[0] & 0x7fffffu));
             float ss, cc;
-            __sincosf(3.14159265358979f * t, &ss, &cc);
+            __sincosf(fmaf(f, 3.14159265358979f, -9.42477796076938f), &ss, &cc);
             s = -ss;
             c = -cc;
         } else {
