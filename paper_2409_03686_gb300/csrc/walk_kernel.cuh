@@ -150,14 +150,14 @@ __device__ __forceinline__ Real walk_dist(const Geom<Real> &g, const Real *x)
         }
         return r;
     }
-    if (KIND == kAnnulus) {  // |x - c| once: the same values as the two distances
+    if (KIND == kAnnulus) {  // |x - c| once; both boundary distances from it
         Real s = Real(0);
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
             s += x[a] * x[a];  // x relative to the centre
         }
         const Real rho = w_sqrt(s);
-        return w_min(g.R - rho, rho - g.hr[0]);
+        return g.ahalf - w_fabs(rho - g.amid);  // = min(R - rho, rho - r_1)
     }
     return domain_dist<Real, DIM>(g, x);
 }

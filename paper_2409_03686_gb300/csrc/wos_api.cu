@@ -296,6 +296,10 @@ void fill_geom(const wos_domain &d, const wos_partition &p, Geom<Real> &g)
         g.hole_off[h] = off;
         off += hole_elements(d, p, h);
     }
+    if (d.n_holes > 0) {
+        g.amid = Real(0.5 * (d.radius + d.hole_radius[0]));
+        g.ahalf = Real(0.5 * (d.radius - d.hole_radius[0]));
+    }
 }
 
 template void fill_geom<float>(const wos_domain &, const wos_partition &, Geom<float> &);

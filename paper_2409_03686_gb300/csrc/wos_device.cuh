@@ -92,6 +92,10 @@ template <typename Real> struct Geom {
     Real vx[kMaxVerts], vy[kMaxVerts], ex[kMaxVerts], ey[kMaxVerts];
     Real il2[kMaxVerts];
     Real hc[kMaxHoles][3], hr[kMaxHoles];
+    // one concentric hole (annulus, shell): the walk distance
+    // min(R - rho, rho - r_1) = ahalf - |rho - amid|, amid = (R + r_1) / 2,
+    // ahalf = (R - r_1) / 2 (each rounded once from double)
+    Real amid, ahalf;
     // partition of the outer component
     int32_t outer_m;         // circle arcs
     Real outer_t0;           // theta0 / (2 pi)
