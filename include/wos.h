@@ -275,7 +275,8 @@ typedef struct {
 
 /* Many MC-REM builds (paper Sec. 5.1, Algorithm MC-REM, applied to each
  * problem) in one persistent launch per class (dimension x kernel kind:
- * plain disc/ball, box, disc/ball with holes, other): the walks of all the
+ * plain disc/ball, box, box with equal half-extents, disc/ball with holes,
+ * disc/ball with one concentric hole, mapped walks, other): the walks of all the
  * problems of a class share a global tile queue, so problems of very
  * different sizes and walk lengths keep the whole GPU busy.  All problems
  * share `seed` and opts->precision; each problem's walks use counter
@@ -306,8 +307,9 @@ typedef struct {
  * over block size {256, 128}, resident blocks per SM {max, 3, 2}, tiles per
  * warp {16, 4, 64}, histogram slots {auto, none} and refill granularity
  * {1, 4, 8}; keeps the fastest in the context for problems of the same
- * precision, dimension and kernel kind (plain disc/ball, box, disc/ball with
- * holes, other).  Later wos_build_operator / wos_build_operators_batched calls
+ * precision, dimension and kernel kind (plain disc/ball, box, box with equal
+ * half-extents, disc/ball with holes, disc/ball with one concentric hole,
+ * mapped walks, other).  Later wos_build_operator / wos_build_operators_batched calls
  * whose opts leave all launch fields 0 use it.  Synchronises `stream`.
  * Errors: those of wos_build_operator. */
 wos_status wos_autotune(wos_context *ctx, const wos_problem *sample, uint64_t seed,

@@ -23,8 +23,8 @@
 //    more steps at the price of more idle lane-steps after a walk stops.
 //  * The Philox counter of step n of walk w is (n / G, w lo, w hi, stream):
 //    results do not depend on scheduling or on the batch a walk runs in.
-//  * Kinds whose distance depends on x - c only (disc / ball, box, annulus /
-//    shell) walk in coordinates relative to the centre c: the start point is
+//  * Kinds whose distance depends on x - c only (disc / ball, box, cube,
+//    annulus / shell) walk in coordinates relative to the centre c: the start point is
 //    shifted once per tile and the exit point back once per walk, which
 //    takes a subtraction per coordinate off every step (the same bits when
 //    c = 0; otherwise a rounding of the sum in another place).
@@ -47,12 +47,13 @@ namespace wos {
 // Kernel kinds: any domain; a disc / ball; a box; a disc / ball with holes;
 // a disc / ball with one concentric hole (annulus, spherical shell: both
 // boundary distances come from one radius); mapped walks (walk-on-spheres in
-// y = S^{-1} x, the domain a convex polytope given by its faces).
+// y = S^{-1} x, the domain a convex polytope given by its faces); a box with
+// equal half-extents (square, cube: h - max |x_a|).
 enum KernelKind : int {
     kGeneric = 0, kSphereOnly = 1, kBoxOnly = 2, kSphereHoles = 3, kAnnulus = 4,
-    kMapped = 5
+    kMapped = 5, kCubeOnly = 6
 };
-constexpr int kNumKinds = 6;
+constexpr int kNumKinds = 7;
 
 // One instance of the operator build.
 template <typename Real> struct WalkInst {
@@ -127,6 +128,15 @@ __device__ __forceinline__ Real walk_dist(const Geom<Real> &g, const Real *x)
             best = w_min(best, g.h[a] - w_fabs(x[a]));
         return best;
     }
+    if (KIND == kCubeOnly) {  // x relative to the centre; every h[a] = h[0]
+        // h - max_a |x_a| = min_a (h - |x_a|) bit for bit (the rounding of
+        // h - t is monotone in t), one subtraction fewer
+        Real m = w_fabs(x[0]);
+#pragma unroll
+        for (int a = 1; a < DIM; ++a)
+            m = w_max(m, w_fabs(x[a]));
+        return g.h[0] - m;
+    }
     if (KIND == kSphereHoles) {
         Real r = sphere_dist<Real, DIM>(g, x);
         for (int h = 0; h < g.n_holes; ++h)
@@ -168,7 +178,7 @@ __device__ __forceinline__ int32_t walk_classify(const Geom<Real> &g, const Real
 {
     if (KIND == kSphereOnly)
         return outer_sphere_cell<Real, DIM>(g, x);
-    if (KIND == kBoxOnly)
+    if (KIND == kBoxOnly || KIND == kCubeOnly)
         return outer_box_cell<Real, DIM>(g, x);
     if (KIND == kSphereHoles || KIND == kAnnulus)
         return sphere_holes_cell<Real, DIM>(g, x);
@@ -347,7 +357,8 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
                     for (int a = 0; a < DIM; ++a)
                         tile_x[a] = T.points_r ? T.points_r[size_t(ti) * DIM + a]
                                                : Real(T.points[size_t(ti) * DIM + a]);
-                    if (KIND == kSphereOnly || KIND == kBoxOnly || KIND == kAnnulus) {
+                    if (KIND == kSphereOnly || KIND == kBoxOnly || KIND == kCubeOnly ||
+                        KIND == kAnnulus) {
 #pragma unroll
                         for (int a = 0; a < DIM; ++a)
                             tile_x[a] -= T.g.c[a];  // walk relative to the centre
@@ -460,7 +471,8 @@ walk_kernel(const __grid_constant__ WalkParams<Real> p)
         const unsigned fin_mask = __ballot_sync(FULL, fin);
         if (fin_mask == 0u)
             continue;
-        if ((KIND == kSphereOnly || KIND == kBoxOnly || KIND == kAnnulus) && fin) {
+        if ((KIND == kSphereOnly || KIND == kBoxOnly || KIND == kCubeOnly ||
+             KIND == kAnnulus) && fin) {
             const WalkInst<Real> &I = inst(linst);
 #pragma unroll
             for (int a = 0; a < DIM; ++a)

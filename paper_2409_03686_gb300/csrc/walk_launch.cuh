@@ -38,11 +38,13 @@ const void *pick_walk_kernel(int kind)
     if (kind == kSphereHoles) return walk_kernel_ptr<Real, DIM, kSphereHoles, MULTI>();
     if (kind == kAnnulus) return walk_kernel_ptr<Real, DIM, kAnnulus, MULTI>();
     if (kind == kMapped) return walk_kernel_ptr<Real, DIM, kMapped, MULTI>();
+    if (kind == kCubeOnly) return walk_kernel_ptr<Real, DIM, kCubeOnly, MULTI>();
     return walk_kernel_ptr<Real, DIM, kGeneric, MULTI>();
 }
 
-// Kernel kind: specialised distance for a plain disc / ball, a box, a disc /
-// ball with holes, or a disc / ball with one hole of the same centre.
+// Kernel kind: specialised distance for a plain disc / ball, a box (a square
+// / cube when its half-extents are equal), a disc / ball with holes, or a
+// disc / ball with one hole of the same centre.
 inline int walk_kind(const wos_domain &d, const wos_partition &part, bool mapped = false)
 {
     if (mapped)
@@ -55,8 +57,12 @@ inline int walk_kind(const wos_domain &d, const wos_partition &part, bool mapped
             concentric = concentric && d.hole_center[0][a] == d.center[a];
         return concentric ? kAnnulus : kSphereHoles;
     }
-    if (part.voronoi_n <= 0 && d.n_holes == 0 && d.outer_kind == WOS_OUTER_BOX)
-        return kBoxOnly;
+    if (part.voronoi_n <= 0 && d.n_holes == 0 && d.outer_kind == WOS_OUTER_BOX) {
+        bool cube = true;
+        for (int a = 1; a < d.dim; ++a)
+            cube = cube && d.half[a] == d.half[0];
+        return cube ? kCubeOnly : kBoxOnly;
+    }
     return kGeneric;
 }
 

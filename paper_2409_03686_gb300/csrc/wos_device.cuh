@@ -57,6 +57,7 @@ WOS_HD double w_atan2(double y, double x) { return atan2(y, x); }
 WOS_HD float w_fabs(float x) { return fabsf(x); }
 WOS_HD double w_fabs(double x) { return fabs(x); }
 template <typename Real> WOS_HD Real w_min(Real a, Real b) { return b < a ? b : a; }
+template <typename Real> WOS_HD Real w_max(Real a, Real b) { return b > a ? b : a; }
 
 template <typename Real> struct Consts;
 template <> struct Consts<float> {

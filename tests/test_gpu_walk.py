@@ -6,6 +6,7 @@ rest are knife-edge walks where FP32 rounding differs from FP64), integer
 counts must equal the histogram of the GPU's own per-walk trace bit for bit,
 and every row must sum to N exactly.  FP64 walks agree with the oracle to
 rounding, so their agreement is essentially total."""
+import dataclasses
 import math
 
 import numpy as np
@@ -49,6 +50,22 @@ def test_fp64_walks_match_oracle_walk_by_walk():
     assert r["stats"]["steps"] == int(r["steps"].sum())
 
 
+def _stretched(inst, half):
+    """The instance on a box with the given half-extents, points scaled with it."""
+    old = np.asarray(inst.domain.half[:inst.dim], float)
+    new = np.asarray(half[:inst.dim], float)
+    dom = dataclasses.replace(inst.domain, half=tuple(half))
+    return inst.replace(domain=dom, points=inst.points * (new / old),
+                        name=inst.name + "-stretched")
+
+
+def _moved(inst, center):
+    """The instance with its domain and points moved to the given centre."""
+    c = np.asarray(center[:inst.dim], float) - np.asarray(inst.domain.center[:inst.dim], float)
+    dom = dataclasses.replace(inst.domain, center=tuple(center))
+    return inst.replace(domain=dom, points=inst.points + c, name=inst.name + "-moved")
+
+
 GEOMS = {
     "disc32": lambda: W.disc_config(N=1000, fp64=False),
     "square": lambda: W.square_config(N=600, grid=8),
@@ -59,6 +76,11 @@ GEOMS = {
     "ball": lambda: W.ball_config(N=500, n_points=40),
     "ball_rand_K": lambda: W.config3_instances(N=500, n_points=40)[1],
     "cube": lambda: W.cube_config(N=500, n_points=40),
+    # unequal half-extents: the general box kernel (squares and cubes take
+    # the equal-extent one)
+    "rectangle": lambda: _stretched(W.square_config(N=600, grid=8), (0.5, 0.3, 0.0)),
+    "cuboid": lambda: _stretched(W.cube_config(N=500, n_points=40), (1.0, 0.8, 0.6)),
+    "square_moved": lambda: _moved(W.square_config(N=600, grid=8), (0.2, -0.1, 0.0)),
     "shell": lambda: W.shell_config(N=500, shift=0.3, n_points=40),
     "shell_concentric": lambda: W.shell_config(N=500, shift=0.0, n_points=40),
     "square_hole": lambda: W.square_hole_config(example=1, N=600, eps=1e-5, fp64=False),
