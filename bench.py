@@ -39,11 +39,16 @@ METRIC = ("WoS walks/s and steps/s on 1 GB300 (% FP32/SFU roofline); "
 # ALU issue peak of one GB300: 152 SMs x 4 schedulers x 32 lanes per clock
 # at the 2070 MHz maximum SM clock (lane-operations per second).
 ALU_PEAK_GOPS = 152 * 4 * 32 * 2.070
-# Algorithmic lane-operations of one step of the chain (FP32, 2-D, full S):
-# Philox4x32-10 share 80/5 = 16 (a block of 80 operations serves five steps,
-# one 23-bit window each), uniform 3, sin/cos 4, move 6, eps and cap tests 3,
-# step counter 1, plus the distance: box 5, disc-minus-disc 9.
-OPS_PER_STEP = {"box": 38, "annulus": 42}
+# Algorithmic lane-operations of one step of the chain (FP32, 2-D, full S),
+# counted on the cheapest formulation known (absolute values are operand
+# modifiers): Philox4x32-10 share 80/5 = 16 (a block of 80 operations serves
+# five steps, one 23-bit window each), window 2 (shift, mask), angle and
+# sine/cosine 4 (one FMA, the scaling to revolutions, two SFU operations),
+# move 6 (S U and the update), eps test and step-length select 2, step
+# counter 1, plus the distance: square 2 (max of |x_a|, subtraction from h),
+# annulus 5 (two products, square root, |rho - mid| and its subtraction from
+# the half-width).
+OPS_PER_STEP = {"box": 33, "annulus": 36}
 # FP64 peak of one GB300: 152 SMs x 2 FP64 FMA per clock (ncu:
 # sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 per
 # chip) x 2 flop x 2070 MHz, in GFLOP/s.
@@ -466,7 +471,7 @@ def run_gpu(args, rank: int, world: int, dist):
                  "frac_of_measured_issue": achieved / (pipes["issue"] / 1e9),
                  "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz "
                                 "(recipe unit counts and max clock)",
-                 "unit_of_work": "one step of the chain: 38 (box) / 42 (annulus) "
+                 "unit_of_work": "one step of the chain: 33 (square) / 36 (annulus) "
                                  "algorithmic lane-operations"}
     # the Jacobi launch of a step's batched SVD (both instances): FP64
     # roofline with every pair visit counted as rotated, an upper bound on the

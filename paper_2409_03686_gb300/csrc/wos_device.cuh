@@ -518,6 +518,21 @@ __device__ __forceinline__ void direction(const uint32_t *w, Real *U)
         }
         U[0] = c;
         U[1] = s;
+    } else if constexpr (sizeof(Real) == 4) {
+        // f_j = 1 + u_j in [1, 2) from the bits (one logic op each); z = 3 -
+        // 2 f_1 is 1 - 2 u_1 exactly (a multiple of 2^-22 in (-1, 1]), and the
+        // angle pi (2 u_2 - 1) = 2 pi f_2 - 3 pi is one FMA (float constants:
+        // within 4e-7 rad), inside [-pi, pi] for the SFU path of w_sincospi
+        const float f1 = __uint_as_float(0x3f800000u | (w[0] >> 9));
+        const float f2 = __uint_as_float(0x3f800000u | (w[1] >> 9));
+        const float z = fmaf(-2.0f, f1, 3.0f);
+        const float s2 = fmaf(-z, z, 1.0f);
+        const float sr = w_sqrt(s2 > 0.0f ? s2 : 0.0f);
+        float ss, cc;
+        __sincosf(fmaf(f2, 6.28318530717959f, -9.42477796076938f), &ss, &cc);
+        U[0] = -sr * cc;
+        U[1] = -sr * ss;
+        U[2] = z;
     } else {
         Real u1 = Uniform<Real>::get(w);
         Real u2 = Uniform<Real>::get(w + Uniform<Real>::kWords);
