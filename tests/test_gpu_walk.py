@@ -119,6 +119,29 @@ def test_schedule_does_not_change_results():
 
 
 @pytest.mark.parametrize("make", [
+    lambda: W.square_config(N=2000, grid=6),
+    lambda: W.cube_config(N=800, n_points=24),
+])
+def test_equal_extent_box_kind_matches_box_kind(make):
+    """A square / cube walks on the equal-half-extent kernel (distance h -
+    max |x_a|); a box whose half-extents differ only in FP64 (by 1e-12, the
+    same FP32 values) walks on the general box kernel (min (h_a - |x_a|)).
+    The rounding of h - t is monotone in t, so both give the same FP32
+    distances and the same walks bit for bit."""
+    inst = make()
+    half = list(inst.domain.half)
+    for a in range(1, inst.dim):
+        half[a] += 1e-12
+    assert all(np.float32(half[a]) == np.float32(half[0]) for a in range(inst.dim))
+    boxed = inst.replace(domain=dataclasses.replace(inst.domain, half=tuple(half)))
+    r_eq = gpu_build(inst, trace_steps=True)
+    r_box = gpu_build(boxed, trace_steps=True)
+    np.testing.assert_array_equal(r_eq["counts"], r_box["counts"])
+    np.testing.assert_array_equal(r_eq["trace"], r_box["trace"])
+    np.testing.assert_array_equal(r_eq["steps"], r_box["steps"])
+
+
+@pytest.mark.parametrize("make", [
     lambda: W.square_config(N=1000, grid=6),
     lambda: W.annulus_config(N=800, grid=4),
     lambda: W.ball_config(N=600, n_points=24),
