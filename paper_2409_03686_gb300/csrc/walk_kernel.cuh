@@ -24,10 +24,10 @@
 //  * The Philox counter of step n of walk w is (n / G, w lo, w hi, stream):
 //    results do not depend on scheduling or on the batch a walk runs in.
 //  * Kinds whose distance depends on x - c only (disc / ball, box, cube,
-//    annulus / shell) walk in coordinates relative to the centre c: the start point is
-//    shifted once per tile and the exit point back once per walk, which
-//    takes a subtraction per coordinate off every step (the same bits when
-//    c = 0; otherwise a rounding of the sum in another place).
+//    annulus / shell) walk in coordinates relative to the centre c: the
+//    start point is shifted once per tile and the exit point back once per
+//    walk, which takes a subtraction per coordinate off every step (the same
+//    bits when c = 0; otherwise a rounding of the sum in another place).
 //  * A finished lane only pushes its stopped point into a per-warp queue in
 //    shared memory; once 32 are queued the whole warp classifies them (pi of
 //    App. A) and tallies them at full lane efficiency.
