@@ -200,7 +200,9 @@ def run_reference(args, rank: int, world: int):
         "steps_per_s": steps / total, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "config": describe(args.workload),
+        "dtype": "f64", "data": "synthetic",
+        "config": dict(describe(args.workload),
+                       l2="not applicable: the CPU oracle on the host cores"),
         "cpu_baseline": {"value": value, "unit": "walks/s", "cores": cores,
                          "kind": "oracle",
                          "sample": f"first {n_pts} points x {n_walks} walks of each "
