@@ -53,7 +53,9 @@ struct ClusterJob {
     unsigned *bar;   // [5] status, [6] sweeps
 };
 
-__global__ void __launch_bounds__(kClThreads, 1)
+// 64 registers a thread (8 bytes of spill): a 128-thread CTA then needs 8 K
+// registers and fits on an SM beside four 56-register walk blocks.
+__global__ void __maxnreg__(64)
 svd_cluster_kernel(const ClusterJob *jobs, int CL)
 {
     cg::cluster_group cluster = cg::this_cluster();

@@ -227,8 +227,14 @@ __device__ __forceinline__ void flush_slot(uint32_t *slot, int32_t words,
     __syncwarp();
 }
 
+// Registers: at most 64 a thread (four 256-thread blocks fill an SM's 64 K);
+// single-instance 2-D FP32 walks fit in 56 without spills, which leaves 8 K
+// registers of an SM for a 128-thread SVD cluster CTA (64 registers) beside
+// four walk blocks when the SVD of one operator overlaps the walks of the
+// next.  (Batched launches, which read their instance records from memory,
+// would spill at 56.)
 template <typename Real, int DIM, int KIND, bool MULTI>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __maxnreg__((sizeof(Real) == 4 && DIM == 2 && !MULTI) ? 56 : 64)
 walk_kernel(const __grid_constant__ WalkParams<Real> p)
 {
     constexpr int G = Steps<Real, DIM>::G;

@@ -124,6 +124,10 @@ wos_status plan_grid(int kind, int32_t max_M_tot, const wos_opts &o, int sm_coun
                                          int(P->smem));
     if (e != cudaSuccess)
         return e == cudaErrorMemoryAllocation ? WOS_OOM : WOS_CUDA_ERROR;
+    // the largest shared-memory carveout: an SM running walk blocks keeps
+    // room for an SVD cluster CTA beside them (the walks barely use L1)
+    cudaFuncSetAttribute(P->kfn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         int(cudaSharedmemCarveoutMaxShared));
     int bps = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, P->kfn, P->block, P->smem);
     if (e != cudaSuccess)

@@ -1031,6 +1031,10 @@ int cluster_fit(const wos_context *ctx, int m, int n, int pre)
     cudaFuncSetAttribute(svd_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaFuncSetAttribute(svd_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          wos::ctx_max_smem(ctx));
+    // the largest carveout, like the walk kernel, so either kernel finds
+    // room on an SM the other one runs on
+    cudaFuncSetAttribute(svd_cluster_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         int(cudaSharedmemCarveoutMaxShared));
     return cluster_launchable(CL, L.total) ? CL : 0;
 }
 
