@@ -280,7 +280,7 @@ def run_gpu(args, rank: int, world: int, dist):
     # the SVD stream runs at high priority: when a step's walk launch drains,
     # the block scheduler places the SVD's clusters before the next step's
     # walk blocks, which fill the rest of the GPU (steps pipeline)
-    # several SVD streams (three by default), taken in turn by the steps, so
+    # several SVD streams (four by default), taken in turn by the steps, so
     # that consecutive steps' SVDs (each a latency-bound cluster launch on a
     # few SMs) overlap each other too
     streams = [torch.cuda.Stream(device=dev, priority=-1) for _ in range(args.svd_streams)]
@@ -920,7 +920,7 @@ def main():
     ap.add_argument("--svd-path", choices=list(SVD_PATHS), default="auto",
                     help="SVD factorisation kernels: auto (cluster kernel when the "
                          "operator fits it) or grid (grid-wide kernels)")
-    ap.add_argument("--svd-streams", type=int, default=3,
+    ap.add_argument("--svd-streams", type=int, default=4,
                     help="SVD streams the pipelined steps alternate over")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default launch configuration (profiling: no trial launches)")
