@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 from pathlib import Path
 
@@ -117,21 +118,31 @@ class ClockSampler:
         self.proc = None
         self.gpu = gpu_index
         self.path = None
+        self.temp = False
 
     def start(self):
+        # samples go to $WOS_CLOCKS_CSV when set (to keep them), else to a
+        # temporary file
         try:
-            out = ROOT / "gpurun_out"
-            out.mkdir(exist_ok=True)
-            self.path = out / f"clocks_gpu{self.gpu}.csv"
+            path = os.environ.get("WOS_CLOCKS_CSV")
+            if path:
+                self.path = Path(path)
+            else:
+                fd, name = tempfile.mkstemp(prefix=f"clocks_gpu{self.gpu}_", suffix=".csv")
+                os.close(fd)
+                self.path = Path(name)
+                self.temp = True
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
 
     def stop(self):
         if self.proc is None:
+            if self.temp and self.path is not None:
+                self.path.unlink(missing_ok=True)
             return None
         time.sleep(0.25)
         self.proc.terminate()
@@ -153,6 +164,8 @@ class ClockSampler:
             for n, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(n)
+        if self.temp:
+            self.path.unlink(missing_ok=True)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
