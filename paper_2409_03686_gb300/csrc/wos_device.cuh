@@ -504,9 +504,11 @@ __device__ __forceinline__ void direction(const uint32_t *w, Real *U)
             // w[0] holds the step's 23-bit window in its low bits: one logic
             // op builds f = 2 + window 2^-22 = 2 + 2u in [2, 4); the angle
             // pi (2u - 1) = pi f - 3 pi is one FMA, rounded once and inside
-            // [-pi, pi]; the float constants move each angle by less than
-            // 4e-7 rad, an offset plus a stretch of 3e-8 relative, below
-            // the SFU sine's own error.  Then the SFU path of w_sincospi
+            // [-pi, pi]; with the float constants each angle is within
+            // 4.5e-7 rad of the exact one (an offset, a stretch of 3e-8
+            // relative and the rounding; checked over every window on the
+            // host), below the SFU sine's own error.  Then the SFU path of
+            // w_sincospi
             const float f = __uint_as_float(0x40000000u | (w[0] & 0x7fffffu));
             float ss, cc;
             __sincosf(fmaf(f, 3.14159265358979f, -9.42477796076938f), &ss, &cc);
@@ -521,8 +523,9 @@ __device__ __forceinline__ void direction(const uint32_t *w, Real *U)
     } else if constexpr (sizeof(Real) == 4) {
         // f_j = 1 + u_j in [1, 2) from the bits (one logic op each); z = 3 -
         // 2 f_1 is 1 - 2 u_1 exactly (a multiple of 2^-22 in (-1, 1]), and the
-        // angle pi (2 u_2 - 1) = 2 pi f_2 - 3 pi is one FMA (float constants:
-        // within 4e-7 rad), inside [-pi, pi] for the SFU path of w_sincospi
+        // angle pi (2 u_2 - 1) = 2 pi f_2 - 3 pi is one FMA (float constants
+        // and rounding: within 4.5e-7 rad), inside [-pi, pi] for the SFU path
+        // of w_sincospi
         const float f1 = __uint_as_float(0x3f800000u | (w[0] >> 9));
         const float f2 = __uint_as_float(0x3f800000u | (w[1] >> 9));
         const float z = fmaf(-2.0f, f1, 3.0f);
