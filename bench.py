@@ -106,6 +106,17 @@ def describe(name: str) -> dict:
     return {"workload": name}
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest of every rank's value (a job's time is its slowest
+    rank's); the value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ----------------------------------------------------------------------------
 # clocks
 # ----------------------------------------------------------------------------
@@ -448,10 +459,7 @@ def run_gpu(args, rank: int, world: int, dist):
     clk = clocks.stop()
     launches = ctx.kernel_launches() - launches0
     total_ms = t_first.elapsed_time(t_last)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     walks_per_step = sum(p["inst"].M_D * p["inst"].N for p in prep)
     steps_per_step = sum(steps_per_inst)
     value = world * walks_per_step * args.steps / (total_ms / 1e3)
@@ -545,10 +553,7 @@ def run_gpu(args, rank: int, world: int, dist):
     e2e_e.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e2e_s.elapsed_time(e2e_e)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
     e2e_value = world * walks_per_step * args.steps / (e2e_ms / 1e3)
 
     if rank != 0:
