@@ -14,7 +14,8 @@ the Monte Carlo method; they are what the walks must reproduce.
   (1/r - 1) / (1/a - 1) in 3-D (harmonic in r, 1 / 0 on the circles / spheres);
   per-arc measures of the annulus from the Fourier series of the Dirichlet
   problem (the paper's Sec. 1 remark that the annulus needs an infinite sum).
-* Unit square (K = I): harmonic measure of one side by the sine series.
+* Unit square and a x b rectangle (K = I): harmonic measure of one side by
+  the sine series of separation of variables.
 """
 from __future__ import annotations
 
@@ -104,6 +105,18 @@ def annulus_arc_measures(x, a, m_outer, m_inner, theta0_outer=0.0,
     p_in = math.log(r) / math.log(a)
     return np.concatenate([arcs(m_outer, theta0_outer, outer_f, 1 - p_in),
                            arcs(m_inner, theta0_inner, inner_f, p_in)])
+
+
+def rectangle_side_measure(x, y, a: float, b: float, n_terms: int = 4001):
+    """Harmonic measure (K = I) of the bottom side of the rectangle [0,a] x
+    [0,b] seen from (x, y): separation of variables for Laplace's equation
+    with data 1 on y = 0 and 0 on the other sides, sum over odd n of
+    4/(n pi) sin(n pi x / a) sinh(n pi (b - y) / a) / sinh(n pi b / a)
+    (the sinh ratio written with decaying exponentials)."""
+    n = np.arange(1, n_terms + 1, 2, dtype=float)
+    k = n * math.pi / a
+    ratio = np.exp(-k * y) * (1 - np.exp(-2 * k * (b - y))) / (1 - np.exp(-2 * k * b))
+    return float(np.sum(4 / (n * math.pi) * np.sin(k * x) * ratio))
 
 
 def square_side_measure(x, y, n_terms: int = 2001):

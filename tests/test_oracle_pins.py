@@ -18,6 +18,7 @@
 The statistical band of an entry is 4 sqrt(p (1 - p) / N) + beta(eps) with
 beta(eps) = 2 (2/pi) rho_max eps (1 + ln(1/eps)), rho_max the largest density.
 """
+import dataclasses
 import math
 from pathlib import Path
 
@@ -314,6 +315,32 @@ def test_finite_difference_brute_force_square():
         for q, (x, y) in enumerate(pts):
             p = fd(x, y)
             assert abs(mu_bottom[q] - p) <= band(p, sq.N, 1e-3), (K, q, mu_bottom[q], p)
+
+
+def test_rectangle_side_measures():
+    """A box with unequal half-extents (K = I) against the sine series of
+    each side's harmonic measure: a mix-up of the axes' half-extents, a side
+    order or a side length in the oracle's box distance or classifier fails
+    it (the square pins cannot see those)."""
+    hx, hy = 0.5, 0.3
+    pts = np.array([[0.0, 0.0], [-0.3, -0.15], [0.35, 0.2], [0.1, -0.22], [-0.42, 0.05]])
+    sq = W.square_config(N=100_000, n_side=4, K=np.eye(2), eps=1e-5)
+    dom = dataclasses.replace(sq.domain, half=(hx, hy, 0.0))
+    rect = sq.replace(domain=dom, points=pts)
+    C, U, _ = O.build_counts(rect)
+    assert (C.sum(1) + U == rect.N).all()
+    a, b = 2 * hx, 2 * hy
+    for q, (x0, y0) in enumerate(pts):
+        x, y = x0 + hx, y0 + hy  # corner at the origin
+        want = [CF.rectangle_side_measure(x, y, a, b),          # bottom
+                CF.rectangle_side_measure(y, a - x, b, a),      # right
+                CF.rectangle_side_measure(a - x, b - y, a, b),  # top
+                CF.rectangle_side_measure(b - y, x, b, a)]      # left
+        assert sum(want) == pytest.approx(1.0, abs=1e-9)
+        got = C[q].reshape(4, 4).sum(1) / rect.N
+        for side in range(4):
+            assert abs(got[side] - want[side]) <= band(want[side], rect.N, 1e-3), \
+                (q, side, got[side], want[side])
 
 
 def test_printed_value_perforated_disc():
