@@ -15,7 +15,8 @@ the Monte Carlo method; they are what the walks must reproduce.
   per-arc measures of the annulus from the Fourier series of the Dirichlet
   problem (the paper's Sec. 1 remark that the annulus needs an infinite sum).
 * Unit square and a x b rectangle (K = I): harmonic measure of one side by
-  the sine series of separation of variables.
+  the sine series of separation of variables; a box's face by the double
+  sine series.
 """
 from __future__ import annotations
 
@@ -117,6 +118,27 @@ def rectangle_side_measure(x, y, a: float, b: float, n_terms: int = 4001):
     k = n * math.pi / a
     ratio = np.exp(-k * y) * (1 - np.exp(-2 * k * (b - y))) / (1 - np.exp(-2 * k * b))
     return float(np.sum(4 / (n * math.pi) * np.sin(k * x) * ratio))
+
+
+def box_face_measure(u, v, w, a: float, b: float, c: float, n_terms: int = 401,
+                     cell=None):
+    """Harmonic measure (K = I) of the face w = 0 of the box [0,a] x [0,b] x
+    [0,c], or of its sub-rectangle cell = (u0, u1, v0, v1), seen from the
+    point with in-face coordinates (u, v) and distance w from that face: the
+    double sine series of separation of variables, sum over m, n of
+    A_m B_n sin(m pi u / a) sin(n pi v / b) sinh(g (c - w)) / sinh(g c),
+    g = pi sqrt((m/a)^2 + (n/b)^2), A_m = 2/(m pi) (cos(m pi u0 / a) -
+    cos(m pi u1 / a)) the sine coefficients of the cell's indicator (4/(m pi)
+    for odd m and 0 for even m on the whole face), B_n likewise."""
+    u0, u1, v0, v1 = cell if cell is not None else (0.0, a, 0.0, b)
+    m = np.arange(1, n_terms + 1, dtype=float)[:, None]
+    n = np.arange(1, n_terms + 1, dtype=float)[None, :]
+    A = 2 / (m * math.pi) * (np.cos(m * math.pi * u0 / a) - np.cos(m * math.pi * u1 / a))
+    B = 2 / (n * math.pi) * (np.cos(n * math.pi * v0 / b) - np.cos(n * math.pi * v1 / b))
+    g = math.pi * np.sqrt((m / a) ** 2 + (n / b) ** 2)
+    ratio = np.exp(-g * w) * (1 - np.exp(-2 * g * (c - w))) / (1 - np.exp(-2 * g * c))
+    terms = A * B * np.sin(m * math.pi * u / a) * np.sin(n * math.pi * v / b) * ratio
+    return float(terms.sum())
 
 
 def square_side_measure(x, y, n_terms: int = 2001):

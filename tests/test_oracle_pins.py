@@ -343,6 +343,43 @@ def test_rectangle_side_measures():
                 (q, side, got[side], want[side])
 
 
+def test_cuboid_face_and_cell_measures():
+    """A 3-D box with unequal half-extents (K = I) against the double sine
+    series of each face's harmonic measure and of each of its 4 x 4 cells
+    (faces in element order -x, -y, -z, +x, +y, +z; cells over the two other
+    axes in increasing axis order): an axis mix-up in the box distance fails
+    the face totals, one in the cell map fails the cells."""
+    half = (1.0, 0.8, 0.6)
+    nf = 4
+    pts = np.array([[0.0, 0.0, 0.0], [-0.5, 0.3, -0.2], [0.6, -0.4, 0.25],
+                    [0.2, 0.5, -0.35], [-0.7, -0.2, 0.1]])
+    cu = W.cube_config(N=100_000, n_face=nf, K=np.eye(3), eps=1e-5)
+    dom = dataclasses.replace(cu.domain, half=half)
+    box = cu.replace(domain=dom, points=pts)
+    C, U, _ = O.build_counts(box)
+    assert (C.sum(1) + U == box.N).all()
+    L = [2 * h for h in half]
+    bad = 0
+    for q, x0 in enumerate(pts):
+        X = [x0[k] + half[k] for k in range(3)]  # corner at the origin
+        got = C[q].reshape(6, nf, nf) / box.N
+        total = 0.0
+        for f in range(6):
+            k = f % 3
+            i, j = [t for t in range(3) if t != k]
+            w = L[k] - X[k] if f >= 3 else X[k]
+            face = CF.box_face_measure(X[i], X[j], w, L[i], L[j], L[k])
+            total += face
+            assert abs(got[f].sum() - face) <= band(face, box.N, 1e-3), (q, f)
+            for r in range(nf):
+                for s_ in range(nf):
+                    cell = (L[i] * r / nf, L[i] * (r + 1) / nf, L[j] * s_ / nf, L[j] * (s_ + 1) / nf)
+                    want = CF.box_face_measure(X[i], X[j], w, L[i], L[j], L[k], cell=cell)
+                    bad += abs(got[f, r, s_] - want) > band(want, box.N, 1e-3)
+        assert total == pytest.approx(1.0, abs=1e-9)
+    assert bad == 0, bad
+
+
 def test_printed_value_perforated_disc():
     vals = {}
     for line in open(GOLDEN / "paper_printed_values.txt"):
