@@ -380,6 +380,81 @@ def test_cuboid_face_and_cell_measures():
     assert bad == 0, bad
 
 
+def _fd_lshape_edge_measures(n):
+    """Discrete harmonic measures (K = I, 5-point Laplacian, grid step 2/n)
+    of the six edges of the L-shape [-1,1]^2 minus (0,1] x [-1,0), edges in
+    the polygon's order from (-1,-1): bottom, the two re-entrant edges,
+    right, top, left; a corner node shared by two edges carries 1/2 for
+    each.  Returns a function (x, y) -> the six values, bilinear between
+    nodes."""
+    h = 2.0 / n
+    xs = -1 + h * np.arange(n + 1)
+    X, Y = np.meshgrid(xs, xs, indexing="ij")
+    tol = 1e-9
+    outside = (X > tol) & (Y < -tol)
+    onb = [(np.abs(Y + 1) < tol) & (X <= tol),            # e0 bottom
+           (np.abs(X) < tol) & (Y <= tol),                 # e1 re-entrant, vertical
+           (np.abs(Y) < tol) & (X >= -tol),                # e2 re-entrant, horizontal
+           (np.abs(X - 1) < tol) & (Y >= -tol),            # e3 right
+           np.abs(Y - 1) < tol,                            # e4 top
+           np.abs(X + 1) < tol]                            # e5 left
+    bnd = np.zeros_like(X, bool)
+    for m in onb:
+        bnd |= m
+    inner = ~outside & ~bnd
+    idx = -np.ones(X.shape, int)
+    idx[inner] = np.arange(inner.sum())
+    G = np.zeros((6,) + X.shape)
+    cnt = sum(m.astype(float) for m in onb)
+    for e, m in enumerate(onb):
+        G[e][m] = 1.0 / cnt[m]
+    rows, cols, vals = [], [], []
+    rhs = np.zeros((inner.sum(), 6))
+    for i, j in zip(*np.nonzero(inner)):
+        r = idx[i, j]
+        rows.append(r); cols.append(r); vals.append(-4.0)
+        for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+            ii, jj = i + di, j + dj
+            if inner[ii, jj]:
+                rows.append(r); cols.append(idx[ii, jj]); vals.append(1.0)
+            else:
+                rhs[r] -= G[:, ii, jj]
+    A = sp.csc_matrix((vals, (rows, cols)), shape=(inner.sum(),) * 2)
+    sol = spla.splu(A).solve(rhs)
+    full = G.copy()
+    for e in range(6):
+        full[e][inner] = sol[idx[inner], e]
+
+    def at(x, y):
+        fx, fy = (x + 1) / h, (y + 1) / h
+        i0, j0 = int(fx), int(fy)
+        tx, ty = fx - i0, fy - j0
+        return ((1 - tx) * (1 - ty) * full[:, i0, j0] + tx * (1 - ty) * full[:, i0 + 1, j0]
+                + (1 - tx) * ty * full[:, i0, j0 + 1] + tx * ty * full[:, i0 + 1, j0 + 1])
+    return at
+
+
+def test_lshape_edge_measures_finite_difference():
+    """The L-shape's six edge totals (K = I) against the finite-difference
+    harmonic measures; the solver is pinned by the six measures summing to 1
+    and by its grid convergence at the test points."""
+    pts = np.array([[-0.5, -0.5], [-0.5, 0.5], [0.5, 0.5], [-0.2, 0.25], [0.3, 0.3],
+                    [-0.6, -0.15]])
+    fine, coarse = _fd_lshape_edge_measures(256), _fd_lshape_edge_measures(128)
+    L = W.lshape_config(N=100_000, eps=1e-5).replace(points=pts)
+    em = list(L.partition.edge_m)
+    off = np.concatenate([[0], np.cumsum(em)])
+    C, U, _ = O.build_counts(L)
+    assert (C.sum(1) + U == L.N).all()
+    for q, (x, y) in enumerate(pts):
+        want = fine(x, y)
+        assert want.sum() == pytest.approx(1.0, abs=1e-9)
+        assert np.abs(want - coarse(x, y)).max() < 2e-3
+        got = np.array([C[q, off[e]:off[e + 1]].sum() for e in range(6)]) / L.N
+        for e in range(6):
+            assert abs(got[e] - want[e]) <= band(want[e], L.N, 2e-3), (q, e, got[e], want[e])
+
+
 def test_printed_value_perforated_disc():
     vals = {}
     for line in open(GOLDEN / "paper_printed_values.txt"):
