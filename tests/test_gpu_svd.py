@@ -29,9 +29,11 @@ def svd_path(request):
     wos.wos_set_svd_path(ctx(), wos.SVD_AUTO)
 
 
-def _svd_pair(C, N, gamma1, sigma, nu):
+def _svd_pair(C, N, gamma1, sigma, nu, sigma_lib=None):
+    """The library's SVD (element measures sigma_lib, default sigma) and the
+    oracle's (sigma) of the same counts."""
     Ct = torch.as_tensor(C.astype(np.int32), device=DEV)
-    sg = torch.as_tensor(sigma, device=DEV)
+    sg = torch.as_tensor(sigma if sigma_lib is None else sigma_lib, device=DEV)
     nut = torch.as_tensor(nu, device=DEV)
     U, S, V, sweeps = wos.wos_op_svd(ctx(), Ct, N, gamma1, sg, nu=nut)
     B = O.operator_B(C, N, gamma1, nu, sigma)
@@ -58,9 +60,12 @@ def _gaps(so, max_r):
 def test_svd_matches_oracle_on_oracle_counts(make, svd_path):
     inst = make()
     C, _, _ = O.build_counts(inst)
+    # each side takes the element measures from its own implementation
     sigma = O.element_measures(inst.domain, inst.partition)
+    sigma_lib = wos.wos_element_measures(inst.domain, inst.partition)
     g1 = inst.partition.gamma1
-    (U, s, V, sweeps), (Uo, so, Vo), _ = _svd_pair(C, inst.N, g1, sigma, inst.nu_vec())
+    (U, s, V, sweeps), (Uo, so, Vo), _ = _svd_pair(C, inst.N, g1, sigma, inst.nu_vec(),
+                                                   sigma_lib)
     _check_sv(s, so)
     k = len(so)
     np.testing.assert_allclose(U.T @ U, np.eye(k), atol=1e-12)
@@ -92,10 +97,12 @@ def test_reconstruction_matches_oracle():
     inst = W.annulus_config(N=2000, grid=6, m_each=32)
     C, _, _ = O.build_counts(inst)
     sigma = O.element_measures(inst.domain, inst.partition)
+    sigma_lib = wos.wos_element_measures(inst.domain, inst.partition)
     g1 = inst.partition.gamma1
     nu = inst.nu_vec()
     meas = W.measurements(inst, noise=0.01)
-    (U, s, V, _), (Uo, so, Vo), (Ct, sg, nut) = _svd_pair(C, inst.N, g1, sigma, nu)
+    (U, s, V, _), (Uo, so, Vo), (Ct, sg, nut) = _svd_pair(C, inst.N, g1, sigma, nu,
+                                                          sigma_lib)
     Ut, St, Vt = (torch.as_tensor(x, device=DEV) for x in (U, s, V))
     uD = torch.as_tensor(meas.uD, device=DEV)
     u0 = torch.as_tensor(meas.u0, device=DEV)

@@ -316,3 +316,67 @@ def test_element_measures_sum_to_boundary_measure():
         m = O.element_measures(inst.domain, inst.partition)
         assert len(m) == inst.M_tot
         assert m.sum() == pytest.approx(total, rel=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# sigma(omega_j) element by element (Eq. (boundary_weights): the surface
+# measure of each cell), on shapes whose sides differ, so that an axis or
+# edge mix-up in the oracle changes a value; the expected numbers are worked
+# by hand from the cell definitions of the partition descriptor.
+# ---------------------------------------------------------------------------
+def test_element_measures_cuboid_by_hand():
+    """Box with half-extents (1/2, 1, 2), 2 x 4 cells per face over the two
+    other axes in increasing order: face -x cells are (2/2) x (4/4) = 1,
+    face -y (1/2) x (4/4) = 1/2, face -z (1/2) x (2/4) = 1/4; +x, +y, +z
+    repeat them."""
+    dom = W.Domain(dim=3, outer="box", center=(0.1, -0.2, 0.3), half=(0.5, 1.0, 2.0))
+    part = W.Partition(face_n1=2, face_n2=4)
+    m = O.element_measures(dom, part)
+    per_face = [1.0, 0.5, 0.25, 1.0, 0.5, 0.25]
+    np.testing.assert_allclose(m, np.repeat(per_face, 8), rtol=1e-15)
+
+
+def test_element_measures_rectangle_and_lshape_by_hand():
+    """2-D box (1/2, 2) with 2, 4, 2, 4 cells on the bottom, right, top, left
+    edges: cell lengths 1/2, 1, 1/2, 1.  The L-shape's edges (lengths 1, 1,
+    1, 1, 2, 2 counter-clockwise from (-1, -1)) with 1, 2, 4, 1, 2, 8 cells:
+    1, 1/2, 1/4, 1, 1, 1/4."""
+    dom = W.Domain(dim=2, outer="box", center=(0.3, 0.0, 0.0), half=(0.5, 2.0, 1.0))
+    m = O.element_measures(dom, W.Partition(edge_m=(2, 4, 2, 4)))
+    np.testing.assert_allclose(m, [0.5] * 2 + [1.0] * 4 + [0.5] * 2 + [1.0] * 4,
+                               rtol=1e-15)
+    L = W.Domain(dim=2, outer="polygon", vertices=W.L_SHAPE)
+    em = (1, 2, 4, 1, 2, 8)
+    m = O.element_measures(L, W.Partition(edge_m=em))
+    want = np.repeat([1.0, 0.5, 0.25, 1.0, 1.0, 0.25], em)
+    np.testing.assert_allclose(m, want, rtol=1e-15)
+
+
+def test_element_measures_sphere_patch_and_holes_by_quadrature():
+    """A z-band x phi-sector patch of a sphere of radius 1.5 (4 bands, 6
+    sectors) against the surface integral R^2 sin(theta) dtheta dphi done by
+    scipy's adaptive quadrature; circle arcs of a hole against R dtheta."""
+    from scipy import integrate
+    R = 1.5
+    dom = W.Domain(dim=3, outer="sphere", radius=R,
+                   holes=(((0.2, 0.0, 0.1), 0.3),))
+    part = W.Partition(outer_nb=4, outer_ns=6, hole_nb=(2,), hole_ns=(3,))
+    m = O.element_measures(dom, part)
+    assert len(m) == 24 + 6
+    # band 1 spans z in [-R/2, 0]: theta from acos(0) to acos(-1/2)
+    th0, th1 = math.acos(0.0), math.acos(-0.5)
+    area, _ = integrate.dblquad(lambda th, ph: R * R * math.sin(th),
+                                2 * math.pi * 2 / 6, 2 * math.pi * 3 / 6, th0, th1,
+                                epsabs=1e-14, epsrel=1e-13)
+    np.testing.assert_allclose(m[1 * 6 + 2], area, rtol=1e-12)
+    np.testing.assert_allclose(m[:24], area, rtol=1e-12)
+    # hole: 2 bands x 3 sectors of the sphere of radius 0.3
+    harea, _ = integrate.dblquad(lambda th, ph: 0.09 * math.sin(th),
+                                 0.0, 2 * math.pi / 3, 0.0, math.pi / 2,
+                                 epsabs=1e-15, epsrel=1e-13)
+    np.testing.assert_allclose(m[24:], harea, rtol=1e-12)
+    disc = W.Domain(dim=2, outer="sphere", radius=2.0, holes=(((0.5, 0.0, 0.0), 0.25),))
+    m2 = O.element_measures(disc, W.Partition(outer_m=5, hole_m=(3,)))
+    arc, _ = integrate.quad(lambda t: 2.0, 0.0, 2 * math.pi / 5)
+    harc, _ = integrate.quad(lambda t: 0.25, 0.0, 2 * math.pi / 3)
+    np.testing.assert_allclose(m2, [arc] * 5 + [harc] * 3, rtol=1e-14)
