@@ -1,19 +1,26 @@
 #!/usr/bin/env python
 """Benchmark of the walk-on-ellipsoids operator build on GB300.
 
-One step = the whole hot path on the two-geometry workload of anisotropic
-2-D Cauchy problems: for the unit square and for the annulus r in [0.5, 1]
-(K = [[1, .5], [.5, 2]], 256 boundary elements, 256 jittered interior
-points, N = 1e5 walks per point, eps = 1e-5, FP32 walks): the Monte Carlo
-operator build (MC-REM), the FP64 one-sided Jacobi SVD of the Gamma_1 block
-and the TSVD reconstruction from measurements with 1 % Gaussian noise.
+One step = the whole hot path on the 3-D workload of anisotropic Cauchy
+problems (the default, ``--workload config3``): the unit ball and the cube
+[-1, 1]^3, each with K = diag(1, 2, 4) and with a random SPD K (eigenvalues
+log-uniform in [0.5, 4]); 1536 boundary patches (Gamma_1 = 768), 1024
+interior points uniform in the inner half, N = 1e5 walks per point, eps =
+1e-4, FP32 walks: the four Monte Carlo operator builds (MC-REM), the FP64
+one-sided Jacobi SVDs of the four 1024 x 768 Gamma_1 blocks and the TSVD
+reconstructions from measurements with 1 % Gaussian noise.
+``--workload square-annulus`` is the 2-D workload (unit square and annulus,
+K = [[1, .5], [.5, 2]], 256 elements and points, N = 1e5, eps = 1e-5).
 
 The timed steps pipeline: step k + 1's walk launches overlap step k's SVD
 and reconstructions, which run on high-priority SVD streams taken in turn;
 ``step_latency_ms`` is one step alone.  Prints one JSON line (metric, value =
-walks/s over all GPUs, roofline of the walk kernel and of the SVD
-factorisation, measured pipe rates, CPU baseline = the FP64 oracle on the
-host cores, e2e = the same steps through the public API with host buffers).
+walks/s over all GPUs, roofline of the dominant kernel by SM-time and of the
+other one, measured pipe rates, CPU baseline = the FP64 oracle on the host
+cores, e2e = the same steps through the public API with host buffers; on the
+3-D workload also the served requests/s and p50 / p99 latency of a bounded
+prefix of the seeded request stream against one-at-a-time plain launches,
+and the batched / sequential ratio of the 64-instance mixed batch).
 ``--impl reference`` times the CPU oracle on a bounded sample of the same
 workload instead.
 """
@@ -49,7 +56,15 @@ ALU_PEAK_GOPS = 152 * 4 * 32 * 2.070
 # counter 1, plus the distance: square 2 (max of |x_a|, subtraction from h),
 # annulus 5 (two products, square root, |rho - mid| and its subtraction from
 # the half-width).
-OPS_PER_STEP = {"box": 33, "annulus": 36}
+OPS_PER_STEP = {"box": 33, "annulus": 36, "ball": 72, "cube": 70}
+# FP32 3-D step, the same rules: Philox share 80/2 = 40 (a block of four
+# words serves two steps of two 23-bit uniforms), uniforms 4 (shift and or
+# per word), z = 3 - 2 f1 and the angle 2 pi f2 - 3 pi 2 (FMAs), sine/cosine
+# 3 (scaling to revolutions, two SFU operations), 1 - z^2 and its square
+# root 2, move 13 (d s, the three products of d U, the nine FMAs of S (d U)
+# added to X), eps test and select 2, step counter 1, plus the distance:
+# ball 5 (three products / FMAs for |x|^2, square root, R - rho), cube 3
+# (two maxima of |x_a|, subtraction from h).
 # FP64 peak of one GB300: 152 SMs x 2 FP64 FMA per clock (ncu:
 # sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 per
 # chip) x 2 flop x 2070 MHz, in GFLOP/s.
@@ -84,6 +99,10 @@ def _traffic_from_profile():
 
 def workload(name: str):
     from paper_2409_03686_gb300 import workloads as W
+    if name == "config3":
+        return W.config3_instances()
+    if name == "config3-small":  # for ncu captures: same kernels, fewer walks
+        return W.config3_instances(N=4_000, n_points=256)
     if name == "square-annulus":
         return [W.square_config(), W.annulus_config()]
     if name == "small":  # for ncu captures: same kernels, smaller sizes
@@ -91,7 +110,28 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def kind_of(inst) -> str:
+    """Operation-count class of an instance's walk kernel."""
+    if inst.dim == 3:
+        return "cube" if inst.domain.outer == "box" else "ball"
+    return "box" if inst.domain.outer == "box" else "annulus"
+
+
 def describe(name: str) -> dict:
+    if name == "config3":
+        return {"workload": ("3-D anisotropic Cauchy operators: unit ball and cube "
+                             "[-1,1]^3, each with K=diag(1,2,4) and a random SPD K "
+                             "(eigenvalues log-uniform in [0.5,4]); 1536 boundary patches "
+                             "(32x48 equal-area on the sphere, 6x16x16 on the cube; "
+                             "Gamma_1 = 768), 1024 points uniform in the inner half, "
+                             "N=1e5 walks/point, eps=1e-4, FP32 walks, uint32 counts; "
+                             "FP64 Jacobi SVD of each 1024x768 Gamma_1 block; TSVD of 1% "
+                             "noisy data"),
+                "walks_per_step": 4 * 1024 * 100_000,
+                "l2": ("flushed between consecutive steps' walks (256 MiB write on the "
+                       "walk stream, inside the timed region; also in the e2e and "
+                       "latency steps)"),
+                "parallelism": "replicas (one full workload per GPU)"}
     if name == "square-annulus":
         return {"workload": ("2-D anisotropic Cauchy operator: unit square [-1/2,1/2]^2 "
                              "and annulus r in [0.5,1], K=[[1,0.5],[0.5,2]], 256 boundary "
@@ -208,7 +248,7 @@ def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
     insts = workload(args.workload)
-    n_pts, n_walks = 32, 100_000
+    n_pts, n_walks = (8 if insts[0].dim == 3 else 32), 100_000
     times, walks, steps = [], 0, 0
     for it in range(args.warmup + args.steps):
         w, s, dt = oracle_sample(insts, n_pts, n_walks)
@@ -330,7 +370,7 @@ def run_gpu(args, rank: int, world: int, dist):
         M_1 = int(inst.partition.gamma1.sum())
         p["svd_mn"] = (max(inst.M_D, M_1), min(inst.M_D, M_1))
         p["steps"] = st["steps"]
-        p["kind"] = "box" if inst.domain.outer == "box" else "annulus"
+        p["kind"] = kind_of(inst)
         steps_per_inst.append(st["steps"])
     def step(timing=None, host_io=False, start_ev=None, svd_timing=None, jac_timing=None,
              join=True, index=0):
@@ -494,8 +534,10 @@ def run_gpu(args, rank: int, world: int, dist):
                  "frac_of_measured_issue": achieved / (pipes["issue"] / 1e9),
                  "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz "
                                 "(recipe unit counts and max clock)",
-                 "unit_of_work": "one step of the chain: 33 (square) / 36 (annulus) "
-                                 "algorithmic lane-operations"}
+                 "unit_of_work": "one step of the chain: 33 (2-D square) / 36 (2-D "
+                                 "annulus) / 72 (3-D ball) / 70 (3-D cube) algorithmic "
+                                 "lane-operations",
+                 "ops_per_step": {p["inst"].name: OPS_PER_STEP[p["kind"]] for p in prep}}
     # the Jacobi launch of a step's batched SVD (both instances): FP64
     # roofline with every pair visit counted as rotated, an upper bound on the
     # work; the whole SVD call (form_B, QR, Jacobi, left vectors, finalize) is
@@ -509,7 +551,7 @@ def run_gpu(args, rank: int, world: int, dist):
     svd_roof = {"kernel": ("svd_cluster_kernel" if args.svd_path == "auto" and
                            all(p["svd_mn"][1] <= 256 for p in prep)
                            else "qrcp_kernel + jacobi_kernel"),
-                "bound": "fp64", "achieved": svd_achieved,
+                "bound": "alu", "pipe": "fp64", "achieved": svd_achieved,
                 "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "frac": svd_achieved / FP64_PEAK_GFLOPS, "traffic": None,
                 "peak_source": "152 SMs x 2 FP64 FMA/clk (ncu dfma peak_sustained 304 "
@@ -587,29 +629,53 @@ def run_gpu(args, rank: int, world: int, dist):
                        **{k: v for k, v in pipes.items()},
                        "per_sm_clk": {k: v / (sms * 2.07e9) for k, v in pipes.items()}},
     }
+    if args.workload == "config3" and not args.no_extras:
+        # the metric's served latency (a bounded prefix of the config-5
+        # stream) and the config-4 batched / sequential ratio, each in a
+        # context of its own, after the timed steps
+        sv = measure_serve(args, local)
+        line["served"] = {"workload": sv["workload"], "requests": sv["requests"],
+                          **sv["served"], "one_at_a_time": sv["one_at_a_time"],
+                          "served_over_one_at_a_time": sv["served_over_one_at_a_time"],
+                          "served_equals_alone": sv["served_equals_alone"]}
+        bt = measure_batch(args, local, reps=3)
+        line["batched"] = {"workload": "config 4: 64 mixed 2-D / 3-D instances "
+                                       f"({bt['walks']:.3g} walks), operator builds only, "
+                                       "median of 3 calls each",
+                           "batched_walks_per_s": bt["batched_walks_per_s"],
+                           "sequential_walks_per_s": bt["sequential_walks_per_s"],
+                           "batched_over_sequential": bt["batched_over_sequential"],
+                           "batched_equals_sequential": bt["batched_equals_sequential"],
+                           "small_requests": bt["small_requests"]}
     if not args.no_cpu_baseline and world == 1:
         insts = [p["inst"] for p in prep]
-        n_pts, n_walks = insts[0].M_D, insts[0].N
-        w, s, dt = oracle_sample(insts, n_pts, n_walks, passes=2)
+        if insts[0].dim == 3:
+            n_pts, n_walks, passes = 96, insts[0].N, 1
+            what = (f"the first {n_pts} of {insts[0].M_D} points x {n_walks} walks of each "
+                    f"of the {len(insts)} instances")
+        else:
+            n_pts, n_walks, passes = insts[0].M_D, insts[0].N, 2
+            what = (f"the whole workload (all {n_pts} points x {n_walks} walks of both "
+                    f"instances) twice with independent walks")
+        w, s, dt = oracle_sample(insts, n_pts, n_walks, passes=passes)
         line["cpu_baseline"] = {
             "value": w / dt, "unit": "walks/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"the whole workload (all {n_pts} points x {n_walks} walks of both "
-                      f"instances) twice with independent walks: {w} walks, {dt:.1f} s, "
-                      f"FP64 C oracle on {os.cpu_count()} threads"}
+            "sample": f"{what}: {w} walks, {dt:.1f} s, FP64 C oracle on "
+                      f"{os.cpu_count()} threads"}
     print(json.dumps(line))
 
 
-def run_batch(args, rank: int, world: int, dist):
+def measure_batch(args, local: int, reps: int) -> dict:
     """Config 4: the 64-instance mixed batch (disc, annulus, square, L-shape,
     ball, box; log-uniform sizes and walks per point) in one autotuned
     persistent launch per dimension, against one plain launch per instance
-    (default launch settings) on the same GPU.  Operator builds only."""
+    (default launch settings) on the same GPU, `reps` timed calls each (a
+    context of its own, so the plain launches use no tuning).  Operator
+    builds only."""
     import torch
     from paper_2409_03686_gb300 import build as B
     from paper_2409_03686_gb300 import workloads as W
     from paper_2409_03686_gb300 import wos
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B.build()
     ctx = wos.Context(local)
@@ -642,7 +708,7 @@ def run_batch(args, rank: int, world: int, dist):
             ms.append(ev0.elapsed_time(ev1))
         return r, ms
     sequential()
-    seq_out, seq_ms = timed(sequential, args.steps)
+    seq_out, seq_ms = timed(sequential, reps)
     # autotune each (dim, kind) class on its largest instance, then batch
     classes = {}
     for inst in insts:
@@ -656,7 +722,7 @@ def run_batch(args, rank: int, world: int, dist):
         return c
     for _ in range(max(1, args.warmup)):
         batched()
-    bat_out, bat_ms = timed(batched, args.steps)
+    bat_out, bat_ms = timed(batched, reps)
     same = all(torch.equal(a, b) for a, b in zip(seq_out, bat_out))
 
     # small requests: 256 instances of 64..256 points x 1e3..1e4 walks
@@ -672,24 +738,17 @@ def run_batch(args, rank: int, world: int, dist):
                                                stats=False)[0]
     small_seq()
     small_bat()
-    s_seq, s_seq_ms = timed(small_seq, args.steps)
-    s_bat, s_bat_ms = timed(small_bat, args.steps)
+    s_seq, s_seq_ms = timed(small_seq, reps)
+    s_bat, s_bat_ms = timed(small_bat, reps)
     s_same = all(torch.equal(a, b) for a, b in zip(s_seq, s_bat))
-    if rank != 0:
-        return
     t_seq = float(np.median(seq_ms)) / 1e3
     t_bat = float(np.median(bat_ms)) / 1e3
     ts_seq = float(np.median(s_seq_ms)) / 1e3
     ts_bat = float(np.median(s_bat_ms)) / 1e3
-    print(json.dumps({
-        "metric": METRIC, "value": walks / t_bat, "unit": "walks/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_bat,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": f"mixed batch of 64 instances (disc, annulus, square, L-shape, "
-                               f"ball, box), {walks:.3g} walks, operator builds only",
-                   "walks_per_step": walks,
-                   "l2": "flushed before every timed call (256 MiB write, outside it)"},
+    ctx.close()
+    return {
+        "walks": walks, "t_bat": t_bat, "t_seq": t_seq,
+        "batched_walks_per_s": walks / t_bat,
         "sequential_walks_per_s": walks / t_seq, "batched_over_sequential": t_seq / t_bat,
         "batched_equals_sequential": bool(same), "tunings": tunings,
         "small_requests": {"instances": len(small), "walks": swalks,
@@ -699,10 +758,33 @@ def run_batch(args, rank: int, world: int, dist):
                            "requests_per_s_batched": len(small) / ts_bat,
                            "requests_per_s_sequential": len(small) / ts_seq,
                            "batched_equals_sequential": bool(s_same)},
+    }
+
+
+def run_batch(args, rank: int, world: int, dist):
+    """Config 4 alone (see measure_batch), ``--steps`` timed calls each."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    r = measure_batch(args, local, args.steps)
+    if rank != 0:
+        return
+    walks, t_bat = r.pop("walks"), r.pop("t_bat")
+    r.pop("t_seq")
+    print(json.dumps({
+        "metric": METRIC, "value": walks / t_bat, "unit": "walks/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_bat,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"mixed batch of 64 instances (disc, annulus, square, L-shape, "
+                               f"ball, box), {walks:.3g} walks, operator builds only",
+                   "walks_per_step": walks,
+                   "l2": "flushed before every timed call (256 MiB write, outside it)"},
+        **r,
     }))
 
 
-def run_serve(args, rank: int, world: int, dist):
+def measure_serve(args, local: int) -> dict:
     """Serving: a prefix of the seeded 10,000-request Poisson stream of 3-D
     ball / cube requests (operator build + FP64 SVD + truncation + TSVD
     reconstruction each, host inputs and outputs) through the request queue,
@@ -710,15 +792,13 @@ def run_serve(args, rank: int, world: int, dist):
     GPU.  Throughput with every request submitted at once; latency with
     Poisson arrivals at 70 % of the served throughput (the one-at-a-time
     latency at the same arrivals follows from its measured service times,
-    first come first served)."""
+    first come first served).  A context of its own."""
     import threading
 
     import torch
     from paper_2409_03686_gb300 import build as B
     from paper_2409_03686_gb300 import workloads as W
     from paper_2409_03686_gb300 import wos
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     B.build()
     ctx = wos.Context(local)
@@ -824,23 +904,17 @@ def run_serve(args, rank: int, world: int, dist):
         fin = max(fin, a) + sv
         seq_lat.append((fin - a) * 1e3)
     seq_lat = np.array(seq_lat)
-    if rank != 0:
-        return
+    ctx.close()
     walks = sum(r.inst.M_D * r.inst.N for r in reqs)
     t_seq = float(np.sum(seq_t))
     pct = lambda a, p: float(np.percentile(a, p))
-    print(json.dumps({
-        "metric": METRIC, "value": len(reqs) / t_sat, "unit": "requests/s", "n_gpus": world,
-        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * t_sat, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 walks, f64 SVD/TSVD",
-        "data": "synthetic",
-        "config": {"workload": f"first {len(reqs)} requests of a seeded 10,000-request "
-                               "Poisson stream: 3-D unit ball / cube, 1536 patches, "
-                               "K = diag(1,2,4) or random SPD, 256-1024 points, "
-                               "N = 1e5, eps in {1e-3, 1e-4}, noise 0.1-5 %; "
-                               "build + SVD + TSVD per request",
-                   "walks": walks, "side_streams": args.serve_side,
-                   "slice_walks": args.serve_slice},
+    return {
+        "requests": len(reqs), "walks": walks, "t_sat": t_sat,
+        "workload": f"first {len(reqs)} requests of a seeded 10,000-request "
+                    "Poisson stream: 3-D unit ball / cube, 1536 patches, "
+                    "K = diag(1,2,4) or random SPD, 256-1024 points, "
+                    "N = 1e5, eps in {1e-3, 1e-4}, noise 0.1-5 %; "
+                    "build + SVD + TSVD per request",
         "served": {"requests_per_s": len(reqs) / t_sat, "walks_per_s": walks / t_sat,
                    "latency_ms_p50": pct(lat, 50), "latency_ms_p99": pct(lat, 99),
                    "arrival_rate_per_s": rate, "slices": qst["slices"]},
@@ -850,11 +924,32 @@ def run_serve(args, rank: int, world: int, dist):
                           "service_ms_p50": pct(np.array(seq_t) * 1e3, 50)},
         "served_over_one_at_a_time": t_seq / t_sat,
         "served_equals_alone": bool(same),
-        "e2e": {"value": len(reqs) / t_sat, "unit": "requests/s",
-                "h2d_bytes_per_step": int(sum(r.inst.points.nbytes + m.uD.nbytes + m.u0.nbytes
-                                              for r, m in zip(reqs, meas))),
-                "d2h_bytes_per_step": int(sum(8 * int(r.inst.partition.gamma1.sum())
-                                              for r in reqs))},
+        "h2d_bytes": int(sum(r.inst.points.nbytes + m.uD.nbytes + m.u0.nbytes
+                             for r, m in zip(reqs, meas))),
+        "d2h_bytes": int(sum(8 * int(r.inst.partition.gamma1.sum()) for r in reqs)),
+    }
+
+
+def run_serve(args, rank: int, world: int, dist):
+    """Serving alone (see measure_serve)."""
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    r = measure_serve(args, local)
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": METRIC, "value": r["requests"] / r["t_sat"], "unit": "requests/s",
+        "n_gpus": world, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * r["t_sat"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 walks, f64 SVD/TSVD", "data": "synthetic",
+        "config": {"workload": r["workload"], "walks": r["walks"],
+                   "side_streams": args.serve_side, "slice_walks": args.serve_slice},
+        "served": r["served"], "one_at_a_time": r["one_at_a_time"],
+        "served_over_one_at_a_time": r["served_over_one_at_a_time"],
+        "served_equals_alone": r["served_equals_alone"],
+        "e2e": {"value": r["requests"] / r["t_sat"], "unit": "requests/s",
+                "h2d_bytes_per_step": r["h2d_bytes"], "d2h_bytes_per_step": r["d2h_bytes"]},
     }))
 
 
@@ -930,10 +1025,15 @@ def run_svd(args, rank: int, world: int, dist):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 30 on config3, 100 on the 2-D workloads)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="square-annulus")
+    ap.add_argument("--workload", default="config3",
+                    help="config3 (default), square-annulus, small, config3-small, "
+                         "batch, serve, svd")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="config3 without the served-latency and batching measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--svd-path", choices=list(SVD_PATHS), default="auto",
                     help="SVD factorisation kernels: auto (cluster kernel when the "
@@ -951,6 +1051,8 @@ def main():
     ap.add_argument("--serve-slice", type=int, default=4096,
                     help="walks per point per batched slice of the queue")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 30 if args.workload.startswith("config3") else 100
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

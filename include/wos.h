@@ -216,7 +216,14 @@ double wos_fp32_eps_floor(const wos_domain *domain);
  * Errors: WOS_INVALID_ARG, WOS_K_NOT_SPD, WOS_EPS_BELOW_FP32_FLOOR (FP32
  * walks only), WOS_COUNT_OVERFLOW, WOS_CUDA_ERROR; WOS_STEP_CAP_HIT is
  * returned as a warning when stats is non-NULL and a walk was capped.
- * Points are not checked here (use wos_check_points). */
+ * WOS_POINT_OUTSIDE: the points are tested on the device before the walks
+ * (FP64, the test of wos_check_points: dist(x_i, dD) > 0, and inside a
+ * polygon by the crossing number); if one lies outside D or on dD no walk
+ * runs, so counts and unterminated keep their values after the zeroing (all
+ * zero unless accumulate).  The status itself needs the device result: it
+ * is returned when stats is non-NULL (the call waits); an asynchronous call
+ * (stats NULL) returns WOS_OK and leaves the zero row sums as the sign --
+ * use wos_check_points on host copies of the points to test them up front. */
 wos_status wos_build_operator(wos_context *ctx, const wos_domain *domain,
                               const double *K, const double *points,
                               int32_t M_D, const wos_partition *partition,
@@ -246,7 +253,14 @@ wos_status wos_build_operator(wos_context *ctx, const wos_domain *domain,
  * capture.  All calls on a device share the array and it keeps the last
  * call's contents: each call clears the counters it needs at zero, but calls
  * whose device work may overlap (other streams, no event ordering) race on
- * it and must be serialised by the caller. */
+ * it and must be serialised by the caller.  The looked-up address, like a
+ * context, does not survive cudaDeviceReset.
+ *
+ * Differences from wos_build_operator: an extrinsic Voronoi partition is
+ * classified by a scan of all its sites per exit (no candidate grid, which
+ * would need scratch), so such builds are slower; its site table is copied
+ * from a host stack buffer with a pageable cudaMemcpyAsync, and a call with
+ * stats waits for the stream -- neither may run under stream capture. */
 wos_status wos_build_operator_noalloc(wos_context *ctx, const wos_domain *domain,
                                       const double *K, const double *points,
                                       int32_t M_D, const wos_partition *partition,
@@ -285,7 +299,8 @@ typedef struct {
  * opts may set precision, accumulate and the launch fields (block_size,
  * blocks_per_sm, tile_walks, hist_slots, kernel_events); opts->k0 / k1 and
  * traces must be zero (each problem has its own walk range).  stats (host or NULL): totals over the batch; non-NULL waits.
- * Errors: those of wos_build_operator, for the first failing problem. */
+ * Errors: those of wos_build_operator, for the first failing problem, except
+ * that the points are not tested here (wos_check_points tests them). */
 wos_status wos_build_operators_batched(wos_context *ctx, int32_t n,
                                        const wos_problem *problems, uint64_t seed,
                                        const wos_opts *opts, wos_stats *stats,

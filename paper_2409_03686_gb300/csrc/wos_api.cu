@@ -649,6 +649,102 @@ extern "C" wos_status wos_check_points(const wos_domain *dp, const double *pts,
 }
 
 // ---------------------------------------------------------------------------
+// observation points inside D, checked on the device before the walks
+// ---------------------------------------------------------------------------
+namespace {
+
+// The test of wos_check_points in FP64 on the device: dist(x, dD) > 0 and,
+// for a polygon (unsigned distance), an odd crossing number.  An outside
+// point records M_D - i in work[5] (the largest value marks the lowest
+// index) and takes every tile of the walk queue (work[0]), so that the walk
+// kernel after it on the stream runs no walk at all instead of walking from
+// outside D until the step cap.
+template <int DIM>
+__global__ void point_check_kernel(const __grid_constant__ Geom<double> g, const double *pts,
+                                   int32_t M_D, unsigned long long *work)
+{
+    const int32_t i = int32_t(blockIdx.x * blockDim.x + threadIdx.x);
+    if (i >= M_D)
+        return;
+    const double *x = pts + size_t(i) * DIM;
+    bool inside = domain_dist<double, DIM>(g, x) > 0.0;
+    if (inside && DIM == 2 && g.outer_kind == kPolygon) {
+        bool in = false;
+        for (int e = 0; e < g.n_vert; ++e) {
+            const int e1 = e + 1 < g.n_vert ? e + 1 : 0;
+            const double ax = g.vx[e], ay = g.vy[e], bx = g.vx[e1], by = g.vy[e1];
+            if ((ay > x[1]) != (by > x[1]) && x[0] < ax + (x[1] - ay) * (bx - ax) / (by - ay))
+                in = !in;
+        }
+        inside = in;
+    }
+    if (!inside) {
+        atomicMax(work + 5, (unsigned long long)(M_D - i));
+        atomicExch(work, 1ull << 62);
+    }
+}
+
+}  // namespace
+
+namespace wos {
+
+cudaError_t launch_point_check(const wos_domain &d, const wos_partition &part,
+                               const double *points, int32_t M_D,
+                               unsigned long long *work, cudaStream_t stream)
+{
+    Geom<double> g;
+    std::memset(&g, 0, sizeof(g));
+    fill_geom(d, part, g);
+    const unsigned blocks = unsigned((M_D + 127) / 128);
+    if (d.dim == 2)
+        point_check_kernel<2><<<blocks, 128, 0, stream>>>(g, points, M_D, work);
+    else
+        point_check_kernel<3><<<blocks, 128, 0, stream>>>(g, points, M_D, work);
+    return cudaGetLastError();
+}
+
+wos_status validate_build(const wos_context *ctx, const wos_domain *domain, const double *K,
+                          const double *points, int32_t M_D,
+                          const wos_partition *partition, uint32_t N, double eps,
+                          const wos_opts *opts, const uint32_t *counts, wos_opts *o,
+                          double *S)
+{
+    if (!ctx)
+        return WOS_INVALID_ARG;
+    wos_status st = validate(domain, partition);
+    if (st != WOS_OK)
+        return st;
+    std::memset(o, 0, sizeof(*o));
+    if (opts)
+        *o = *opts;
+    const uint32_t k1 = o->k1 ? o->k1 : N;
+    if (M_D < 1 || N < 1 || !points || !counts || !(eps > 0.0) || o->k0 >= k1 || k1 > N)
+        return WOS_INVALID_ARG;
+    if (o->precision != WOS_FP32 && o->precision != WOS_FP64)
+        return WOS_INVALID_ARG;
+    if (o->block_size && (o->block_size % 32 != 0 || o->block_size > 256))
+        return WOS_INVALID_ARG;
+    if (o->hist_slots < -1 || o->hist_slots > 2)
+        return WOS_INVALID_ARG;
+    if (num_elements(*domain, *partition) < 1)
+        return WOS_INVALID_ARG;
+    // walk ids i * N + k must fit 64 bits (always true for int32 M_D)
+    if (uint64_t(M_D) * uint64_t(N) > (1ull << 63))
+        return WOS_COUNT_OVERFLOW;
+    st = setup_S(domain->dim, K, S);
+    if (st != WOS_OK)
+        return st;
+    if (o->mapped != 0 && (o->mapped != 1 || !mapped_supported(*domain)))
+        return WOS_INVALID_ARG;
+    if (o->precision == WOS_FP32 &&
+        eps < (o->mapped ? fp32_floor_mapped(*domain, S) : fp32_floor(*domain)))
+        return WOS_EPS_BELOW_FP32_FLOOR;
+    return WOS_OK;
+}
+
+}  // namespace wos
+
+// ---------------------------------------------------------------------------
 // the walk launch
 // ---------------------------------------------------------------------------
 namespace {
@@ -738,6 +834,13 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
         set_voronoi_grid(vgrid, dstart, dcand, p.one.g);
     }
     cudaMemsetAsync(scratch, 0, 64, stream);
+    e = launch_point_check(d, part, points, M_D, p.work, stream);
+    count_launches(ctx, 1);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(scratch, stream);
+        delete pp;
+        return cuda_status(e);
+    }
     if (convert) {
         Real *dpts = reinterpret_cast<Real *>(static_cast<char *>(scratch) + 256 + site_bytes +
                                               grid_bytes);
@@ -764,7 +867,7 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
         cudaEventRecord(ctx->ev1, stream);
     wos_status st = cuda_status(e);
     if (st == WOS_OK && stats) {
-        unsigned long long w[5] = {0, 0, 0, 0, 0};
+        unsigned long long w[6] = {0, 0, 0, 0, 0, 0};
         cudaMemcpyAsync(w, scratch, sizeof(w), cudaMemcpyDeviceToHost, stream);
         e = cudaStreamSynchronize(stream);
         st = cuda_status(e);
@@ -779,7 +882,9 @@ wos_status build_impl(wos_context *ctx, const wos_domain &d,
         stats->tile_walks = int32_t(tw);
         stats->hist_slots = nslot;
         stats->kernel_ms = ms;
-        if (st == WOS_OK && w[3] > 0)
+        if (st == WOS_OK && w[5] > 0)
+            st = WOS_POINT_OUTSIDE;
+        else if (st == WOS_OK && w[3] > 0)
             st = WOS_STEP_CAP_HIT;
     }
     cudaFreeAsync(scratch, stream);
@@ -797,38 +902,12 @@ extern "C" wos_status wos_build_operator(wos_context *ctx, const wos_domain *dom
                                          uint32_t *unterminated, wos_stats *stats,
                                          void *stream)
 {
-    if (!ctx)
-        return WOS_INVALID_ARG;
-    wos_status st = validate(domain, partition);
-    if (st != WOS_OK)
-        return st;
     wos_opts o;
-    std::memset(&o, 0, sizeof(o));
-    if (opts)
-        o = *opts;
-    uint32_t k1 = o.k1 ? o.k1 : N;
-    if (M_D < 1 || N < 1 || !points || !counts || !(eps > 0.0) || o.k0 >= k1 || k1 > N)
-        return WOS_INVALID_ARG;
-    if (o.precision != WOS_FP32 && o.precision != WOS_FP64)
-        return WOS_INVALID_ARG;
-    if (o.block_size && (o.block_size % 32 != 0 || o.block_size > 256))
-        return WOS_INVALID_ARG;
-    if (o.hist_slots < -1 || o.hist_slots > 2)
-        return WOS_INVALID_ARG;
-    if (num_elements(*domain, *partition) < 1)
-        return WOS_INVALID_ARG;
-    // walk ids i * N + k must fit 64 bits (always true for int32 M_D)
-    if (uint64_t(M_D) * uint64_t(N) > (1ull << 63))
-        return WOS_COUNT_OVERFLOW;
     double S[9];
-    st = setup_S(domain->dim, K, S);
+    const wos_status st = validate_build(ctx, domain, K, points, M_D, partition, N, eps, opts,
+                                         counts, &o, S);
     if (st != WOS_OK)
         return st;
-    if (o.mapped != 0 && (o.mapped != 1 || !mapped_supported(*domain)))
-        return WOS_INVALID_ARG;
-    if (o.precision == WOS_FP32 &&
-        eps < (o.mapped ? fp32_floor_mapped(*domain, S) : fp32_floor(*domain)))
-        return WOS_EPS_BELOW_FP32_FLOOR;
     cudaSetDevice(ctx->device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (o.precision == WOS_FP64)

@@ -33,6 +33,24 @@ template <typename Real>
 void set_mapped(const wos_domain &d, const double *S, Geom<Real> &g);
 double fp32_floor_mapped(const wos_domain &d, const double *S);
 
+// Argument checks of an operator build (wos_build_operator and its
+// no-allocation variant): *o = opts (or zeros), S = (K / lambda_max)^{1/2};
+// returns the first error (WOS_INVALID_ARG, WOS_COUNT_OVERFLOW,
+// WOS_K_NOT_SPD, WOS_EPS_BELOW_FP32_FLOOR).
+wos_status validate_build(const wos_context *ctx, const wos_domain *domain, const double *K,
+                          const double *points, int32_t M_D,
+                          const wos_partition *partition, uint32_t N, double eps,
+                          const wos_opts *opts, const uint32_t *counts, wos_opts *o,
+                          double *S);
+// Enqueues the FP64 inside test of the points (device, M_D x dim) on
+// `stream`: an outside point sets work[5] = M_D - (its index), the largest
+// such value, and work[0] past every tile, so the walk kernel launched next
+// on the stream with this work array runs no walk.  work[0] and work[5]
+// must be zero before.
+cudaError_t launch_point_check(const wos_domain &d, const wos_partition &part,
+                               const double *points, int32_t M_D,
+                               unsigned long long *work, cudaStream_t stream);
+
 // Points the geometry at a Voronoi candidate grid already on the device.
 template <typename Real, typename Grid>
 void set_voronoi_grid(const Grid &G, const int32_t *dstart, const int32_t *dcand,

@@ -122,10 +122,17 @@ wos_status build_noalloc(wos_context *ctx, unsigned char *scratch, const wos_dom
     e = cudaMemsetAsync(scratch, 0, kCounterBytes, stream);
     if (e != cudaSuccess)
         return cuda_status(e);
+    // observation points outside D: no walk runs (work[0] past every tile)
+    e = launch_point_check(d, part, points, M_D, p.work, stream);
+    count_launches(ctx, 1);
+    if (e != cudaSuccess)
+        return cuda_status(e);
     if (!o.accumulate) {
-        cudaMemsetAsync(counts, 0, size_t(M_D) * M * 4, stream);
-        if (unterm)
-            cudaMemsetAsync(unterm, 0, size_t(M_D) * 4, stream);
+        e = cudaMemsetAsync(counts, 0, size_t(M_D) * M * 4, stream);
+        if (e == cudaSuccess && unterm)
+            e = cudaMemsetAsync(unterm, 0, size_t(M_D) * 4, stream);
+        if (e != cudaSuccess)
+            return cuda_status(e);
     }
     if (o.kernel_events[0])
         cudaEventRecord(static_cast<cudaEvent_t>(o.kernel_events[0]), stream);
@@ -136,7 +143,7 @@ wos_status build_noalloc(wos_context *ctx, unsigned char *scratch, const wos_dom
         cudaEventRecord(static_cast<cudaEvent_t>(o.kernel_events[1]), stream);
     wos_status st = cuda_status(e);
     if (st == WOS_OK && stats) {
-        unsigned long long w[5] = {0, 0, 0, 0, 0};
+        unsigned long long w[6] = {0, 0, 0, 0, 0, 0};
         cudaMemcpyAsync(w, scratch, sizeof(w), cudaMemcpyDeviceToHost, stream);
         st = cuda_status(cudaStreamSynchronize(stream));
         std::memset(stats, 0, sizeof(*stats));
@@ -148,7 +155,9 @@ wos_status build_noalloc(wos_context *ctx, unsigned char *scratch, const wos_dom
         stats->block = block;
         stats->tile_walks = int32_t(tw);
         stats->hist_slots = nslot;
-        if (st == WOS_OK && w[3] > 0)
+        if (st == WOS_OK && w[5] > 0)
+            st = WOS_POINT_OUTSIDE;
+        else if (st == WOS_OK && w[3] > 0)
             st = WOS_STEP_CAP_HIT;
     }
     return st;
@@ -162,39 +171,15 @@ extern "C" wos_status wos_build_operator_noalloc(
     const wos_opts *opts, uint32_t *counts, uint32_t *unterminated, wos_stats *stats,
     void *stream)
 {
-    if (!ctx)
-        return WOS_INVALID_ARG;
-    wos_status st = validate(domain, partition);
+    // the checks of wos_build_operator, then the limit of the fixed scratch
+    wos_opts o;
+    double S[9];
+    wos_status st = validate_build(ctx, domain, K, points, M_D, partition, N, eps, opts,
+                                   counts, &o, S);
     if (st != WOS_OK)
         return st;
-    wos_opts o;
-    std::memset(&o, 0, sizeof(o));
-    if (opts)
-        o = *opts;
-    const uint32_t k1 = o.k1 ? o.k1 : N;
-    if (M_D < 1 || N < 1 || !points || !counts || !(eps > 0.0) || o.k0 >= k1 || k1 > N)
-        return WOS_INVALID_ARG;
-    if (o.precision != WOS_FP32 && o.precision != WOS_FP64)
-        return WOS_INVALID_ARG;
-    if (o.block_size && (o.block_size % 32 != 0 || o.block_size > 256))
-        return WOS_INVALID_ARG;
-    if (o.hist_slots < -1 || o.hist_slots > 2)
-        return WOS_INVALID_ARG;
-    if (num_elements(*domain, *partition) < 1)
-        return WOS_INVALID_ARG;
     if (partition->voronoi_n > kNoAllocMaxSites)
         return WOS_NOALLOC_LIMIT;
-    if (uint64_t(M_D) * uint64_t(N) > (1ull << 63))
-        return WOS_COUNT_OVERFLOW;
-    double S[9];
-    st = setup_S(domain->dim, K, S);
-    if (st != WOS_OK)
-        return st;
-    if (o.mapped != 0 && (o.mapped != 1 || !mapped_supported(*domain)))
-        return WOS_INVALID_ARG;
-    if (o.precision == WOS_FP32 &&
-        eps < (o.mapped ? fp32_floor_mapped(*domain, S) : fp32_floor(*domain)))
-        return WOS_EPS_BELOW_FP32_FLOOR;
     const int dev = ctx_device(ctx);
     if (cudaSetDevice(dev) != cudaSuccess)
         return WOS_CUDA_ERROR;

@@ -438,6 +438,39 @@ def make_opts(precision: int = 0, step_cap: int = 0, stream_id: int = 0, k0: int
     return o
 
 
+def _check_build_tensors(ctx: Context, where: str, points, dim: int, M_tot: int,
+                         counts, unterminated) -> None:
+    """The device arrays of a build must match what the library reads and
+    writes: points contiguous float64 (M_D, dim); counts contiguous 32-bit
+    (M_D, M_tot); unterminated (optional) contiguous 32-bit with >= M_D
+    entries; all on the context's device.  Raises WosError(INVALID_ARG)
+    before any launch otherwise (an undersized buffer would be written out of
+    bounds)."""
+    import torch
+
+    def bad(msg):
+        raise WosError(1, f"{where}: {msg}")
+
+    want = torch.device("cuda", ctx.device)
+    if not isinstance(points, torch.Tensor) or points.device != want:
+        bad(f"points must be a tensor on {want}")
+    if points.dtype != torch.float64 or not points.is_contiguous() or points.dim() != 2 \
+            or points.shape[1] != dim or points.shape[0] < 1:
+        bad(f"points must be contiguous float64 of shape (M_D, {dim})")
+    M_D = int(points.shape[0])
+    if not isinstance(counts, torch.Tensor) or counts.device != want:
+        bad(f"counts must be a tensor on {want}")
+    if counts.dtype not in (torch.int32, torch.uint32) or not counts.is_contiguous() \
+            or tuple(counts.shape) != (M_D, M_tot):
+        bad(f"counts must be contiguous 32-bit of shape ({M_D}, {M_tot})")
+    if unterminated is not None:
+        if not isinstance(unterminated, torch.Tensor) or unterminated.device != want:
+            bad(f"unterminated must be a tensor on {want}")
+        if unterminated.dtype not in (torch.int32, torch.uint32) \
+                or not unterminated.is_contiguous() or unterminated.numel() < M_D:
+            bad(f"unterminated must be contiguous 32-bit with at least {M_D} entries")
+
+
 def wos_build_operator(ctx: Context, domain, K, points, partition, N: int, eps: float,
                        seed: int, opts: WosOpts | None = None, counts=None,
                        unterminated=None, stats: bool = True, stream=None):
@@ -457,6 +490,8 @@ def wos_build_operator(ctx: Context, domain, K, points, partition, N: int, eps: 
         counts = torch.empty((M_D, M_tot), dtype=torch.int32, device=dev)
     if unterminated is None:
         unterminated = torch.empty(M_D, dtype=torch.int32, device=dev)
+    _check_build_tensors(ctx, "wos_build_operator", points, domain.dim, M_tot, counts,
+                         unterminated)
     Kc = np.ascontiguousarray(K, dtype=np.float64)
     st = WosStats() if stats else None
     code = L.wos_build_operator(ctx.h, ctypes.byref(D), Kc.ctypes.data, points.data_ptr(),
@@ -476,11 +511,17 @@ def wos_build_operator_noalloc(ctx: Context, domain, K, points, partition, N: in
     """The same build as wos_build_operator for callers that cannot allocate
     device memory: the library takes its scratch from a fixed device array
     instead of allocating, and this wrapper allocates nothing either -- the
-    caller passes the counts (and optional unterminated) tensors.  Calls on
-    one device must not overlap on the GPU."""
+    caller passes the counts (and optional unterminated) tensors, which are
+    checked against the partition's size (a host call) before the build.
+    Calls on one device must not overlap on the GPU."""
     L = load()
     D = make_domain(domain)
     P, keep = make_partition(domain, partition)
+    M_tot = int(L.wos_num_elements(ctypes.byref(D), ctypes.byref(P)))
+    if M_tot < 1:
+        raise WosError(1, "wos_num_elements")
+    _check_build_tensors(ctx, "wos_build_operator_noalloc", points, domain.dim, M_tot,
+                         counts, unterminated)
     Kc = np.ascontiguousarray(K, dtype=np.float64)
     st = WosStats() if stats else None
     code = L.wos_build_operator_noalloc(

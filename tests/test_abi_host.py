@@ -173,3 +173,25 @@ def test_voronoi_partition_with_holes_marshals(lib):
     x = np.array([[0.0, 0.99], [0.51, 0.0]])
     np.testing.assert_array_equal(O.classify(inst.domain, part, x),
                                   np.argmin(((sites[None] - x[:, None]) ** 2).sum(-1), 1))
+
+
+def test_build_wrappers_refuse_host_tensors_before_the_library(lib):
+    """Device arrays are checked by the binding before any library call: a
+    host (CPU) points tensor would hand the library a host address."""
+    import torch
+
+    class FakeCtx:      # never reaches the library: the checks raise first
+        h = None
+        device = 0
+
+    inst = W.square_config(N=10, grid=2)
+    pts = torch.as_tensor(inst.points, dtype=torch.float64)
+    counts = torch.zeros((inst.M_D, inst.M_tot), dtype=torch.int32)
+    with pytest.raises(wos.WosError) as e:
+        wos.wos_build_operator(FakeCtx(), inst.domain, inst.K, pts, inst.partition, inst.N,
+                               inst.eps, inst.seed)
+    assert e.value.code == 1
+    with pytest.raises(wos.WosError) as e:
+        wos.wos_build_operator_noalloc(FakeCtx(), inst.domain, inst.K, pts, inst.partition,
+                                       inst.N, inst.eps, inst.seed, counts)
+    assert e.value.code == 1

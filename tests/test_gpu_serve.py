@@ -199,3 +199,51 @@ def test_preconditioned_svd_requests_equal_lone_solves():
         wos.wos_queue_destroy(q)
     for inst, m, t in zip(insts, meas, tickets):
         _check(t, _alone(inst, m), inst.name)
+
+
+def test_served_requests_match_the_oracle():
+    """Requests served in a mix, checked against the oracle itself (not only
+    against the lone GPU solve): three sampled rows of every request's counts
+    replayed walk by walk (the rows may differ only by the walks whose exit
+    element differs, <= 0.1 % of them, each moving one count out of one
+    column and into another), its singular values against the oracle's
+    Jacobi SVD of the served counts (1e-10 relative, the floor rule for the
+    tiny ones) and u_Gamma1 against the oracle's TSVD at the served
+    truncation (1e-8 relative)."""
+    from gpu_util import oracle_walks
+    from oracle import oracle as O
+    insts, meas = _requests(6)
+    q = wos.wos_queue_create(ctx(), seed=SEED, slice_walks=1500)
+    try:
+        tickets = [wos.wos_submit(q, inst, m.uD, m.u0, want_counts=True)
+                   for inst, m in zip(insts, meas)]
+        for t in tickets:
+            assert wos.wos_wait(q, t, 120_000)
+    finally:
+        wos.wos_queue_destroy(q)
+    checked = 0
+    for inst, m, t in zip(insts, meas, tickets):
+        inst = inst.replace(seed=SEED)
+        C = t.counts.astype(np.int64)
+        assert (C.sum(1) == inst.N).all(), inst.name
+        rows = sorted({0, inst.M_D // 2, inst.M_D - 1})
+        el, _, _ = oracle_walks(inst, rows=rows)
+        for q_, i in enumerate(rows):
+            ref = np.bincount(el[q_][el[q_] >= 0], minlength=inst.M_tot)
+            assert np.abs(C[i] - ref).sum() <= 2 * max(1, int(0.001 * inst.N)), (inst.name, i)
+        g1 = inst.partition.gamma1
+        sig = O.element_measures(inst.domain, inst.partition)
+        nu = inst.nu_vec()
+        Uo, so, Vo, _, ok = O.jacobi_svd(O.operator_B(C, inst.N, g1, nu, sig))
+        assert ok
+        big = so >= 1e-6 * so[0]
+        err = np.abs(t.S - so)
+        assert np.all(err[big] <= 1e-10 * so[big]), inst.name
+        assert np.all(err[~big] <= 1e-10 * so[0]), inst.name
+        r = t.r_used.value
+        if r < len(so) and so[r - 1] / so[r] < 1.5:
+            continue  # not at a gap: the r-TSVD is not stable to 1e-8
+        ro, _ = O.reconstruct(Uo, so, Vo, r, C, inst.N, g1, nu, sig, m.uD, m.u0)
+        assert np.linalg.norm(t.u_gamma1 - ro) <= 1e-8 * np.linalg.norm(ro), (inst.name, r)
+        checked += 1
+    assert checked >= 3

@@ -239,17 +239,58 @@ def test_harmonic_martingale_on_gpu_exit_points():
     assert np.abs(z).max() < 4.5, z
 
 
-def test_full_size_sampled_parity():
-    """The benchmark workload (square, 256 points, N = 1e5, FP32) in its own
-    launch configuration; sampled rows are replayed walk by walk by the
-    oracle, every row is checked for exact sums."""
-    inst = W.square_config()
+@pytest.mark.parametrize("make", [
+    W.square_config,
+    W.annulus_config,
+    lambda: W.config3_instances()[0],   # ball, K = diag(1, 2, 4)
+    lambda: W.config3_instances()[3],   # cube, random SPD K
+], ids=["square", "annulus", "ball-diag124", "cube-randK"])
+def test_full_size_sampled_parity(make):
+    """The benchmark instances at full size (2-D: 256 points, N = 1e5, eps =
+    1e-5; 3-D: 1024 points, 1536 patches, N = 1e5, eps = 1e-4; FP32) in the
+    default launch configuration: every row sums to N exactly, three sampled
+    rows are replayed walk by walk by the oracle, and the untraced launch the
+    benchmark times gives the traced launch's counts bit for bit."""
+    inst = make()
     r = gpu_build(inst)
     _check_consistent(inst, r)
-    rows = [0, 137, 255]
+    rows = [0, inst.M_D // 2 + 9, inst.M_D - 1]
     el, _, _ = oracle_walks(inst, rows=rows)
     agree = (r["trace"][rows] == el).mean()
     assert agree >= 0.999, agree
+    u = gpu_build(inst, trace=False)
+    np.testing.assert_array_equal(u["counts"], r["counts"])
+    np.testing.assert_array_equal(u["unterm"], r["unterm"])
+
+
+def test_point_outside_is_reported_and_runs_no_walk():
+    """An observation point outside D (the L-shape's missing quadrant, where
+    the unsigned polygon distance stays positive) or on dD: the build runs no
+    walk; with statistics it returns WOS_POINT_OUTSIDE, without them it
+    returns at once and every row sums to zero.  The no-allocation build
+    behaves the same."""
+    inst = W.lshape_config(N=5000, m_total=24, n_points=4)
+    for bad in ([0.5, -0.5], [1.0, 0.5]):
+        pts = inst.points.copy()
+        pts[2] = bad
+        b = inst.replace(points=pts)
+        with pytest.raises(wos.WosError) as e:
+            gpu_build(b, trace=False)
+        assert e.value.code == 3
+        t = torch.as_tensor(pts, dtype=torch.float64, device=torch.device("cuda:0"))
+        c, u, st = wos.wos_build_operator(ctx(), b.domain, b.K, t, b.partition, b.N, b.eps,
+                                          b.seed, stats=False)
+        torch.cuda.synchronize()
+        assert st is None and int(c.abs().sum()) == 0 and int(u.abs().sum()) == 0
+        c2 = torch.full_like(c, 5)
+        with pytest.raises(wos.WosError) as e:
+            wos.wos_build_operator_noalloc(ctx(), b.domain, b.K, t, b.partition, b.N,
+                                           b.eps, b.seed, c2)
+        assert e.value.code == 3
+        assert int(c2.abs().sum()) == 0
+    # the same points inside D build normally
+    r = gpu_build(inst)
+    _check_consistent(inst, r)
 
 
 def test_errors_are_reported():
