@@ -49,6 +49,7 @@ struct SvdWork {
                       // [8..13] per sweep mod 3 (uint64): 1 if a rotated pair
                       // had cos^2 > kLast^2
     unsigned *ver;    // n_pad column versions (rounds finished per column)
+    double *nrm;      // n squared column norms (kernels without V only)
 };
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -170,6 +171,188 @@ __device__ __forceinline__ void jacobi_rotation(double al, double be, double ga,
     const double z = rsqrt(c2);                  // 1 / c
     c = c2 * z;
     s = gy * z;
+}
+
+// The rotation of jacobi_rotation together with its tangent t = s / c.
+__device__ __forceinline__ void jacobi_rotation_t(double al, double be, double ga, double &c,
+                                                  double &s, double &t)
+{
+    const double h = 0.5 * (be - al);
+    const double y = rsqrt(fma(h, h, ga * ga));  // 1 / r
+    const double c2 = fma(fabs(h) * y, 0.5, 0.5);
+    const double gy = copysign(0.5, h) * ga * y;
+    const double z = rsqrt(c2);                  // 1 / c
+    c = c2 * z;
+    s = gy * z;
+    t = s * z;
+}
+
+// Jacobi without the accumulated V, for the large problems (worked matrices
+// of more than 256 columns, where the FP64 work of the sweeps bounds the
+// factorisation): the right singular vectors of W come from X's final
+// columns and the left ones from W itself afterwards (L = W P X_final), so a
+// pair reads and rotates only its two columns of X.  Its Gram entries take
+// one dot product instead of three: the squared norms are kept per column in
+// nrm[] and carried through each rotation by the identities of a rotation
+// that makes the pair orthogonal, |x_p'|^2 = |x_p|^2 - t g and |x_q'|^2 =
+// |x_q|^2 + t g (g = x_p . x_q, t = s / c); a norm whose identity cancelled
+// more than 63/64 of its terms is recomputed from the rotated column in the
+// same pass (the final singular values are recomputed exactly anyway).
+// Rounds, flags, stopping rule and the order of the pairs are those of
+// jacobi_body.
+constexpr double kRecompute = 1.0 / 64.0;
+
+template <int RPT>
+__device__ void jacobi_lean_body(const SvdWork &w, const int bid, const int nblk)
+{
+    __shared__ double part[kPairThreads / 32];
+    __shared__ double prm[2];
+    __shared__ int flag;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int half = w.n_pad / 2;
+    const int m = w.m, n = w.n;
+    unsigned *status = w.bar + 5;
+    unsigned long long *maxcos = reinterpret_cast<unsigned long long *>(w.bar + 8);
+    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+        unsigned *rot = w.bar + 2 + (sweep % 3);
+        if (bid == 0 && tid == 0) {
+            w.bar[2 + ((sweep + 1) % 3)] = 0u;
+            maxcos[(sweep + 1) % 3] = 0ull;
+        }
+        bool my_big = false;
+        for (int r = 0; r < w.n_pad - 1; ++r) {
+            const unsigned R = unsigned(sweep) * unsigned(w.n_pad - 1) + unsigned(r);
+            for (int pr = bid; pr < half; pr += nblk) {
+                int a = rr_player(pr, r, w.n_pad);
+                int b = rr_player(w.n_pad - 1 - pr, r, w.n_pad);
+                int p = min(a, b), q = max(a, b);
+                bool ok = true;
+                if (tid == 0)
+                    ok = wait_version(w.ver, p, R, status);
+                else if (tid == 32 && q < n)
+                    ok = wait_version(w.ver, q, R, status);
+                if (!__syncthreads_and(ok))
+                    return;
+                bool rotated = false;
+                if (q < n) {
+                    double *wp = w.W + size_t(p) * m, *wq = w.W + size_t(q) * m;
+                    double xr[RPT], yr[RPT];
+                    double ga = 0.0;
+#pragma unroll
+                    for (int k = 0; k < RPT; ++k) {
+                        int i = tid + k * kPairThreads;
+                        xr[k] = i < m ? __ldcg(wp + i) : 0.0;
+                        yr[k] = i < m ? __ldcg(wq + i) : 0.0;
+                    }
+#pragma unroll
+                    for (int k = 0; k < RPT; ++k)
+                        if (tid + k * kPairThreads < m)
+                            ga = fma(xr[k], yr[k], ga);
+                    for (int i = tid + RPT * kPairThreads; i < m; i += kPairThreads)
+                        ga = fma(__ldcg(wp + i), __ldcg(wq + i), ga);
+                    ga = warp_sum(ga);
+                    if (lane == 0)
+                        part[wid] = ga;
+                    __syncthreads();
+                    if (tid == 0) {
+                        ga = (part[0] + part[1]) + (part[2] + part[3]);
+                        const double al = __ldcg(w.nrm + p), be = __ldcg(w.nrm + q);
+                        double c = 1.0, sn = 0.0, t = 0.0;
+                        int f = 0;
+                        const double ab = al * be, g2 = ga * ga;
+                        if (al != 0.0 && be != 0.0 && g2 > (kTol * kTol) * ab) {
+                            jacobi_rotation_t(al, be, ga, c, sn, t);
+                            f = 1;
+                            my_big = my_big || g2 > (kLast * kLast) * ab;
+                            const double tg = t * ga;
+                            const double an = al - tg, bn = be + tg;
+                            const double scale = al + be + fabs(tg);
+                            // recompute a norm whose identity cancelled
+                            if (!(an > kRecompute * scale))
+                                f |= 2;
+                            else
+                                w.nrm[p] = an;
+                            if (!(bn > kRecompute * scale))
+                                f |= 4;
+                            else
+                                w.nrm[q] = bn;
+                        }
+                        prm[0] = c;
+                        prm[1] = sn;
+                        flag = f;
+                    }
+                    __syncthreads();
+                    const int f = flag;
+                    if (f & 1) {
+                        rotated = true;
+                        const double c = prm[0], sn = prm[1];
+                        double np2 = 0.0, nq2 = 0.0;
+#pragma unroll
+                        for (int k = 0; k < RPT; ++k) {
+                            const int i = tid + k * kPairThreads;
+                            const double x = c * xr[k] - sn * yr[k];
+                            const double y = sn * xr[k] + c * yr[k];
+                            if (i < m) {
+                                __stcg(wp + i, x);
+                                __stcg(wq + i, y);
+                                if (f & 2)
+                                    np2 = fma(x, x, np2);
+                                if (f & 4)
+                                    nq2 = fma(y, y, nq2);
+                            }
+                        }
+                        for (int i = tid + RPT * kPairThreads; i < m; i += kPairThreads) {
+                            const double x0 = __ldcg(wp + i), y0 = __ldcg(wq + i);
+                            const double x = c * x0 - sn * y0, y = sn * x0 + c * y0;
+                            __stcg(wp + i, x);
+                            __stcg(wq + i, y);
+                            if (f & 2)
+                                np2 = fma(x, x, np2);
+                            if (f & 4)
+                                nq2 = fma(y, y, nq2);
+                        }
+                        if (f & 6) {  // CTA-uniform: the flag is in shared memory
+                            np2 = warp_sum(np2);
+                            nq2 = warp_sum(nq2);
+                            __shared__ double rp[2][kPairThreads / 32];
+                            if (lane == 0) {
+                                rp[0][wid] = np2;
+                                rp[1][wid] = nq2;
+                            }
+                            __syncthreads();
+                            if (tid == 0) {
+                                if (f & 2)
+                                    w.nrm[p] = (rp[0][0] + rp[0][1]) + (rp[0][2] + rp[0][3]);
+                                if (f & 4)
+                                    w.nrm[q] = (rp[1][0] + rp[1][1]) + (rp[1][2] + rp[1][3]);
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    __threadfence();
+                    st_relaxed(w.ver + p, R + 1u);
+                    if (q < n)
+                        st_relaxed(w.ver + q, R + 1u);
+                    if (rotated)
+                        atomicAdd(rot, 1u);
+                }
+            }
+        }
+        if (tid == 0 && my_big)
+            atomicMax(maxcos + (sweep % 3), 1ull);
+        if (!grid_barrier(w.bar, unsigned(nblk)))
+            return;
+        const unsigned long long big = *(volatile unsigned long long *)(maxcos + (sweep % 3));
+        bool done = *(volatile unsigned *)rot == 0u || big == 0ull;
+        if (bid == 0 && tid == 0)
+            w.bar[6] = unsigned(sweep + 1);
+        if (done)
+            return;
+    }
+    if (bid == 0 && tid == 0)
+        atomicExch(w.bar + 5, unsigned(WOS_NO_CONVERGENCE));
 }
 
 // One pair per CTA of kPairThreads threads; the m rows are split over the
@@ -341,6 +524,96 @@ jacobi_kernel(const SvdWork *works, const int *begin, int np)
     const int p = problem_of(begin, np);
     const SvdWork w = works[p];
     jacobi_body<RPT>(w, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
+}
+
+template <int RPT>
+__global__ void __launch_bounds__(kPairThreads)
+jacobi_lean_kernel(const SvdWork *works, const int *begin, int np)
+{
+    const int p = problem_of(begin, np);
+    const SvdWork w = works[p];
+    jacobi_lean_body<RPT>(w, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
+}
+
+// Squared norms of the n columns (length m) of w.W into w.nrm, a warp per
+// column.
+__global__ void column_sq_norms_kernel(SvdWork w)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int j = gw; j < w.n; j += nw) {
+        const double *c = w.W + size_t(j) * w.m;
+        double s = 0.0;
+        for (int i = lane; i < w.m; i += 32)
+            s = fma(c[i], c[i], s);
+        s = warp_sum(s);
+        if (lane == 0)
+            w.nrm[j] = s;
+    }
+}
+
+// Z = P X: row perm[k] of Z is row k of X (n x n, column-major), so that the
+// columns of Z are the right singular vectors of W scaled by sigma.
+__global__ void permute_rows_kernel(const double *X, const int *perm, int n, double *Z)
+{
+    const size_t nn = size_t(n) * n;
+    for (size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nn;
+         t += size_t(gridDim.x) * blockDim.x) {
+        const int j = int(t / n), k = int(t - size_t(j) * n);
+        Z[size_t(j) * n + perm[k]] = X[t];
+    }
+}
+
+// C = A B in FP64, column-major: A m x k (lda = m), B k x n (ldb = k), C m x n
+// (ldc = m).  64 x 64 tiles of C per block of 256 threads, 4 x 4 per thread,
+// k in steps of 16 through shared memory.
+constexpr int kGemmTile = 64, kGemmK = 16;
+
+__global__ void __launch_bounds__(256)
+dgemm_nn_kernel(int m, int n, int k, const double *A, const double *B, double *C)
+{
+    __shared__ double As[kGemmK][kGemmTile + 1];
+    __shared__ double Bs[kGemmK][kGemmTile + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;  // 16 x 16 threads, 4 x 4 each
+    const int i0 = blockIdx.x * kGemmTile, j0 = blockIdx.y * kGemmTile;
+    double acc[4][4] = {};
+    for (int l0 = 0; l0 < k; l0 += kGemmK) {
+        // A tile: 64 rows x 16 columns; B tile: 16 rows x 64 columns
+        for (int e = tid; e < kGemmTile * kGemmK; e += 256) {
+            const int ii = e % kGemmTile, ll = e / kGemmTile;
+            const int gi = i0 + ii, gl = l0 + ll;
+            As[ll][ii] = (gi < m && gl < k) ? A[size_t(gl) * m + gi] : 0.0;
+            const int lb = e % kGemmK, jj = e / kGemmK;
+            const int gl2 = l0 + lb, gj = j0 + jj;
+            Bs[lb][jj] = (gl2 < k && gj < n) ? B[size_t(gj) * k + gl2] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ll = 0; ll < kGemmK; ++ll) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = As[ll][tx + 16 * u];
+                b[u] = Bs[ll][ty + 16 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    acc[u][v] = fma(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int gi = i0 + tx + 16 * u, gj = j0 + ty + 16 * v;
+            if (gi < m && gj < n)
+                C[size_t(gj) * m + gi] = acc[u][v];
+        }
 }
 
 
@@ -719,7 +992,7 @@ __global__ void form_left_kernel(const LeftJob *jobs, int njobs, int ncols)
 // as finalize_kernel.
 __global__ void finalize_pre_kernel(const double *L, const double *X, const int *perm,
                                     const double *sv, int m, int n, int transposed,
-                                    double *U, double *S, double *V)
+                                    int lean, double *U, double *S, double *V)
 {
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -736,6 +1009,8 @@ __global__ void finalize_pre_kernel(const double *L, const double *X, const int 
         for (int o = 16; o > 0; o >>= 1)
             rank += __shfl_xor_sync(FULL, rank, o);
         const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
+        // L's columns: unit (Q V_X), or sigma^2 times unit without V (W P X)
+        const double ls = lean ? inv * inv : 1.0;
         const double *lc = L + size_t(j) * m;
         const double *xc = X + size_t(j) * n;
         // sign: largest-magnitude entry of the B-side right vector (lowest
@@ -745,7 +1020,7 @@ __global__ void finalize_pre_kernel(const double *L, const double *X, const int 
         double at = 0.0;
         const int rn = transposed ? m : n;
         for (int i = lane; i < rn; i += 32) {
-            const double val = transposed ? lc[i] : xc[i];
+            const double val = transposed ? lc[i] * ls : xc[i];
             const int row = transposed ? i : perm[i];
             const double a = fabs(val);
             if (a > big || (a == big && row < arg)) {
@@ -770,12 +1045,12 @@ __global__ void finalize_pre_kernel(const double *L, const double *X, const int 
             S[rank] = sj;
         if (!transposed) {
             for (int i = lane; i < m; i += 32)   // U: M_D = m rows
-                U[size_t(i) * k + rank] = sign * lc[i];
+                U[size_t(i) * k + rank] = sign * (lc[i] * ls);
             for (int i = lane; i < n; i += 32)   // V: M_1 = n rows
                 V[size_t(perm[i]) * k + rank] = sign * xc[i] * inv;
         } else {
             for (int i = lane; i < m; i += 32)   // V: M_1 = m rows
-                V[size_t(i) * k + rank] = sign * lc[i];
+                V[size_t(i) * k + rank] = sign * (lc[i] * ls);
             for (int i = lane; i < n; i += 32)   // U: M_D = n rows
                 U[size_t(perm[i]) * k + rank] = sign * xc[i] * inv;
         }
@@ -924,13 +1199,20 @@ struct SvdProb {
     double *U, *S, *V;
     Lists L;
     bool pre;
+    bool lean;       // grid-wide Jacobi without V (more than 256 columns)
     int cl;          // cluster size of the cluster kernel, 0 = grid-wide kernels
     SvdWork w, wj;   // W itself, and the matrix Jacobi works on (W or X = R^T)
     QrWork q;
     double *sv, *Lb;
+    double *W0;      // lean: a copy of W (the QR overwrites W)
     int *g1;
     int qgrid;
 };
+
+// Columns above which the grid-wide Jacobi runs without V (jacobi_lean_body):
+// the sizes the cluster kernel cannot take, where the sweeps' FP64 work
+// bounds the factorisation.
+constexpr int kLeanMinN = kClMaxN + 1;
 
 int rpt_of(int m)
 {
@@ -938,6 +1220,19 @@ int rpt_of(int m)
     // costs its warp's FP64 instruction)
     const int need = (m + kPairThreads - 1) / kPairThreads;
     return need <= 6 ? (need < 1 ? 1 : need) : 8;
+}
+
+const void *jacobi_lean_kernel_rpt(int rpt)
+{
+    switch (rpt) {
+    case 1: return reinterpret_cast<const void *>(&jacobi_lean_kernel<1>);
+    case 2: return reinterpret_cast<const void *>(&jacobi_lean_kernel<2>);
+    case 3: return reinterpret_cast<const void *>(&jacobi_lean_kernel<3>);
+    case 4: return reinterpret_cast<const void *>(&jacobi_lean_kernel<4>);
+    case 5: return reinterpret_cast<const void *>(&jacobi_lean_kernel<5>);
+    case 6: return reinterpret_cast<const void *>(&jacobi_lean_kernel<6>);
+    default: return reinterpret_cast<const void *>(&jacobi_lean_kernel<8>);
+    }
 }
 
 const void *jacobi_kernel_rpt(int rpt)
@@ -1055,7 +1350,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     std::vector<size_t> o_base(np);
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off += al(b); return o; };
-    struct Off { size_t W, V, sv, bar, ver, g1, X, L, tau, perm, cn, cn0, done, pv, pi, qbar; };
+    struct Off { size_t W, V, sv, bar, ver, g1, X, L, tau, perm, cn, cn0, done, pv, pi, qbar, W0, nrm; };
     std::vector<Off> O(np);
     for (int p = 0; p < np; ++p) {
         SvdProb &b = P[p];
@@ -1065,6 +1360,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         w.n_pad = std::max(2, w.n + (w.n & 1));
         b.pre = w.n >= kPrecondMinN;
         b.cl = wos::ctx_svd_path(ctx) == WOS_SVD_GRID ? 0 : cluster_fit(ctx, w.m, w.n, b.pre);
+        b.lean = b.pre && !b.cl && w.n >= kLeanMinN;
         b.qgrid = b.pre ? std::max(1, std::min({w.n, 2 * sms, qbudget})) : 0;
         Off &o = O[p];
         o.W = take(size_t(w.m) * w.n * 8);
@@ -1084,6 +1380,10 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
             o.pv = take(size_t(b.qgrid) * 2 * 8);
             o.pi = take(size_t(b.qgrid) * 2 * 4);
             o.qbar = take(64);
+        }
+        if (b.lean) {
+            o.W0 = take(size_t(w.m) * w.n * 8);
+            o.nrm = take(size_t(w.n) * 8);
         }
     }
     const size_t o_jrec = take(sizeof(SvdWork) * np), o_qrec = take(sizeof(QrWork) * np);
@@ -1115,7 +1415,13 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         form_B_kernel<<<sms * 4, 256, 0, st>>>(w, b.counts, b.M_D, b.M_tot, 1.0 / double(b.N),
                                               b.g1, b.M_1, b.nu, b.sigma, b.transposed);
         ++launches;
+        b.W0 = nullptr;
+        if (b.lean) {
+            b.W0 = reinterpret_cast<double *>(base + o.W0);
+            cudaMemcpyAsync(b.W0, w.W, size_t(w.m) * w.n * 8, cudaMemcpyDeviceToDevice, st);
+        }
         b.wj = w;
+        b.wj.nrm = b.lean ? reinterpret_cast<double *>(base + o.nrm) : nullptr;
         if (b.pre) {
             QrWork &q = b.q;
             q.A = w.W;
@@ -1211,20 +1517,27 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         if (P[p].pre && !P[p].cl) {
             build_x_kernel<<<sms * 4, 256, 0, st>>>(P[p].q, P[p].wj.W, P[p].wj.Vw);
             ++launches;
+            if (P[p].lean) {  // the squared column norms the lean sweeps carry
+                column_sq_norms_kernel<<<sms * 2, 256, 0, st>>>(P[p].wj);
+                ++launches;
+            }
         }
     // Jacobi: one cooperative launch per class of rows per thread (and per
     // group of co-resident problems); the CTAs are shared in proportion to
     // the pairs when the batch is larger than the GPU
-    for (int rpt : {1, 2, 3, 4, 5, 6, 8}) {
+    for (int cls = 0; cls < 14; ++cls) {
         if (e != cudaSuccess)
             break;
+        static const int kRpts[7] = {1, 2, 3, 4, 5, 6, 8};
+        const int rpt = kRpts[cls % 7];
+        const bool lean = cls >= 7;
         std::vector<int> idx;
         for (int p = 0; p < np; ++p)
-            if (!P[p].cl && rpt_of(P[p].wj.m) == rpt)
+            if (!P[p].cl && rpt_of(P[p].wj.m) == rpt && P[p].lean == lean)
                 idx.push_back(p);
         if (idx.empty())
             continue;
-        const void *jk = jacobi_kernel_rpt(rpt);
+        const void *jk = lean ? jacobi_lean_kernel_rpt(rpt) : jacobi_kernel_rpt(rpt);
         int bps = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, jk, kPairThreads, 0);
         const int budget = std::max(1, bps) * sms;
@@ -1241,29 +1554,47 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     }
     if (jacobi_events && jacobi_events[1])
         cudaEventRecord(static_cast<cudaEvent_t>(jacobi_events[1]), st);
-    if (e == cudaSuccess && !pidx.empty()) {  // left vectors of every preconditioned problem
+    // left vectors without V: L = W P X_final (an FP64 GEMM of the saved W
+    // with the row-permuted final X; its columns are sigma^2 times the unit
+    // left vectors, scaled in finalize)
+    for (int p = 0; e == cudaSuccess && p < np; ++p)
+        if (P[p].lean) {
+            SvdProb &b = P[p];
+            const int m = b.w.m, n = b.w.n;
+            permute_rows_kernel<<<sms * 4, 256, 0, st>>>(b.wj.W, b.q.perm, n, b.wj.Vw);
+            dim3 gg(unsigned((m + kGemmTile - 1) / kGemmTile),
+                    unsigned((n + kGemmTile - 1) / kGemmTile));
+            dgemm_nn_kernel<<<gg, 256, 0, st>>>(m, n, n, b.W0, b.wj.Vw, b.Lb);
+            launches += 2;
+        }
+    if (e == cudaSuccess) {  // left vectors of every other preconditioned problem
         std::vector<LeftJob> jobs;
         int ncols = 0;
         for (int p : pidx) {
+            if (P[p].lean)
+                continue;
             jobs.push_back(LeftJob{P[p].q, P[p].wj.Vw, P[p].Lb, ncols});
             ncols += P[p].w.n;
         }
-        LeftJob *dl = reinterpret_cast<LeftJob *>(base + o_left);
-        cudaMemcpyAsync(dl, jobs.data(), sizeof(LeftJob) * jobs.size(), cudaMemcpyHostToDevice,
-                        st);
-        // two warps (columns) per block: the columns spread over the SMs'
-        // sub-partitions (each warp's dependent FP64 chain of n reflectors
-        // holds its sub-partition's FP64 unit; two per SM would queue)
-        form_left_kernel<<<std::max(1, std::min((ncols + 1) / 2, sms * 16)), 64, 0, st>>>(
-            dl, int(jobs.size()), ncols);
-        ++launches;
+        if (!jobs.empty()) {
+            LeftJob *dl = reinterpret_cast<LeftJob *>(base + o_left);
+            cudaMemcpyAsync(dl, jobs.data(), sizeof(LeftJob) * jobs.size(),
+                            cudaMemcpyHostToDevice, st);
+            // two warps (columns) per block: the columns spread over the SMs'
+            // sub-partitions (each warp's dependent FP64 chain of n reflectors
+            // holds its sub-partition's FP64 unit; two per SM would queue)
+            form_left_kernel<<<std::max(1, std::min((ncols + 1) / 2, sms * 16)), 64, 0, st>>>(
+                dl, int(jobs.size()), ncols);
+            ++launches;
+        }
     }
     for (int p = 0; e == cudaSuccess && p < np; ++p) {
         SvdProb &b = P[p];
         column_norms_kernel<<<sms, 256, 0, st>>>(b.wj, b.sv);
         if (b.pre)
             finalize_pre_kernel<<<sms, 256, 0, st>>>(b.Lb, b.wj.W, b.q.perm, b.sv, b.w.m, b.w.n,
-                                                     b.transposed, b.U, b.S, b.V);
+                                                     b.transposed, b.lean ? 1 : 0, b.U, b.S,
+                                                     b.V);
         else
             finalize_kernel<<<sms, 256, 0, st>>>(b.w, b.sv, b.transposed, b.U, b.S, b.V);
         launches += 2;

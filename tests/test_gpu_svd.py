@@ -79,8 +79,28 @@ def test_svd_matches_oracle_on_oracle_counts(make, svd_path):
     np.testing.assert_allclose(s ** 2, ev, rtol=1e-9, atol=1e-14 * ev[0])
 
 
-@pytest.mark.parametrize("shape", [(256, 256, 128), (96, 300, 200), (1024, 1536, 768)])
+def _orth_tol(s):
+    """Elementwise bound of |U^T U - I| for singular vectors recovered as
+    W v / sigma (the grid-wide path above 256 columns, which does not
+    accumulate V): the rounding error of column i is about eps |W| / s_i
+    relative, so entry (i, j) may reach c eps s_1 / min(s_i, s_j), c = 64;
+    plus 1e-12 for the norms, W v_j and sigma_j (from the preconditioned
+    factor) agreeing to ~1e-12 relative."""
+    eps = np.finfo(float).eps
+    sm = np.minimum.outer(s, s)
+    return 64 * eps * s[0] / np.maximum(sm, 1e-300) + 1e-12
+
+
+@pytest.mark.parametrize("shape", [(256, 256, 128), (96, 300, 200), (1024, 1536, 768),
+                                   (600, 900, 300), (300, 900, 600)])
 def test_svd_matches_oracle_at_benchmark_shapes(shape, svd_path):
+    """Operator-shaped counts at the benchmark sizes (1024 x 768 is the 3-D
+    configuration's Gamma_1 block) and beyond the cluster kernel in both
+    orientations (300 and 600 columns of the worked matrix): singular values
+    as the oracle's, both sets of singular vectors orthonormal (to 1e-12, or
+    to the bound of _orth_tol for vectors formed as W v / sigma), B
+    reproduced to 1e-13 s_1, and the leading subspaces at gaps as the
+    oracle's."""
     M_D, M_tot, M_1 = shape
     N = 100_000
     C = W.synthetic_counts(M_D, M_tot, N, seed=M_D)
@@ -91,6 +111,15 @@ def test_svd_matches_oracle_at_benchmark_shapes(shape, svd_path):
     (U, s, V, sweeps), (Uo, so, Vo), _ = _svd_pair(C, N, g1, sigma, nu)
     _check_sv(s, so)
     assert sweeps < 40
+    k = len(s)
+    tol = _orth_tol(so) if max(M_D, M_1) > 256 and min(M_D, M_1) > 256 else 1e-12
+    assert np.all(np.abs(U.T @ U - np.eye(k)) <= tol)
+    assert np.all(np.abs(V.T @ V - np.eye(k)) <= tol)
+    B = O.operator_B(C, N, g1, nu, sigma)
+    np.testing.assert_allclose(U @ np.diag(s) @ V.T, B, atol=1e-13 * so[0])
+    for r in _gaps(so, 12):
+        np.testing.assert_allclose(U[:, :r] @ U[:, :r].T, Uo[:, :r] @ Uo[:, :r].T, atol=1e-8)
+        np.testing.assert_allclose(V[:, :r] @ V[:, :r].T, Vo[:, :r] @ Vo[:, :r].T, atol=1e-8)
 
 
 def test_reconstruction_matches_oracle():
@@ -266,3 +295,35 @@ def test_svd_path_setting_is_checked():
             wos.wos_set_svd_path(ctx(), bad)
         assert e.value.code == 1
     wos.wos_set_svd_path(ctx(), wos.SVD_AUTO)
+
+
+def test_bauer_spiral_shell_end_to_end_with_library_measures():
+    """The paper's own discretisation of Ex. 5.6 (unit ball minus the ball of
+    radius 1/2; extrinsic Voronoi cells of 1000 + 100 Bauer-spiral sites;
+    100 points on the spiral of radius 0.95) through the library alone:
+    build, cell measures sigma(omega_j) from wos_element_measures (no caller
+    measures), SVD and TSVD.  Against the oracle on the same counts (with the
+    oracle's own measures): singular values to 1e-10, the reconstruction at
+    the gaps to 1e-8."""
+    from gpu_util import gpu_build
+    inst = W.shell_config(N=20_000, n_points=100, voronoi=(1000, 100))
+    r = gpu_build(inst, trace=False)
+    C = r["counts"]
+    assert (C.sum(1) + r["unterm"] == inst.N).all()
+    sigma = O.voronoi_measures(inst.domain, inst.partition)
+    sigma_lib = wos.wos_element_measures(inst.domain, inst.partition)
+    g1 = inst.partition.gamma1
+    nu = inst.nu_vec()
+    meas = W.measurements(inst, noise=0.01)
+    (U, s, V, _), (Uo, so, Vo), (Ct, sg, nut) = _svd_pair(C, inst.N, g1, sigma, nu, sigma_lib)
+    _check_sv(s, so)
+    Ut, St, Vt = (torch.as_tensor(x, device=DEV) for x in (U, s, V))
+    uD = torch.as_tensor(meas.uD, device=DEV)
+    u0 = torch.as_tensor(meas.u0, device=DEV)
+    gaps = _gaps(so, 40)   # clusters of 1, 3, 5, 7, ... (Sec. 5.3): gaps at 16, 25
+    assert gaps
+    for rr in gaps:
+        u1, _ = wos.wos_reconstruct(ctx(), Ut, St, Vt, Ct, inst.N, g1, sg, uD, rr, u0=u0,
+                                    nu=nut)
+        ro, _ = O.reconstruct(Uo, so, Vo, rr, C, inst.N, g1, nu, sigma, meas.uD, meas.u0)
+        assert np.linalg.norm(u1.cpu().numpy() - ro) <= 1e-8 * np.linalg.norm(ro), rr
