@@ -128,13 +128,20 @@ typedef struct {
     void *kernel_events[2]; /* optional cudaEvent_t pair (caller-created):
                                recorded on `stream` right before and after
                                the walk kernel, to time it alone */
-    int32_t mapped;      /* 1: walk-on-spheres in y = S^{-1} x with the exact
-                            distance to the polytope S^{-1} D (larger steps
-                            than the paper's ellipsoids inside the Euclidean
-                            ball, Sec. 4.2); stop at dist_y <= eps (then
-                            dist_x <= eps); exits classified in x.  Boxes and
-                            convex counter-clockwise polygons of at most 8
-                            edges without holes, else WOS_INVALID_ARG */
+    int32_t mapped;      /* 1: the chain of Sec. 4.2 with larger steps: the
+                            ellipsoid X + rho S B(0,1) of each step is the
+                            largest inside D, i.e. rho = dist_y(S^{-1} X) in
+                            y = S^{-1} x (instead of dist_x).  Boxes and convex
+                            counter-clockwise polygons of at most 8 edges
+                            without holes: walk-on-spheres in y with the
+                            exact distance to the polytope S^{-1} D, stop at
+                            dist_y <= eps.  Discs / balls minus disc / ball
+                            holes: rho = a lower bound of dist_y that is
+                            exact to first order at dD and >= dist_x (one
+                            quadratic majorant per boundary component), stop
+                            at rho <= eps.  Either way dist_x <= eps at the
+                            stop and exits are classified in x; other
+                            domains: WOS_INVALID_ARG */
     int32_t group_blocks; /* Philox blocks per group of steps (0 = about 16
                             steps, at most 16 blocks): a group is
                             group_blocks x (4 / words per step) steps, the
@@ -179,8 +186,16 @@ int32_t wos_num_elements(const wos_domain *domain, const wos_partition *part);
 
 /* sigma(omega_j) of every element (arc length, edge-cell length or patch
  * area: the surface measure of the cell, paper Sec. 3.1, Eq.
- * (boundary_weights)).  out: host, M_tot doubles.  Extrinsic Voronoi
- * partitions have no closed form: WOS_INVALID_ARG. */
+ * (boundary_weights)).  out: host, M_tot doubles.  Host only.
+ * Extrinsic Voronoi partitions (App. A, Ex. A.2) are supported when every
+ * site lies on a circle / sphere of D (the outer sphere or a hole, within
+ * 1e-9 of its radius), each such surface shared among its own sites: 2-D
+ * cells are arcs between the bisectors of angular neighbours, 3-D cells
+ * spherical Voronoi polygons (built by half-plane clipping in the central
+ * projection at the site; areas from spherical triangles); identical sites
+ * give the lowest index the cell and the others 0.  Errors: WOS_INVALID_ARG
+ * (bad descriptors; Voronoi sites on a box or polygon, off every circle /
+ * sphere, or a cell reaching 89.9 degrees from its site). */
 wos_status wos_element_measures(const wos_domain *domain,
                                 const wos_partition *part, double *out);
 

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <atomic>
@@ -427,6 +428,8 @@ static int polytope_faces(const wos_domain &d, double (*a)[3], double *c)
 
 bool mapped_supported(const wos_domain &d)
 {
+    if (d.outer_kind == WOS_OUTER_SPHERE)
+        return true;  // a disc / ball minus any holes: the quadric bound
     if (d.n_holes != 0)
         return false;
     if (d.outer_kind == WOS_OUTER_BOX)
@@ -496,6 +499,23 @@ void set_mapped(const wos_domain &d, const double *S, Geom<Real> &g)
     }
 }
 
+template <typename Real>
+void set_quadric(const wos_domain &d, const double *S, Geom<Real> &g)
+{
+    const int dim = d.dim;
+    double w[3], Q[9];
+    sym_eig(dim, S, w, Q);
+    double mu = w[0];
+    for (int a = 1; a < dim; ++a)
+        mu = std::min(mu, w[a]);
+    g.mapped = 2;
+    for (int i = 0; i < 9; ++i)
+        g.mS[i] = i < dim * dim ? Real(S[i]) : Real(0);
+    g.qmu2 = Real(mu * mu);
+}
+
+template void set_quadric<float>(const wos_domain &, const double *, Geom<float> &);
+template void set_quadric<double>(const wos_domain &, const double *, Geom<double> &);
 template void set_mapped<float>(const wos_domain &, const double *, Geom<float> &);
 template void set_mapped<double>(const wos_domain &, const double *, Geom<double> &);
 
@@ -549,14 +569,233 @@ extern "C" double wos_fp32_eps_floor(const wos_domain *d)
     return d ? fp32_floor(*d) : 0.0;
 }
 
+// ---------------------------------------------------------------------------
+// sigma(omega_j) of extrinsic Voronoi cells (App. A, Ex. A.2) whose sites lie
+// on the circles / spheres of the domain (the outer sphere and the holes);
+// each of those surfaces is shared among its own sites (a site belongs to the
+// circle or sphere it lies on, within 1e-9 of its radius).
+//   2-D: the cell of a site on a circle of radius r is the arc between the
+//        bisectors of its two angular neighbours (the perpendicular bisector
+//        of two points of a circle passes through its centre), of length
+//        r (theta_next - theta_prev) / 2; a lone site owns the whole circle.
+//   3-D: the cell of a site s on a sphere is {x : x.s >= x.s' for every other
+//        site s' of the sphere}, an intersection of hemispheres.  In the
+//        central (gnomonic) projection onto the plane tangent at s every
+//        great circle is a line, so the cell is a convex polygon, built by
+//        clipping a square by one half-plane per other site; its area is
+//        the sum of the spherical triangles (s, v_k, v_{k+1}), each from
+//        tan(E / 2) = a.(b x c) / (1 + a.b + b.c + c.a) (Van Oosterom &
+//        Strackee, IEEE Trans. Biomed. Eng. 30, 1983).  A cell reaching
+//        89.9 degrees from its site is not representable: WOS_INVALID_ARG.
+// Identical sites: the lowest index owns the cell, the others get 0 (the
+// classifier's tie rule).  Outer boxes and polygons: WOS_INVALID_ARG.
+// ---------------------------------------------------------------------------
+namespace {
+
+// A vertex of the clipped polygon and the line of the edge that starts at
+// it (line index into the caller's table).
+struct P2 {
+    double a, b;
+    int next;
+};
+struct Line {
+    double A, B, C;  // A a + B b = C
+};
+
+// Keeps the part of the convex polygon with A a + B b <= C, line j of the
+// table (Sutherland & Hodgman, one edge).
+void clip_half_plane(std::vector<P2> &poly, const Line &ln, int j, std::vector<P2> &tmp)
+{
+    tmp.clear();
+    const size_t n = poly.size();
+    for (size_t k = 0; k < n; ++k) {
+        const P2 u = poly[k], v = poly[(k + 1) % n];
+        const double fu = ln.A * u.a + ln.B * u.b - ln.C, fv = ln.A * v.a + ln.B * v.b - ln.C;
+        if (fu <= 0.0)
+            tmp.push_back(u);
+        if ((fu < 0.0 && fv > 0.0) || (fu > 0.0 && fv < 0.0)) {
+            const double t = fu / (fu - fv);
+            const P2 x{u.a + t * (v.a - u.a), u.b + t * (v.b - u.b), fu < 0.0 ? j : u.next};
+            tmp.push_back(x);
+        }
+    }
+    poly.swap(tmp);
+}
+
+double spherical_cell_area(const double *u0, const std::vector<const double *> &others,
+                           bool *ok)
+{
+    // tangent basis e1, e2 of the plane at u0
+    double t[3] = {0, 0, 0};
+    int ax = 0;
+    for (int a = 1; a < 3; ++a)
+        if (std::fabs(u0[a]) < std::fabs(u0[ax]))
+            ax = a;
+    t[ax] = 1.0;
+    double e1[3], e2[3];
+    const double td = t[0] * u0[0] + t[1] * u0[1] + t[2] * u0[2];
+    for (int a = 0; a < 3; ++a)
+        e1[a] = t[a] - td * u0[a];
+    const double n1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (int a = 0; a < 3; ++a)
+        e1[a] /= n1;
+    e2[0] = u0[1] * e1[2] - u0[2] * e1[1];
+    e2[1] = u0[2] * e1[0] - u0[0] * e1[2];
+    e2[2] = u0[0] * e1[1] - u0[1] * e1[0];
+    const double L = 1.0e3;  // tan(89.94 degrees)
+    // lines 0..3: the square's sides; 4 + q: the bisector of other site q
+    std::vector<Line> lines = {{0, -1, L}, {1, 0, L}, {0, 1, L}, {-1, 0, L}};
+    std::vector<P2> poly = {{-L, -L, 0}, {L, -L, 1}, {L, L, 2}, {-L, L, 3}}, tmp;
+    for (const double *uj : others) {
+        // x = u0 + a e1 + b e2 is in the cell when x.(u0 - uj) >= 0
+        const Line ln{e1[0] * uj[0] + e1[1] * uj[1] + e1[2] * uj[2],
+                      e2[0] * uj[0] + e2[1] * uj[1] + e2[2] * uj[2],
+                      1.0 - (u0[0] * uj[0] + u0[1] * uj[1] + u0[2] * uj[2])};
+        lines.push_back(ln);
+        clip_half_plane(poly, ln, int(lines.size()) - 1, tmp);
+        if (poly.empty())
+            return 0.0;
+    }
+    // every vertex again as the intersection of the lines of its two edges
+    // (the clipping interpolated along edges whose far ends can lie 1e3 away)
+    const size_t n = poly.size();
+    for (size_t k = 0; k < n; ++k) {
+        const Line &l1 = lines[poly[(k + n - 1) % n].next], &l2 = lines[poly[k].next];
+        const double det = l1.A * l2.B - l1.B * l2.A;
+        if (det != 0.0) {
+            poly[k].a = (l1.C * l2.B - l1.B * l2.C) / det;
+            poly[k].b = (l1.A * l2.C - l1.C * l2.A) / det;
+        }
+    }
+    double area = 0.0;
+    std::vector<std::array<double, 3>> v(n);
+    for (size_t k = 0; k < n; ++k) {
+        if (std::fabs(poly[k].a) >= 0.5 * L || std::fabs(poly[k].b) >= 0.5 * L)
+            *ok = false;
+        double x[3];
+        for (int a = 0; a < 3; ++a)
+            x[a] = u0[a] + poly[k].a * e1[a] + poly[k].b * e2[a];
+        const double nx = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        for (int a = 0; a < 3; ++a)
+            v[k][a] = x[a] / nx;
+    }
+    for (size_t k = 0; k < n; ++k) {
+        const double *b = v[k].data(), *c = v[(k + 1) % n].data();
+        const double bc[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2],
+                              b[0] * c[1] - b[1] * c[0]};
+        const double num = u0[0] * bc[0] + u0[1] * bc[1] + u0[2] * bc[2];
+        const double den = 1.0 + (u0[0] * b[0] + u0[1] * b[1] + u0[2] * b[2]) +
+                           (b[0] * c[0] + b[1] * c[1] + b[2] * c[2]) +
+                           (c[0] * u0[0] + c[1] * u0[1] + c[2] * u0[2]);
+        area += 2.0 * std::atan2(num, den);
+    }
+    return std::fabs(area);
+}
+
+wos_status voronoi_cell_measures(const wos_domain &d, const wos_partition &p, double *out)
+{
+    if (d.outer_kind != WOS_OUTER_SPHERE)
+        return WOS_INVALID_ARG;
+    const int dim = d.dim, ns = p.voronoi_n;
+    const int ncomp = 1 + d.n_holes;
+    auto centre = [&](int c) { return c == 0 ? d.center : d.hole_center[c - 1]; };
+    auto radius = [&](int c) { return c == 0 ? d.radius : d.hole_radius[c - 1]; };
+    std::vector<int> owner(ns, -1);
+    std::vector<double> u(size_t(ns) * 3, 0.0);  // unit vector from the centre
+    for (int j = 0; j < ns; ++j) {
+        const double *x = p.voronoi_sites + size_t(j) * dim;
+        for (int c = 0; c < ncomp && owner[j] < 0; ++c) {
+            const double *cc = centre(c);
+            const double r = radius(c);
+            double v[3] = {0, 0, 0}, n2 = 0.0;
+            for (int a = 0; a < dim; ++a) {
+                v[a] = x[a] - cc[a];
+                n2 += v[a] * v[a];
+            }
+            const double nv = std::sqrt(n2);
+            if (std::fabs(nv - r) <= 1e-9 * std::max(r, 1.0) && nv > 0.0) {
+                owner[j] = c;
+                for (int a = 0; a < dim; ++a)
+                    u[size_t(j) * 3 + a] = v[a] / nv;
+            }
+        }
+        if (owner[j] < 0)
+            return WOS_INVALID_ARG;  // a site on no circle / sphere of D
+    }
+    const double pi = 3.14159265358979323846;
+    for (int c = 0; c < ncomp; ++c) {
+        std::vector<int> idx;
+        for (int j = 0; j < ns; ++j)
+            if (owner[j] == c)
+                idx.push_back(j);
+        if (idx.empty())
+            continue;
+        const double r = radius(c);
+        // identical sites: the lowest index keeps the cell
+        std::vector<char> dup(ns, 0);
+        for (size_t a = 0; a < idx.size(); ++a)
+            for (size_t b = 0; b < a; ++b) {
+                const double *ua = &u[size_t(idx[a]) * 3], *ub = &u[size_t(idx[b]) * 3];
+                if (ua[0] == ub[0] && ua[1] == ub[1] && ua[2] == ub[2]) {
+                    dup[idx[a]] = 1;
+                    break;
+                }
+            }
+        std::vector<int> live;
+        for (int j : idx) {
+            if (dup[j])
+                out[j] = 0.0;
+            else
+                live.push_back(j);
+        }
+        if (dim == 2) {
+            if (live.size() == 1) {
+                out[live[0]] = 2 * pi * r;
+                continue;
+            }
+            std::vector<std::pair<double, int>> ang;
+            for (int j : live)
+                ang.push_back({std::atan2(u[size_t(j) * 3 + 1], u[size_t(j) * 3]), j});
+            std::sort(ang.begin(), ang.end());
+            const size_t n = ang.size();
+            for (size_t k = 0; k < n; ++k) {
+                double nxt = ang[(k + 1) % n].first - ang[k].first;
+                double prv = ang[k].first - ang[(k + n - 1) % n].first;
+                if (k + 1 == n)
+                    nxt += 2 * pi;
+                if (k == 0)
+                    prv += 2 * pi;
+                out[ang[k].second] = r * 0.5 * (nxt + prv);
+            }
+        } else {
+            bool ok = true;
+            std::vector<const double *> others;
+            for (int j : live) {
+                others.clear();
+                for (int q : live)
+                    if (q != j)
+                        others.push_back(&u[size_t(q) * 3]);
+                out[j] = r * r * spherical_cell_area(&u[size_t(j) * 3], others, &ok);
+            }
+            if (!ok)
+                return WOS_INVALID_ARG;
+        }
+    }
+    return WOS_OK;
+}
+
+}  // namespace
+
 extern "C" wos_status wos_element_measures(const wos_domain *dp,
                                            const wos_partition *pp, double *out)
 {
     wos_status st = validate(dp, pp);
     if (st != WOS_OK)
         return st;
-    if (!out || pp->voronoi_n > 0)
+    if (!out)
         return WOS_INVALID_ARG;
+    if (pp->voronoi_n > 0)
+        return voronoi_cell_measures(*dp, *pp, out);
     const wos_domain &d = *dp;
     const wos_partition &p = *pp;
     const double pi = 3.14159265358979323846;
@@ -736,8 +975,10 @@ wos_status validate_build(const wos_context *ctx, const wos_domain *domain, cons
         return st;
     if (o->mapped != 0 && (o->mapped != 1 || !mapped_supported(*domain)))
         return WOS_INVALID_ARG;
+    // the polytope walks run in y = S^{-1} x, the others in x
+    const bool in_y = o->mapped && domain->outer_kind != WOS_OUTER_SPHERE;
     if (o->precision == WOS_FP32 &&
-        eps < (o->mapped ? fp32_floor_mapped(*domain, S) : fp32_floor(*domain)))
+        eps < (in_y ? fp32_floor_mapped(*domain, S) : fp32_floor(*domain)))
         return WOS_EPS_BELOW_FP32_FLOOR;
     return WOS_OK;
 }

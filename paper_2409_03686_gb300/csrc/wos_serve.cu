@@ -512,8 +512,6 @@ extern "C" wos_status wos_submit(wos_queue *q, const wos_request *rq, uint64_t *
     if (rq->u0 && R->M_0 > 0)
         R->u0.assign(rq->u0, rq->u0 + R->M_0);
     R->sigma.resize(R->M_tot);
-    if (rq->partition->voronoi_n > 0)
-        return WOS_INVALID_ARG;  // cell measures needed: intrinsic cells only
     st = wos_element_measures(rq->domain, rq->partition, R->sigma.data());
     if (st != WOS_OK)
         return st;

@@ -3,6 +3,7 @@ declare, its struct layout matches the binding, and its host-side logic
 (K set-up, element counts and measures, point check, FP32 floor, truncation
 rule) agrees with the oracle.  No device code runs here."""
 import ctypes
+import math
 import re
 import subprocess
 from pathlib import Path
@@ -195,3 +196,42 @@ def test_build_wrappers_refuse_host_tensors_before_the_library(lib):
         wos.wos_build_operator_noalloc(FakeCtx(), inst.domain, inst.K, pts, inst.partition,
                                        inst.N, inst.eps, inst.seed, counts)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("make", [
+    lambda: W.shell_config(voronoi=(1000, 100)),             # Ex. 5.6 sizes
+    lambda: W.shell_config(voronoi=(300, 40), shift=0.3),    # off-centre hole
+    lambda: W.annulus_voronoi_config(m0=500, m1=200),        # Ex. 5.2 / 5.3
+], ids=["shell-1000-100", "shell-shifted", "annulus"])
+def test_voronoi_cell_measures_match_the_oracle(lib, make):
+    """sigma(omega_j) of extrinsic Voronoi cells (App. A, Ex. A.2): the
+    library's own construction (half-plane clipping in the central
+    projection; arcs between bisectors) against the oracle's (scipy's
+    spherical Voronoi diagram; arcs), cell by cell, and their totals against
+    the surfaces' measures."""
+    inst = make()
+    a = wos.wos_element_measures(inst.domain, inst.partition)
+    b = O.voronoi_measures(inst.domain, inst.partition)
+    np.testing.assert_allclose(a, b, rtol=1e-12)
+    d = inst.domain
+    if d.dim == 3:
+        total = 4 * math.pi * (d.radius ** 2 + sum(r ** 2 for _, r in d.holes))
+    else:
+        total = 2 * math.pi * (d.radius + sum(r for _, r in d.holes))
+    assert a.sum() == pytest.approx(total, rel=1e-13)
+
+
+def test_voronoi_cell_measures_reject_unsupported_sites(lib):
+    """Sites off every circle / sphere of D, or a box domain: no closed
+    construction, WOS_INVALID_ARG."""
+    inst = W.shell_config(voronoi=(50, 10))
+    sites = inst.partition.voronoi_sites.copy()
+    sites[3] *= 0.9
+    bad = W.Partition(voronoi_sites=sites, gamma1=inst.partition.gamma1)
+    with pytest.raises(wos.WosError):
+        wos.wos_element_measures(inst.domain, bad)
+    sq = W.square_config(n_side=4)
+    part = W.Partition(voronoi_sites=W.element_centres(sq.domain, sq.partition),
+                       gamma1=sq.partition.gamma1)
+    with pytest.raises(wos.WosError):
+        wos.wos_element_measures(sq.domain, part)

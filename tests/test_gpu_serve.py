@@ -44,7 +44,7 @@ _alone_cache = {}
 
 
 def _alone(inst, m, r=0, alpha=0.0):
-    key = (inst.name, inst.fp64, r, alpha)
+    key = (inst.name, inst.M_D, inst.M_tot, inst.N, inst.stream, inst.eps, inst.fp64, r, alpha)
     if key in _alone_cache:
         return _alone_cache[key]
     dev = torch.device("cuda:0")
@@ -247,3 +247,25 @@ def test_served_requests_match_the_oracle():
         assert np.linalg.norm(t.u_gamma1 - ro) <= 1e-8 * np.linalg.norm(ro), (inst.name, r)
         checked += 1
     assert checked >= 3
+
+
+def test_voronoi_requests_are_served():
+    """Requests on extrinsic Voronoi partitions (the cell measures come from
+    the library): served in a mix with an intrinsic-cell request, each equal
+    to its lone solve bit for bit."""
+    insts = [W.shell_config(N=2000, n_points=40, voronoi=(300, 60), shift=0.3).replace(
+                 stream=1, seed=SEED),
+             W.annulus_voronoi_config(N=1500, eps=1e-5, fp64=False, n_points=30, m0=120,
+                                      m1=80).replace(stream=2, seed=SEED),
+             W.square_config(N=2000, grid=5, n_side=12).replace(stream=3, seed=SEED)]
+    meas = [W.measurements(inst, noise=0.01, seed=q) for q, inst in enumerate(insts)]
+    q = wos.wos_queue_create(ctx(), seed=SEED, slice_walks=700)
+    try:
+        tickets = [wos.wos_submit(q, inst, m.uD, m.u0, want_counts=True)
+                   for inst, m in zip(insts, meas)]
+        for t in tickets:
+            assert wos.wos_wait(q, t, 120_000)
+    finally:
+        wos.wos_queue_destroy(q)
+    for inst, m, t in zip(insts, meas, tickets):
+        _check(t, _alone(inst, m), inst.name)
