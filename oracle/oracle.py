@@ -64,6 +64,7 @@ def lib() -> ctypes.CDLL:
         build()
         L = ctypes.CDLL(str(_LIB_PATH))
         L.orc_dist.restype = ctypes.c_double
+        L.orc_quadric_radius.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -111,6 +112,7 @@ class OrcInstance(ctypes.Structure):
         ("plane_n", (ctypes.c_double * 3) * 64),
         ("plane_d", ctypes.c_double * 64),
         ("Sinv", ctypes.c_double * 9),
+        ("mu2", ctypes.c_double),
     ]
 
 
@@ -226,7 +228,11 @@ def make_instance(inst, words_per_uniform: int | None = None):
     if words_per_uniform is None:
         words_per_uniform = 2 if inst.fp64 else 1
     I.words_per_uniform = words_per_uniform
-    if getattr(inst, "mapped", False):
+    if getattr(inst, "mapped", False) and inst.domain.outer == "sphere":
+        # disc / ball minus holes: the quadric lower bound of dist_y
+        I.mapped = 2
+        I.mu2 = float(np.linalg.eigvalsh(S)[0]) ** 2
+    elif getattr(inst, "mapped", False):
         pn, pd = mapped_planes(inst.domain, S)
         I.mapped = 1
         I.n_planes = len(pd)
@@ -260,6 +266,16 @@ def dist(dom, part, X):
     for q in range(len(X)):
         out[q] = L.orc_dist(ctypes.byref(D), _p(X[q]))
     return out
+
+
+def mapped_radius(inst, X):
+    """Step radius of the mapped chain on a disc / ball minus holes (the
+    quadric lower bound of dist_y, Sec. 4.2 in y = S^{-1} x) at points X."""
+    I, keep = make_instance(inst.replace(mapped=True))
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, inst.dim)
+    L = lib()
+    return np.array([L.orc_quadric_radius(ctypes.byref(I), _p(X[q]))
+                     for q in range(len(X))])
 
 
 def classify(dom, part, X):

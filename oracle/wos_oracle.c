@@ -437,10 +437,71 @@ static int orc_walk_mapped(const orc_instance *I, const double *x0, uint64_t wal
     }
 }
 
+/* The mapped chain on a disc / ball D minus disc / ball holes (mapped = 2).
+ * Its step from X is the largest ellipsoid X + rho S B(0, 1) inside D, whose
+ * radius is rho = dist_y(S^{-1} X, S^{-1} dD) in y = S^{-1} x (where the
+ * diffusion of div(K grad) is a Brownian motion, Sec. 4.2); that distance to
+ * an ellipse / ellipsoid is replaced by a lower bound, component by
+ * component.  With v = X - c and w = S v (S symmetric, lambda_max(S) = 1):
+ *   outer |x - c| <= R:  along y + s u, |S(y + s u) - c|^2 - R^2 <=
+ *     (rho^2 - R^2) + 2 s |w| + s^2, negative for s below the root
+ *     s_out = (R^2 - rho^2) / (|w| + sqrt(|w|^2 + R^2 - rho^2));
+ *   hole |x - c_h| >= r:  |S(y + s u) - c_h|^2 - r^2 >= F - 2 s |w| +
+ *     s^2 mu^2 (F = rho^2 - r^2, mu = lambda_min(S)), positive below the
+ *     smaller root s_h = F / (|w| + sqrt(|w|^2 - mu^2 F)); also
+ *     dist_y >= dist_x = rho - r (y -> S y does not expand distances), so
+ *     the hole gives max(s_h, rho - r).
+ * Both bounds equal the distance to first order at the boundary, and with
+ * S = I they are R - rho and rho - r exactly; s_out >= R - rho because
+ * |w| <= rho.  The radius is the smallest bound (<= 0 outside D).  The walk
+ * stops when it is <= eps, and then dist_x <= eps. */
+double orc_quadric_radius(const orc_instance *I, const double *x)
+{
+    const orc_domain *D = &I->dom;
+    const int d = D->dim;
+    double v[3] = {0.0, 0.0, 0.0}, rho2 = 0.0, w2 = 0.0;
+    for (int a = 0; a < d; ++a) {
+        v[a] = x[a] - D->center[a];
+        rho2 += v[a] * v[a];
+    }
+    for (int a = 0; a < d; ++a) {
+        double wa = 0.0;
+        for (int b = 0; b < d; ++b)
+            wa += I->S[a * d + b] * v[b];
+        w2 += wa * wa;
+    }
+    const double F0 = D->radius * D->radius - rho2;
+    if (F0 <= 0.0)
+        return 0.0;
+    double r = F0 / (sqrt(w2) + sqrt(w2 + F0));
+    for (int h = 0; h < D->n_holes; ++h) {
+        rho2 = 0.0;
+        w2 = 0.0;
+        for (int a = 0; a < d; ++a) {
+            v[a] = x[a] - D->hole_center[h][a];
+            rho2 += v[a] * v[a];
+        }
+        for (int a = 0; a < d; ++a) {
+            double wa = 0.0;
+            for (int b = 0; b < d; ++b)
+                wa += I->S[a * d + b] * v[b];
+            w2 += wa * wa;
+        }
+        const double rh = D->hole_radius[h];
+        const double F = rho2 - rh * rh;
+        if (F <= 0.0)
+            return 0.0;
+        double sh = F / (sqrt(w2) + sqrt(fmax(0.0, w2 - I->mu2 * F)));
+        sh = fmax(sh, sqrt(rho2) - rh);
+        r = fmin(r, sh);
+    }
+    return r;
+}
+
 int orc_walk(const orc_instance *I, const double *x0, uint64_t walk,
              double *x_exit, uint32_t *nsteps)
 {
-    if (I->mapped)
+    if (I->mapped == 1)
         return orc_walk_mapped(I, x0, walk, x_exit, nsteps);
     const int d = I->dom.dim;
     const int wpu = I->words_per_uniform;
@@ -451,7 +512,7 @@ int orc_walk(const orc_instance *I, const double *x0, uint64_t walk,
     double X[3] = {x0[0], x0[1], d == 3 ? x0[2] : 0.0};
     uint32_t words[4] = {0, 0, 0, 0};
     for (uint32_t n = 0;; ++n) {
-        double r = orc_dist(&I->dom, X);
+        double r = I->mapped == 2 ? orc_quadric_radius(I, X) : orc_dist(&I->dom, X);
         if (r <= I->eps || n >= I->step_cap) {
             for (int a = 0; a < d; ++a)
                 x_exit[a] = X[a];

@@ -55,13 +55,18 @@ typedef struct {
     uint32_t step_cap;  /* walks reaching it are left unterminated */
     int32_t words_per_uniform; /* 1: 23-bit, 2: 53-bit uniforms */
     /* mapped = 1: walk-on-spheres in y = S^{-1} x, whose domain S^{-1} D is a
-     * convex polytope: dist_y(y) = min_f (plane_d[f] - plane_n[f] . y) */
+     * convex polytope: dist_y(y) = min_f (plane_d[f] - plane_n[f] . y);
+     * mapped = 2: D a disc / ball minus disc / ball holes; the chain moves by
+     * the radius of orc_quadric_radius (a lower bound of dist_y) */
     int32_t mapped;
     int32_t n_planes;
     double plane_n[ORC_MAX_PLANES][3];
     double plane_d[ORC_MAX_PLANES];
     double Sinv[9];     /* row-major d x d */
+    double mu2;         /* lambda_min(S)^2 (mapped = 2) */
 } orc_instance;
+
+double orc_quadric_radius(const orc_instance *I, const double *x);
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
                        uint32_t out[4]);
