@@ -29,6 +29,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -1022,6 +1023,74 @@ def run_svd(args, rank: int, world: int, dist):
     }))
 
 
+def run_chains(args, rank: int, world: int, dist):
+    """The paper's eps and the mapped chains, measured (operator builds
+    only, median of 3 timed builds after one warm-up, L2 flushed before each):
+    * Ex. 5.4 (perforated disc) and Ex. 5.2 (annulus, extrinsic Voronoi
+      cells) at the paper's N = 1e6 and eps = 1e-10 with FP64 walks: ms per
+      build, walks/s, steps per walk and the averaged measure of Gamma_1
+      (printed 0.1126 for Ex. 5.4; ln 0.95 / ln 0.5 = 0.0740 for Ex. 5.2);
+    * the benchmark instances with the paper's chain and with the mapped
+      chain (wos_opts.mapped: exact distance in y = S^{-1} x for the square
+      and the cube, the quadric lower bound for the annulus and the balls),
+      FP32: ms per build and steps per walk."""
+    import torch
+    from paper_2409_03686_gb300 import build as B
+    from paper_2409_03686_gb300 import workloads as W
+    from paper_2409_03686_gb300 import wos
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    ctx = wos.Context(local)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed_build(inst, mapped=False):
+        pts = torch.as_tensor(inst.points, dtype=torch.float64, device=dev)
+        opts = wos.make_opts(precision=int(inst.fp64), stream_id=inst.stream, mapped=mapped)
+        ms, st, c = [], None, None
+        for it in range(4):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c, _, st = wos.wos_build_operator(ctx, inst.domain, inst.K, pts, inst.partition,
+                                              inst.N, inst.eps, inst.seed, opts=opts)
+            e1.record()
+            torch.cuda.synchronize()
+            if it:
+                ms.append(e0.elapsed_time(e1))
+        walks = inst.M_D * inst.N
+        m = float(np.median(ms))
+        return {"ms_per_build": m, "walks_per_s": walks / (m / 1e3),
+                "steps_per_walk": st["steps"] / walks, "unterminated": st["unterminated"]}, c
+
+    out = {}
+    for name, inst, ref in (
+            ("ex5.4 perforated disc, FP64, eps=1e-10, N=1e6",
+             W.perforated_disc_config(), 0.1126),
+            ("ex5.2 annulus (Voronoi cells), FP64, eps=1e-10, N=1e6",
+             W.annulus_voronoi_config(), math.log(0.95) / math.log(0.5))):
+        r, c = timed_build(inst)
+        g1 = torch.as_tensor(inst.partition.gamma1.astype(bool), device=dev)
+        r["avg_mu_gamma1"] = float((c[:, g1].sum(1).double() / inst.N).mean())
+        r["reference_value"] = ref
+        out[name] = r
+    cmp = {}
+    insts = [W.square_config(), W.annulus_config()] + W.config3_instances()
+    for inst in insts:
+        a, _ = timed_build(inst)
+        b, _ = timed_build(inst, mapped=True)
+        cmp[inst.name + ("-randK" if inst.dim == 3 and inst.K[0, 1] != 0 else "")] = {
+            "paper_chain": a, "mapped_chain": b,
+            "speedup": a["ms_per_build"] / b["ms_per_build"]}
+    if rank == 0:
+        print(json.dumps({"metric": "operator build ms (paper eps; mapped chains)",
+                          "value": out, "mapped_vs_paper_chain": cmp, "unit": "ms",
+                          "higher_is_better": False, "n_gpus": world,
+                          "data": "synthetic"}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1031,7 +1100,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="config3",
                     help="config3 (default), square-annulus, small, config3-small, "
-                         "batch, serve, svd")
+                         "batch, serve, svd, chains")
     ap.add_argument("--no-extras", action="store_true",
                     help="config3 without the served-latency and batching measurements")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -1069,6 +1138,8 @@ def main():
         run_serve(args, rank, world, dist)
     elif args.workload == "svd":
         run_svd(args, rank, world, dist)
+    elif args.workload == "chains":
+        run_chains(args, rank, world, dist)
     else:
         run_gpu(args, rank, world, dist)
     if dist is not None:

@@ -48,12 +48,15 @@ namespace wos {
 // a disc / ball with one concentric hole (annulus, spherical shell: both
 // boundary distances come from one radius); mapped walks (walk-on-spheres in
 // y = S^{-1} x, the domain a convex polytope given by its faces); a box with
-// equal half-extents (square, cube: h - max |x_a|).
+// equal half-extents (square, cube: h - max |x_a|); mapped walks on a disc /
+// ball minus holes (steps of the largest ellipsoid X + rho S B inside D, rho
+// a quadric lower bound of the distance in y), the general form and the one
+// with a single concentric hole.
 enum KernelKind : int {
     kGeneric = 0, kSphereOnly = 1, kBoxOnly = 2, kSphereHoles = 3, kAnnulus = 4,
-    kMapped = 5, kCubeOnly = 6
+    kMapped = 5, kCubeOnly = 6, kQuadric = 7, kQuadricConc = 8
 };
-constexpr int kNumKinds = 7;
+constexpr int kNumKinds = 9;
 
 // One instance of the operator build.
 template <typename Real> struct WalkInst {
@@ -160,6 +163,64 @@ __device__ __forceinline__ Real walk_dist(const Geom<Real> &g, const Real *x)
         }
         return r;
     }
+    if (KIND == kQuadric || KIND == kQuadricConc) {
+        // Mapped chain on a disc / ball minus holes.  The largest rho with
+        // X + rho S B(0, 1) inside D is the distance in y = S^{-1} x to the
+        // mapped boundary (ellipses / ellipsoids); per component a lower
+        // bound from a quadratic majorant of |S y - c|^2 - R^2 along a ray
+        // (v = x - c, w = S v, lambda_max(S) = 1):
+        //   outer:  (R^2 - |v|^2) / (|w| + sqrt(|w|^2 + R^2 - |v|^2)),
+        //   hole:   max(F / (|w| + sqrt(|w|^2 - mu^2 F)), |v| - r),
+        //           F = |v|^2 - r^2, mu = lambda_min(S);
+        // both first-order exact at the boundary and >= the Euclidean
+        // distance, <= 0 outside D (the walk then stops).  R^2 - |v|^2 is
+        // formed as (R - |v|)(R + |v|), which keeps its digits near dD.
+        Real v[DIM], rho2 = Real(0), w2 = Real(0);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            v[a] = x[a] - g.c[a];
+            rho2 = fma(v[a], v[a], rho2);
+        }
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            Real wa = g.mS[a * DIM] * v[0];
+#pragma unroll
+            for (int b = 1; b < DIM; ++b)
+                wa = fma(g.mS[a * DIM + b], v[b], wa);
+            w2 = fma(wa, wa, w2);
+        }
+        const Real rho = w_sqrt(rho2), wn = w_sqrt(w2);
+        const Real F0 = (g.R - rho) * (g.R + rho);
+        Real r = w_div(F0, wn + w_sqrt(w_max(Real(0), w2 + F0)));
+        if (KIND == kQuadricConc) {  // one hole of the same centre: v, w shared
+            const Real r1 = g.hr[0];
+            const Real F = (rho - r1) * (rho + r1);
+            const Real sh = w_div(F, wn + w_sqrt(w_max(Real(0), fma(-g.qmu2, F, w2))));
+            r = w_min(r, w_max(sh, rho - r1));
+        } else {
+            for (int h = 0; h < g.n_holes; ++h) {
+                Real p2 = Real(0), q2 = Real(0), u[DIM];
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
+                    u[a] = x[a] - g.hc[h][a];
+                    p2 = fma(u[a], u[a], p2);
+                }
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) {
+                    Real wa = g.mS[a * DIM] * u[0];
+#pragma unroll
+                    for (int b = 1; b < DIM; ++b)
+                        wa = fma(g.mS[a * DIM + b], u[b], wa);
+                    q2 = fma(wa, wa, q2);
+                }
+                const Real p = w_sqrt(p2), r1 = g.hr[h];
+                const Real F = (p - r1) * (p + r1);
+                const Real sh = w_div(F, w_sqrt(q2) + w_sqrt(w_max(Real(0), fma(-g.qmu2, F, q2))));
+                r = w_min(r, w_max(sh, p - r1));
+            }
+        }
+        return r;
+    }
     if (KIND == kAnnulus) {  // |x - c| once; both boundary distances from it
         Real s = Real(0);
 #pragma unroll
@@ -181,6 +242,8 @@ __device__ __forceinline__ int32_t walk_classify(const Geom<Real> &g, const Real
     if (KIND == kBoxOnly || KIND == kCubeOnly)
         return outer_box_cell<Real, DIM>(g, x);
     if (KIND == kSphereHoles || KIND == kAnnulus)
+        return sphere_holes_cell<Real, DIM>(g, x);
+    if ((KIND == kQuadric || KIND == kQuadricConc) && g.vn == 0)
         return sphere_holes_cell<Real, DIM>(g, x);
     if (KIND == kMapped && g.vn == 0 && g.n_holes == 0 && g.outer_kind == kBox)
         return outer_box_cell<Real, DIM>(g, x);

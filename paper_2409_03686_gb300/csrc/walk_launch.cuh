@@ -39,6 +39,8 @@ const void *pick_walk_kernel(int kind)
     if (kind == kAnnulus) return walk_kernel_ptr<Real, DIM, kAnnulus, MULTI>();
     if (kind == kMapped) return walk_kernel_ptr<Real, DIM, kMapped, MULTI>();
     if (kind == kCubeOnly) return walk_kernel_ptr<Real, DIM, kCubeOnly, MULTI>();
+    if (kind == kQuadric) return walk_kernel_ptr<Real, DIM, kQuadric, MULTI>();
+    if (kind == kQuadricConc) return walk_kernel_ptr<Real, DIM, kQuadricConc, MULTI>();
     return walk_kernel_ptr<Real, DIM, kGeneric, MULTI>();
 }
 
@@ -47,6 +49,12 @@ const void *pick_walk_kernel(int kind)
 // disc / ball with one hole of the same centre.
 inline int walk_kind(const wos_domain &d, const wos_partition &part, bool mapped = false)
 {
+    if (mapped && d.outer_kind == WOS_OUTER_SPHERE) {
+        bool concentric = d.n_holes == 1;
+        for (int a = 0; a < d.dim; ++a)
+            concentric = concentric && d.hole_center[0][a] == d.center[a];
+        return concentric ? kQuadricConc : kQuadric;
+    }
     if (mapped)
         return kMapped;
     if (part.voronoi_n <= 0 && d.outer_kind == WOS_OUTER_SPHERE) {
@@ -78,7 +86,9 @@ void fill_inst(const wos_domain &d, const wos_partition &part, const double *S,
     fill_geom(d, part, I->g);
     for (int i = 0; i < 9; ++i)
         I->S[i] = i < d.dim * d.dim ? Real(S[i]) : Real(0);
-    if (mapped) {  // isotropic steps in y = S^{-1} x
+    if (mapped && d.outer_kind == WOS_OUTER_SPHERE) {
+        set_quadric(d, S, I->g);  // the paper's moves X + rho S U, larger rho
+    } else if (mapped) {  // isotropic steps in y = S^{-1} x
         set_mapped(d, S, I->g);
         for (int i = 0; i < 9; ++i)
             I->S[i] = (i < d.dim * d.dim && i % (d.dim + 1) == 0) ? Real(1) : Real(0);

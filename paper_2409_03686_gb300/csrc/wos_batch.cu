@@ -226,9 +226,10 @@ extern "C" wos_status wos_build_operators_batched(wos_context *ctx, int32_t n,
             return st;
         if (o.mapped != 0 && (o.mapped != 1 || !mapped_supported(*pb.domain)))
             return WOS_INVALID_ARG;
+        const bool in_y = o.mapped && pb.domain->outer_kind != WOS_OUTER_SPHERE;
         if (o.precision == WOS_FP32 &&
-            pb.eps < (o.mapped ? fp32_floor_mapped(*pb.domain, S[q].data())
-                               : fp32_floor(*pb.domain)))
+            pb.eps < (in_y ? fp32_floor_mapped(*pb.domain, S[q].data())
+                           : fp32_floor(*pb.domain)))
             return WOS_EPS_BELOW_FP32_FLOOR;
         by_class[pb.domain->dim - 2][walk_kind(*pb.domain, *pb.partition, o.mapped != 0)]
             .push_back(q);

@@ -50,6 +50,17 @@ WOS_HD float w_sqrt(float x)
 #endif
 }
 WOS_HD double w_sqrt(double x) { return sqrt(x); }
+// Division: FP32 from the SFU reciprocal (__fdividef, 2 ulp for divisors of
+// normal size), FP64 IEEE.
+WOS_HD float w_div(float a, float b)
+{
+#ifdef __CUDA_ARCH__
+    return __fdividef(a, b);
+#else
+    return a / b;
+#endif
+}
+WOS_HD double w_div(double a, double b) { return a / b; }
 WOS_HD float w_floor(float x) { return floorf(x); }
 WOS_HD double w_floor(double x) { return floor(x); }
 WOS_HD float w_atan2(float y, float x) { return atan2f(y, x); }
@@ -112,6 +123,7 @@ template <typename Real> struct Geom {
     int32_t np;
     Real pn[kMaxPlanes][3], pd[kMaxPlanes];
     Real mS[9], mSinv[9];    // S and S^{-1}, row-major DIM x DIM
+    Real qmu2;               // mapped disc / ball: lambda_min(S)^2
 };
 
 // Index of the cell of t in [0, 1) split into m equal cells (clamped).

@@ -32,6 +32,10 @@ bool mapped_supported(const wos_domain &d);
 template <typename Real>
 void set_mapped(const wos_domain &d, const double *S, Geom<Real> &g);
 double fp32_floor_mapped(const wos_domain &d, const double *S);
+// Mapped walks on a disc / ball minus holes: S and lambda_min(S)^2 for the
+// quadric bound of the step radius (walk_dist, kQuadric kinds).
+template <typename Real>
+void set_quadric(const wos_domain &d, const double *S, Geom<Real> &g);
 
 // Argument checks of an operator build (wos_build_operator and its
 // no-allocation variant): *o = opts (or zeros), S = (K / lambda_max)^{1/2};

@@ -64,8 +64,44 @@ def test_mapped_chain_takes_fewer_steps():
 
 
 def test_unsupported_domains_are_rejected():
-    for inst in (W.annulus_config(N=100, grid=2), W.lshape_config(N=100, n_points=4),
+    """Polygons must be convex and polytopes hole-free (discs / balls minus
+    holes take the quadric bound instead, tested below)."""
+    for inst in (W.lshape_config(N=100, n_points=4),
                  W.square_hole_config(N=100, eps=1e-5, n_points=4, fp64=False)):
         with pytest.raises(wos.WosError) as e:
             gpu_build(inst.replace(mapped=True), trace=False)
         assert e.value.code == 1
+
+
+# ---------------------------------------------------------------------------
+# Mapped walks on discs / balls minus holes (the quadric lower bound of the
+# distance in y = S^{-1} x as the radius of the paper's ellipsoid steps)
+# ---------------------------------------------------------------------------
+QUADRIC = {
+    "annulus": lambda: W.annulus_config(N=600, grid=8),
+    "ball_diag": lambda: W.ball_config(N=500, n_points=40),
+    "ball_rand": lambda: W.config3_instances(N=500, n_points=40)[1],
+    "shell_shifted": lambda: W.shell_config(N=500, shift=0.3, n_points=40,
+                                            K=W.config3_instances(N=1, n_points=1)[1].K),
+    "perforated": lambda: W.perforated_disc_config(N=600, eps=1e-5, fp64=False, n_points=40,
+                                                   m_outer=100, m_hole=20).replace(
+                                                       K=W.K_CONFIG2),
+    "ball_fp64": lambda: W.ball_config(N=300, n_points=20).replace(fp64=True, eps=1e-8),
+}
+
+
+@pytest.mark.parametrize("name", list(QUADRIC))
+def test_quadric_mapped_walks_match_oracle(name):
+    """Walk by walk against the oracle's mapped chain (the same bound in
+    FP64): >= 99.9 % of exit elements equal; counts differ by at most the
+    disagreeing walks; far fewer steps than the paper's chain."""
+    inst = QUADRIC[name]().replace(mapped=True)
+    r = gpu_build(inst, trace_steps=True)
+    tr = r["trace"]
+    assert (tr >= -1).all()
+    assert (r["counts"].sum(1) + r["unterm"] == inst.N).all()
+    el, ns, _ = oracle_walks(inst)
+    agree = (tr == el).mean()
+    assert agree >= 0.999, (name, agree)
+    plain = gpu_build(inst.replace(mapped=False), trace=False)
+    assert r["stats"]["steps"] < 0.8 * plain["stats"]["steps"], name

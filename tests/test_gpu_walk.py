@@ -304,3 +304,54 @@ def test_errors_are_reported():
     with pytest.raises(wos.WosError) as e:
         gpu_build(inst, trace=False, k0=5, k1=3)
     assert e.value.code == 1
+
+
+def _golden(key):
+    from pathlib import Path
+    for line in open(Path(__file__).resolve().parent / "golden" / "paper_printed_values.txt"):
+        if line.strip() and not line.startswith("#"):
+            k, v, _ = line.split()
+            if k == key:
+                return float(v)
+    raise KeyError(key)
+
+
+def test_paper_eps_perforated_disc_fp64():
+    """Ex. 5.4 at the paper's eps = 1e-10 with FP64 walks (500 + 5 x 100
+    arcs, 100 points on the circle at distance 0.05 from Gamma_0): the
+    averaged harmonic measure of Gamma_1 lies within the printed 0.1126 +-
+    0.002 (Sec. 1), and the first 2000 walks of three rows are replayed walk
+    by walk by the oracle at the same eps."""
+    inst = W.perforated_disc_config(N=20_000, eps=1e-10)
+    r = gpu_build(inst, trace=False)
+    assert (r["counts"].sum(1) + r["unterm"] == inst.N).all()
+    assert r["unterm"].sum() == 0
+    g1 = inst.partition.gamma1.astype(bool)
+    avg = (r["counts"][:, g1].sum(1) / inst.N).mean()
+    assert abs(avg - _golden("avg_mu_gamma1_on_dotted_circle")) < 2e-3, avg
+    part = gpu_build(inst, k0=0, k1=2000, trace_steps=True)
+    rows = [0, 37, 99]
+    el, ns, _ = oracle_walks(inst, rows=rows, k0=0, k1=2000)
+    agree = (part["trace"][rows] == el).mean()
+    assert agree >= 0.999, agree
+    assert (part["steps"][rows] == ns).mean() >= 0.999
+
+
+def test_paper_eps_annulus_fp64():
+    """Ex. 5.2's annulus (K = I, extrinsic Voronoi cells of 500 + 100 equally
+    spaced sites) at eps = 1e-10 with FP64 walks: the measure of the inner
+    circle averaged over the 100 points at radius 0.95 against ln r / ln a =
+    0.0740005814 (4 sigma + beta(eps)), and three rows walk by walk against
+    the oracle."""
+    inst = W.annulus_voronoi_config(N=20_000, eps=1e-10)
+    r = gpu_build(inst, trace=False)
+    assert (r["counts"].sum(1) + r["unterm"] == inst.N).all()
+    g1 = inst.partition.gamma1.astype(bool)
+    mu = r["counts"][:, g1].sum(1) / inst.N
+    p = math.log(0.95) / math.log(0.5)
+    sd = math.sqrt(p * (1 - p) / (inst.N * inst.M_D))
+    assert abs(mu.mean() - p) <= 4 * sd + 1e-9, (mu.mean(), p, sd)
+    part = gpu_build(inst, k0=0, k1=2000)
+    rows = [0, 50, 99]
+    el, _, _ = oracle_walks(inst, rows=rows, k0=0, k1=2000)
+    assert (part["trace"][rows] == el).mean() >= 0.999
