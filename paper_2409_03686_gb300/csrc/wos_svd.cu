@@ -526,8 +526,10 @@ jacobi_kernel(const SvdWork *works, const int *begin, int np)
     jacobi_body<RPT>(w, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
 }
 
+// At most 48 registers a thread (ten 128-thread CTAs per SM): the 384 pairs
+// of each of four 768-column problems run a CTA each, none serialised.
 template <int RPT>
-__global__ void __launch_bounds__(kPairThreads)
+__global__ void __launch_bounds__(kPairThreads, 10)
 jacobi_lean_kernel(const SvdWork *works, const int *begin, int np)
 {
     const int p = problem_of(begin, np);
