@@ -294,8 +294,12 @@ def qr_flop(m: int, n: int) -> int:
 def jacobi_flop(m: int, n: int, sweeps: int) -> int:
     """FP64 flop of the Jacobi sweeps of one SVD of an m x n worked matrix
     (m >= n) as the library runs it (on X = R^T, n x n, when n >= 32): every
-    pair visit counted as rotated (dots 6l, column updates 6l + 6n)."""
+    pair visit counted as rotated.  Up to 256 columns the sweeps accumulate V
+    (three dot products 6l, column updates 6l + 6n); above, they do not and
+    carry the norms (one dot product 2l, column updates 6l)."""
     rows = n if n >= 32 else m
+    if n > 256:
+        return sweeps * (n * (n - 1) // 2) * (8 * rows)
     return sweeps * (n * (n - 1) // 2) * (12 * rows + 6 * n)
 
 
@@ -551,6 +555,10 @@ def run_gpu(args, rank: int, world: int, dist):
     svd_achieved = flop / (jac_ms / 1e3) / 1e9
     svd_roof = {"kernel": ("svd_cluster_kernel" if args.svd_path == "auto" and
                            all(p["svd_mn"][1] <= 256 for p in prep)
+                           else ("qrcp_kernel + jacobi_group_kernel"
+                                 if sum(p["svd_mn"][1] for p in prep) > 2 * 3 * 152
+                                 else "qrcp_kernel + jacobi_lean_kernel")
+                           if all(p["svd_mn"][1] > 256 for p in prep)
                            else "qrcp_kernel + jacobi_kernel"),
                 "bound": "alu", "pipe": "fp64", "achieved": svd_achieved,
                 "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
@@ -559,8 +567,9 @@ def run_gpu(args, rank: int, world: int, dist):
                                "per chip) x 2 flop x 2070 MHz",
                 "unit_of_work": "one factorisation: the pivoted Householder QR (2mn^2 - "
                                 "2n^3/3 flop, n >= 32) and every pair visit of every sweep "
-                                "(12 l + 6n flop, l = rows of the matrix Jacobi works on: n "
-                                "after the QR, m without; every visit counted as rotated)",
+                                "(12 l + 6n flop with V accumulated, n <= 256; 8 l without, "
+                                "n > 256; l = rows of the matrix Jacobi works on: n after the "
+                                "QR, m without; every visit counted as rotated)",
                 "sweeps": [p["sweeps"] for p in prep],
                 "problems_per_launch": len(prep),
                 "ms_per_step": jac_ms,

@@ -198,10 +198,211 @@ __device__ __forceinline__ void jacobi_rotation_t(double al, double be, double g
 // |x_q|^2 + t g (g = x_p . x_q, t = s / c); a norm whose identity cancelled
 // more than 63/64 of its terms is recomputed from the rotated column in the
 // same pass (the final singular values are recomputed exactly anyway).
-// Rounds, flags, stopping rule and the order of the pairs are those of
-// jacobi_body.
+//
+// A CTA of four warps takes four pairs of a round, a warp per pair with the
+// pair's two columns in its registers (RPL rows a lane, the rest streamed),
+// and one warp forms the four rotations at once (lane k for pair k): an FP64
+// warp instruction holds its sub-partition's FP64 unit for 64 cycles
+// whatever its active lanes, so the scalar chain of a rotation is shared by
+// four pairs, and a pair's reduction is one warp's.  Rounds, flags, stopping
+// rule and the order of the pairs are those of jacobi_body.
 constexpr double kRecompute = 1.0 / 64.0;
+constexpr int kGroupPairs = 4;             // pairs (warps) per CTA
+constexpr int kGroupThreads = 32 * kGroupPairs;
 
+template <int RPL>
+__device__ void jacobi_group_body(const SvdWork &w, const int bid, const int nblk)
+{
+    __shared__ double gk[kGroupPairs];       // x_p . x_q of each pair
+    __shared__ double prm[kGroupPairs][2];   // c, s
+    __shared__ int flg[kGroupPairs];         // 1 rotate, 2 / 4 recompute |x_p|^2 / |x_q|^2
+    __shared__ int s_rot, s_big;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int half = w.n_pad / 2;
+    const int groups = (half + kGroupPairs - 1) / kGroupPairs;
+    const int m = w.m, n = w.n;
+    unsigned *status = w.bar + 5;
+    unsigned long long *maxcos = reinterpret_cast<unsigned long long *>(w.bar + 8);
+    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+        unsigned *rot = w.bar + 2 + (sweep % 3);
+        if (bid == 0 && tid == 0) {
+            w.bar[2 + ((sweep + 1) % 3)] = 0u;
+            maxcos[(sweep + 1) % 3] = 0ull;
+        }
+        if (tid == 0) {
+            s_rot = 0;
+            s_big = 0;
+        }
+        bool my_big = false;
+        int my_rot = 0;
+        for (int r = 0; r < w.n_pad - 1; ++r) {
+            const unsigned R = unsigned(sweep) * unsigned(w.n_pad - 1) + unsigned(r);
+            for (int gi = bid; gi < groups; gi += nblk) {
+                const int pr = gi * kGroupPairs + wid;  // this warp's pair
+                int p = n, q = n;                       // none past the last pair
+                if (pr < half) {
+                    const int a = rr_player(pr, r, w.n_pad);
+                    const int b = rr_player(w.n_pad - 1 - pr, r, w.n_pad);
+                    p = min(a, b);
+                    q = max(a, b);
+                }
+                const bool live = pr < half && q < n;   // a real pair (not the dummy)
+                bool ok = true;
+                if (pr < half && lane == 0)
+                    ok = wait_version(w.ver, p, R, status);
+                else if (live && lane == 1)
+                    ok = wait_version(w.ver, q, R, status);
+                if (!__syncthreads_and(ok))
+                    return;
+                double xr[RPL], yr[RPL];
+                double *wp = w.W + size_t(live ? p : 0) * m, *wq = w.W + size_t(live ? q : 0) * m;
+                double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
+                if (live) {
+#pragma unroll
+                    for (int k = 0; k < RPL; ++k) {
+                        const int i = lane + 32 * k;
+                        xr[k] = i < m ? __ldcg(wp + i) : 0.0;
+                        yr[k] = i < m ? __ldcg(wq + i) : 0.0;
+                    }
+#pragma unroll
+                    for (int k = 0; k < RPL; k += 4) {  // four chains: DFMA latency
+                        g0 = fma(xr[k], yr[k], g0);
+                        if (k + 1 < RPL) g1 = fma(xr[k + 1], yr[k + 1], g1);
+                        if (k + 2 < RPL) g2 = fma(xr[k + 2], yr[k + 2], g2);
+                        if (k + 3 < RPL) g3 = fma(xr[k + 3], yr[k + 3], g3);
+                    }
+                    for (int i = lane + 32 * RPL; i < m; i += 32)
+                        g0 = fma(__ldcg(wp + i), __ldcg(wq + i), g0);
+                    const double g = warp_sum((g0 + g1) + (g2 + g3));
+                    if (lane == 0)
+                        gk[wid] = g;
+                }
+                __syncthreads();
+                // warp 0 forms the rotations of the CTA's pairs, lane k for pair k
+                if (wid == 0 && lane < kGroupPairs) {
+                    const int prk = gi * kGroupPairs + lane;
+                    int f = 0;
+                    double c = 1.0, sn = 0.0;
+                    if (prk < half) {
+                        const int a = rr_player(prk, r, w.n_pad);
+                        const int b = rr_player(w.n_pad - 1 - prk, r, w.n_pad);
+                        const int pk = min(a, b), qk = max(a, b);
+                        if (qk < n) {
+                            const double g = gk[lane];
+                            const double al = __ldcg(w.nrm + pk), be = __ldcg(w.nrm + qk);
+                            const double ab = al * be, gg = g * g;
+                            if (al != 0.0 && be != 0.0 && gg > (kTol * kTol) * ab) {
+                                double t;
+                                jacobi_rotation_t(al, be, g, c, sn, t);
+                                f = 1;
+                                my_big = my_big || gg > (kLast * kLast) * ab;
+                                ++my_rot;
+                                const double tg = t * g;
+                                const double an = al - tg, bn = be + tg;
+                                const double scale = al + be + fabs(tg);
+                                if (!(an > kRecompute * scale))
+                                    f |= 2;
+                                else
+                                    w.nrm[pk] = an;
+                                if (!(bn > kRecompute * scale))
+                                    f |= 4;
+                                else
+                                    w.nrm[qk] = bn;
+                            }
+                        }
+                    }
+                    prm[lane][0] = c;
+                    prm[lane][1] = sn;
+                    flg[lane] = f;
+                }
+                __syncthreads();
+                const int f = flg[wid];
+                if (live && (f & 1)) {
+                    const double c = prm[wid][0], sn = prm[wid][1];
+                    double np2 = 0.0, nq2 = 0.0;
+#pragma unroll
+                    for (int k = 0; k < RPL; ++k) {
+                        const int i = lane + 32 * k;
+                        const double x = c * xr[k] - sn * yr[k];
+                        const double y = sn * xr[k] + c * yr[k];
+                        if (i < m) {
+                            __stcg(wp + i, x);
+                            __stcg(wq + i, y);
+                            if (f & 2)
+                                np2 = fma(x, x, np2);
+                            if (f & 4)
+                                nq2 = fma(y, y, nq2);
+                        }
+                    }
+                    for (int i = lane + 32 * RPL; i < m; i += 32) {
+                        const double x0 = __ldcg(wp + i), y0 = __ldcg(wq + i);
+                        const double x = c * x0 - sn * y0, y = sn * x0 + c * y0;
+                        __stcg(wp + i, x);
+                        __stcg(wq + i, y);
+                        if (f & 2)
+                            np2 = fma(x, x, np2);
+                        if (f & 4)
+                            nq2 = fma(y, y, nq2);
+                    }
+                    if (f & 2) {  // warp-uniform
+                        np2 = warp_sum(np2);
+                        if (lane == 0)
+                            w.nrm[p] = np2;
+                    }
+                    if (f & 4) {
+                        nq2 = warp_sum(nq2);
+                        if (lane == 0)
+                            w.nrm[q] = nq2;
+                    }
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    // the CTA's stores are ordered before the flags by the
+                    // barrier above and this fence (a release pattern)
+                    __threadfence();
+                    for (int k = 0; k < kGroupPairs; ++k) {
+                        const int prk = gi * kGroupPairs + k;
+                        if (prk >= half)
+                            break;
+                        const int a = rr_player(prk, r, w.n_pad);
+                        const int b = rr_player(w.n_pad - 1 - prk, r, w.n_pad);
+                        st_relaxed(w.ver + min(a, b), R + 1u);
+                        if (max(a, b) < n)
+                            st_relaxed(w.ver + max(a, b), R + 1u);
+                    }
+                }
+            }
+        }
+        if (wid == 0 && lane < kGroupPairs) {
+            if (my_rot)
+                atomicAdd(&s_rot, my_rot);
+            if (my_big)
+                atomicOr(&s_big, 1);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            if (s_rot)
+                atomicAdd(rot, unsigned(s_rot));
+            if (s_big)
+                atomicMax(maxcos + (sweep % 3), 1ull);
+        }
+        if (!grid_barrier(w.bar, unsigned(nblk)))
+            return;
+        const unsigned long long big = *(volatile unsigned long long *)(maxcos + (sweep % 3));
+        bool done = *(volatile unsigned *)rot == 0u || big == 0ull;
+        if (bid == 0 && tid == 0)
+            w.bar[6] = unsigned(sweep + 1);
+        if (done)
+            return;
+    }
+    if (bid == 0 && tid == 0)
+        atomicExch(w.bar + 5, unsigned(WOS_NO_CONVERGENCE));
+}
+
+// The same sweeps with a CTA of kPairThreads threads per pair (its rows
+// split over four warps): the shorter critical path of a round when the
+// batch has too few pairs to fill the GPU (a lone problem), where the
+// grouped kernel's one-warp pairs would leave FP64 units idle.
 template <int RPT>
 __device__ void jacobi_lean_body(const SvdWork &w, const int bid, const int nblk)
 {
@@ -535,6 +736,15 @@ jacobi_lean_kernel(const SvdWork *works, const int *begin, int np)
     const int p = problem_of(begin, np);
     const SvdWork w = works[p];
     jacobi_lean_body<RPT>(w, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
+}
+
+template <int RPL>
+__global__ void __launch_bounds__(kGroupThreads, 3)
+jacobi_group_kernel(const SvdWork *works, const int *begin, int np)
+{
+    const int p = problem_of(begin, np);
+    const SvdWork w = works[p];
+    jacobi_group_body<RPL>(w, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
 }
 
 // Squared norms of the n columns (length m) of w.W into w.nrm, a warp per
@@ -1224,6 +1434,24 @@ int rpt_of(int m)
     return need <= 6 ? (need < 1 ? 1 : need) : 8;
 }
 
+// Rows a lane keeps in registers in the lean sweeps (a column of m rows
+// over a warp; longer columns stream the rest).
+int rpl_of(int m)
+{
+    const int need = (m + 31) / 32;
+    return need <= 8 ? 8 : need <= 16 ? 16 : need <= 24 ? 24 : 32;
+}
+
+const void *jacobi_group_kernel_rpl(int rpl)
+{
+    switch (rpl) {
+    case 8: return reinterpret_cast<const void *>(&jacobi_group_kernel<8>);
+    case 16: return reinterpret_cast<const void *>(&jacobi_group_kernel<16>);
+    case 24: return reinterpret_cast<const void *>(&jacobi_group_kernel<24>);
+    default: return reinterpret_cast<const void *>(&jacobi_group_kernel<32>);
+    }
+}
+
 const void *jacobi_lean_kernel_rpt(int rpt)
 {
     switch (rpt) {
@@ -1527,32 +1755,52 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     // Jacobi: one cooperative launch per class of rows per thread (and per
     // group of co-resident problems); the CTAs are shared in proportion to
     // the pairs when the batch is larger than the GPU
-    for (int cls = 0; cls < 14; ++cls) {
+    // Without V: four pairs per CTA when the batch has pairs for more than
+    // three CTAs of one pair per SM (several large problems: the FP64 units
+    // bound the sweeps), else a CTA per pair (a lone problem: the round's
+    // critical path bounds them)
+    long long lean_pairs = 0;
+    for (int p = 0; p < np; ++p)
+        if (P[p].lean)
+            lean_pairs += P[p].wj.n_pad / 2;
+    const bool grouped = lean_pairs > 3LL * sms;
+    for (int cls = 0; cls < 18; ++cls) {
         if (e != cudaSuccess)
             break;
         static const int kRpts[7] = {1, 2, 3, 4, 5, 6, 8};
-        const int rpt = kRpts[cls % 7];
+        static const int kRpls[4] = {8, 16, 24, 32};
+        // classes: 0-6 with V (rows per thread), 7-10 grouped (rows per
+        // lane), 11-17 a CTA per pair without V (rows per thread)
         const bool lean = cls >= 7;
+        const bool group = cls >= 7 && cls < 11;
+        if (lean && group != grouped)
+            continue;
+        const int rpt = group ? kRpls[cls - 7] : kRpts[cls < 7 ? cls : cls - 11];
         std::vector<int> idx;
         for (int p = 0; p < np; ++p)
-            if (!P[p].cl && rpt_of(P[p].wj.m) == rpt && P[p].lean == lean)
+            if (!P[p].cl && P[p].lean == lean &&
+                (group ? rpl_of(P[p].wj.m) : rpt_of(P[p].wj.m)) == rpt)
                 idx.push_back(p);
         if (idx.empty())
             continue;
-        const void *jk = lean ? jacobi_lean_kernel_rpt(rpt) : jacobi_kernel_rpt(rpt);
+        const void *jk = group ? jacobi_group_kernel_rpl(rpt)
+                               : lean ? jacobi_lean_kernel_rpt(rpt) : jacobi_kernel_rpt(rpt);
+        const int threads = group ? kGroupThreads : kPairThreads;
         int bps = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, jk, kPairThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, jk, threads, 0);
         const int budget = std::max(1, bps) * sms;
         long long want = 0;
         for (int p : idx) {
-            jgrids[p] = std::min(P[p].wj.n_pad / 2, budget);  // a CTA per pair if they fit
+            // a CTA per pair (per four pairs without V) if they fit
+            const int half = P[p].wj.n_pad / 2;
+            jgrids[p] = std::min(group ? (half + kGroupPairs - 1) / kGroupPairs : half, budget);
             want += jgrids[p];
         }
         if (want > budget)
             for (int p : idx)
                 jgrids[p] = std::max(1, int(jgrids[p] * (long long)budget / want));
-        e = launch_groups(jk, kPairThreads, budget, idx, jgrids, jrecs, dj,
-                          dbegin + np + 1, st, &launches);
+        e = launch_groups(jk, threads, budget, idx, jgrids, jrecs, dj, dbegin + np + 1, st,
+                          &launches);
     }
     if (jacobi_events && jacobi_events[1])
         cudaEventRecord(static_cast<cudaEvent_t>(jacobi_events[1]), st);
