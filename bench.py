@@ -70,32 +70,48 @@ OPS_PER_STEP = {"box": 33, "annulus": 36, "ball": 72, "cube": 70}
 # sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained = 304 per
 # chip) x 2 flop x 2070 MHz, in GFLOP/s.
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.070
-PROFILE_NOTE = ROOT / "profiles" / "walk_kernel_square_annulus.md"
+PROFILES = ROOT / "profiles"
+CSRC = ROOT / "paper_2409_03686_gb300" / "csrc"
 
 
-def _walk_kernel_hash() -> str:
+def _source_hash(files) -> str:
     h = hashlib.sha256()
-    for f in ("walk_kernel.cuh", "wos_device.cuh"):
-        h.update((ROOT / "paper_2409_03686_gb300" / "csrc" / f).read_bytes())
+    for f in files:
+        h.update((CSRC / f).read_bytes())
     return h.hexdigest()[:16]
 
 
-def _traffic_from_profile():
-    """DRAM bytes per walk-kernel launch from the committed ncu summary, if it
-    was taken on the current kernel source."""
-    if not PROFILE_NOTE.exists():
+def _traffic_from_profile(note: str, hash_key: str, files, value_key: str):
+    """DRAM bytes from a committed ncu summary (profiles/<note>), if it was
+    taken on the current source of the kernel (its hash_key line equals the
+    SHA-256 prefix of `files`); else None."""
+    path = PROFILES / note
+    if not path.exists():
         return None
     vals = {}
-    for line in PROFILE_NOTE.read_text().splitlines():
+    for line in path.read_text().splitlines():
         if ":" in line and line.strip().startswith("- "):
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_hash") != _walk_kernel_hash():
+    if vals.get(hash_key) != _source_hash(files):
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals[value_key])
     except (KeyError, ValueError):
         return None
+
+
+def walk_traffic(dim: int):
+    """DRAM bytes per walk-kernel launch (the 2-D or 3-D capture)."""
+    note = "walk_kernel_ball_cube.md" if dim == 3 else "walk_kernel_square_annulus.md"
+    return _traffic_from_profile(note, "kernel_source_hash",
+                                 ("walk_kernel.cuh", "wos_device.cuh"), "dram_bytes_per_launch")
+
+
+def svd_traffic():
+    """DRAM bytes of the four 1024 x 768 factorisations of a 3-D step."""
+    return _traffic_from_profile("jacobi_svd_fp64.md", "svd_source_hash", ("wos_svd.cu",),
+                                 "dram_bytes_per_step")
 
 
 def workload(name: str):
@@ -531,7 +547,7 @@ def run_gpu(args, rank: int, world: int, dist):
         unions.append(tot)
     kernel_ms_step = float(np.mean(unions))
     achieved = ops / (kernel_ms_step / 1e3) / 1e9
-    traffic = _traffic_from_profile()
+    traffic = walk_traffic(prep[0]["inst"].dim)
     walk_roof = {"kernel": "walk_kernel", "bound": "alu", "achieved": achieved,
                  "peak": ALU_PEAK_GOPS, "unit": "Gop/s", "frac": achieved / ALU_PEAK_GOPS,
                  "traffic": traffic,
@@ -562,7 +578,8 @@ def run_gpu(args, rank: int, world: int, dist):
                            else "qrcp_kernel + jacobi_kernel"),
                 "bound": "alu", "pipe": "fp64", "achieved": svd_achieved,
                 "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": svd_achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                "frac": svd_achieved / FP64_PEAK_GFLOPS,
+                "traffic": svd_traffic() if args.workload == "config3" else None,
                 "peak_source": "152 SMs x 2 FP64 FMA/clk (ncu dfma peak_sustained 304 "
                                "per chip) x 2 flop x 2070 MHz",
                 "unit_of_work": "one factorisation: the pivoted Householder QR (2mn^2 - "
