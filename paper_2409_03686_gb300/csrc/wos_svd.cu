@@ -206,8 +206,26 @@ __device__ __forceinline__ void jacobi_rotation_t(double al, double be, double g
 // whatever its active lanes, so the scalar chain of a rotation is shared by
 // four pairs, and a pair's reduction is one warp's.  Rounds, flags, stopping
 // rule and the order of the pairs are those of jacobi_body.
+//
+// Both kernels without V (this one and jacobi_lean_body) add a pair's dot
+// product, and a recomputed norm, in one canonical order, so that a problem
+// gets the same bits from either (alone or in a batch): lane l of the
+// pair's warp(s) owns rows l + 32 k, k < RPL; four chains c = k mod 4 (the
+// rows past 32 RPL on chain 0), the lane's value (g0 + g1) + (g2 + g3), then
+// the butterfly of warp_sum over the 32 lanes.
 constexpr double kRecompute = 1.0 / 64.0;
 constexpr int kGroupPairs = 4;             // pairs (warps) per CTA
+
+// The rotated pair (c x - s y, s x + c y), each output one product and one
+// FMA in a fixed order, so that every kernel without V forms the same bits.
+__device__ __forceinline__ double rot_x(double c, double s, double x, double y)
+{
+    return fma(c, x, -(s * y));
+}
+__device__ __forceinline__ double rot_y(double c, double s, double x, double y)
+{
+    return fma(s, x, c * y);
+}
 constexpr int kGroupThreads = 32 * kGroupPairs;
 
 template <int RPL>
@@ -267,9 +285,9 @@ __device__ void jacobi_group_body(const SvdWork &w, const int bid, const int nbl
 #pragma unroll
                     for (int k = 0; k < RPL; k += 4) {  // four chains: DFMA latency
                         g0 = fma(xr[k], yr[k], g0);
-                        if (k + 1 < RPL) g1 = fma(xr[k + 1], yr[k + 1], g1);
-                        if (k + 2 < RPL) g2 = fma(xr[k + 2], yr[k + 2], g2);
-                        if (k + 3 < RPL) g3 = fma(xr[k + 3], yr[k + 3], g3);
+                        g1 = fma(xr[k + 1], yr[k + 1], g1);
+                        g2 = fma(xr[k + 2], yr[k + 2], g2);
+                        g3 = fma(xr[k + 3], yr[k + 3], g3);
                     }
                     for (int i = lane + 32 * RPL; i < m; i += 32)
                         g0 = fma(__ldcg(wp + i), __ldcg(wq + i), g0);
@@ -319,40 +337,40 @@ __device__ void jacobi_group_body(const SvdWork &w, const int bid, const int nbl
                 const int f = flg[wid];
                 if (live && (f & 1)) {
                     const double c = prm[wid][0], sn = prm[wid][1];
-                    double np2 = 0.0, nq2 = 0.0;
+                    double np2[4] = {0.0, 0.0, 0.0, 0.0}, nq2[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
                     for (int k = 0; k < RPL; ++k) {
                         const int i = lane + 32 * k;
-                        const double x = c * xr[k] - sn * yr[k];
-                        const double y = sn * xr[k] + c * yr[k];
+                        const double x = rot_x(c, sn, xr[k], yr[k]);
+                        const double y = rot_y(c, sn, xr[k], yr[k]);
                         if (i < m) {
                             __stcg(wp + i, x);
                             __stcg(wq + i, y);
                             if (f & 2)
-                                np2 = fma(x, x, np2);
+                                np2[k & 3] = fma(x, x, np2[k & 3]);
                             if (f & 4)
-                                nq2 = fma(y, y, nq2);
+                                nq2[k & 3] = fma(y, y, nq2[k & 3]);
                         }
                     }
                     for (int i = lane + 32 * RPL; i < m; i += 32) {
                         const double x0 = __ldcg(wp + i), y0 = __ldcg(wq + i);
-                        const double x = c * x0 - sn * y0, y = sn * x0 + c * y0;
+                        const double x = rot_x(c, sn, x0, y0), y = rot_y(c, sn, x0, y0);
                         __stcg(wp + i, x);
                         __stcg(wq + i, y);
                         if (f & 2)
-                            np2 = fma(x, x, np2);
+                            np2[0] = fma(x, x, np2[0]);
                         if (f & 4)
-                            nq2 = fma(y, y, nq2);
+                            nq2[0] = fma(y, y, nq2[0]);
                     }
                     if (f & 2) {  // warp-uniform
-                        np2 = warp_sum(np2);
+                        const double t = warp_sum((np2[0] + np2[1]) + (np2[2] + np2[3]));
                         if (lane == 0)
-                            w.nrm[p] = np2;
+                            w.nrm[p] = t;
                     }
                     if (f & 4) {
-                        nq2 = warp_sum(nq2);
+                        const double t = warp_sum((nq2[0] + nq2[1]) + (nq2[2] + nq2[3]));
                         if (lane == 0)
-                            w.nrm[q] = nq2;
+                            w.nrm[q] = t;
                     }
                 }
                 __syncthreads();
@@ -399,14 +417,19 @@ __device__ void jacobi_group_body(const SvdWork &w, const int bid, const int nbl
         atomicExch(w.bar + 5, unsigned(WOS_NO_CONVERGENCE));
 }
 
-// The same sweeps with a CTA of kPairThreads threads per pair (its rows
-// split over four warps): the shorter critical path of a round when the
-// batch has too few pairs to fill the GPU (a lone problem), where the
-// grouped kernel's one-warp pairs would leave FP64 units idle.
-template <int RPT>
+// The same sweeps with a CTA of kPairThreads threads per pair: the shorter
+// critical path of a round when the batch has too few pairs to fill the GPU
+// (a lone problem), where the grouped kernel's one-warp pairs would leave
+// FP64 units idle.  Warp w, lane l holds the rows l + 32 k with k = w mod 4
+// of the canonical order (chain w of the grouped kernel's lane l; warp 0 also
+// the rows past 32 RPL), and warp 0 combines the four chains of each lane
+// as that kernel does, so the two give the same bits.
+template <int RPL>
 __device__ void jacobi_lean_body(const SvdWork &w, const int bid, const int nblk)
 {
-    __shared__ double part[kPairThreads / 32];
+    constexpr int J = RPL / 4;  // rows a thread
+    static_assert(kPairThreads == 128, "four warps: the four chains of the canonical order");
+    __shared__ double part[4][32];
     __shared__ double prm[2];
     __shared__ int flag;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -437,50 +460,50 @@ __device__ void jacobi_lean_body(const SvdWork &w, const int bid, const int nblk
                 bool rotated = false;
                 if (q < n) {
                     double *wp = w.W + size_t(p) * m, *wq = w.W + size_t(q) * m;
-                    double xr[RPT], yr[RPT];
-                    double ga = 0.0;
+                    double xr[J], yr[J];
+                    double g = 0.0;
 #pragma unroll
-                    for (int k = 0; k < RPT; ++k) {
-                        int i = tid + k * kPairThreads;
-                        xr[k] = i < m ? __ldcg(wp + i) : 0.0;
-                        yr[k] = i < m ? __ldcg(wq + i) : 0.0;
+                    for (int j = 0; j < J; ++j) {
+                        const int i = lane + 32 * (4 * j + wid);
+                        xr[j] = i < m ? __ldcg(wp + i) : 0.0;
+                        yr[j] = i < m ? __ldcg(wq + i) : 0.0;
                     }
 #pragma unroll
-                    for (int k = 0; k < RPT; ++k)
-                        if (tid + k * kPairThreads < m)
-                            ga = fma(xr[k], yr[k], ga);
-                    for (int i = tid + RPT * kPairThreads; i < m; i += kPairThreads)
-                        ga = fma(__ldcg(wp + i), __ldcg(wq + i), ga);
-                    ga = warp_sum(ga);
-                    if (lane == 0)
-                        part[wid] = ga;
+                    for (int j = 0; j < J; ++j)
+                        g = fma(xr[j], yr[j], g);
+                    if (wid == 0)
+                        for (int i = lane + 32 * RPL; i < m; i += 32)
+                            g = fma(__ldcg(wp + i), __ldcg(wq + i), g);
+                    part[wid][lane] = g;
                     __syncthreads();
-                    if (tid == 0) {
-                        ga = (part[0] + part[1]) + (part[2] + part[3]);
-                        const double al = __ldcg(w.nrm + p), be = __ldcg(w.nrm + q);
-                        double c = 1.0, sn = 0.0, t = 0.0;
-                        int f = 0;
-                        const double ab = al * be, g2 = ga * ga;
-                        if (al != 0.0 && be != 0.0 && g2 > (kTol * kTol) * ab) {
-                            jacobi_rotation_t(al, be, ga, c, sn, t);
-                            f = 1;
-                            my_big = my_big || g2 > (kLast * kLast) * ab;
-                            const double tg = t * ga;
-                            const double an = al - tg, bn = be + tg;
-                            const double scale = al + be + fabs(tg);
-                            // recompute a norm whose identity cancelled
-                            if (!(an > kRecompute * scale))
-                                f |= 2;
-                            else
-                                w.nrm[p] = an;
-                            if (!(bn > kRecompute * scale))
-                                f |= 4;
-                            else
-                                w.nrm[q] = bn;
+                    if (wid == 0) {
+                        g = warp_sum((part[0][lane] + part[1][lane]) +
+                                     (part[2][lane] + part[3][lane]));
+                        if (lane == 0) {
+                            const double al = __ldcg(w.nrm + p), be = __ldcg(w.nrm + q);
+                            double c = 1.0, sn = 0.0, t = 0.0;
+                            int f = 0;
+                            const double ab = al * be, g2 = g * g;
+                            if (al != 0.0 && be != 0.0 && g2 > (kTol * kTol) * ab) {
+                                jacobi_rotation_t(al, be, g, c, sn, t);
+                                f = 1;
+                                my_big = my_big || g2 > (kLast * kLast) * ab;
+                                const double tg = t * g;
+                                const double an = al - tg, bn = be + tg;
+                                const double scale = al + be + fabs(tg);
+                                if (!(an > kRecompute * scale))
+                                    f |= 2;
+                                else
+                                    w.nrm[p] = an;
+                                if (!(bn > kRecompute * scale))
+                                    f |= 4;
+                                else
+                                    w.nrm[q] = bn;
+                            }
+                            prm[0] = c;
+                            prm[1] = sn;
+                            flag = f;
                         }
-                        prm[0] = c;
-                        prm[1] = sn;
-                        flag = f;
                     }
                     __syncthreads();
                     const int f = flag;
@@ -489,10 +512,10 @@ __device__ void jacobi_lean_body(const SvdWork &w, const int bid, const int nblk
                         const double c = prm[0], sn = prm[1];
                         double np2 = 0.0, nq2 = 0.0;
 #pragma unroll
-                        for (int k = 0; k < RPT; ++k) {
-                            const int i = tid + k * kPairThreads;
-                            const double x = c * xr[k] - sn * yr[k];
-                            const double y = sn * xr[k] + c * yr[k];
+                        for (int j = 0; j < J; ++j) {
+                            const int i = lane + 32 * (4 * j + wid);
+                            const double x = rot_x(c, sn, xr[j], yr[j]);
+                            const double y = rot_y(c, sn, xr[j], yr[j]);
                             if (i < m) {
                                 __stcg(wp + i, x);
                                 __stcg(wq + i, y);
@@ -502,36 +525,44 @@ __device__ void jacobi_lean_body(const SvdWork &w, const int bid, const int nblk
                                     nq2 = fma(y, y, nq2);
                             }
                         }
-                        for (int i = tid + RPT * kPairThreads; i < m; i += kPairThreads) {
-                            const double x0 = __ldcg(wp + i), y0 = __ldcg(wq + i);
-                            const double x = c * x0 - sn * y0, y = sn * x0 + c * y0;
-                            __stcg(wp + i, x);
-                            __stcg(wq + i, y);
-                            if (f & 2)
-                                np2 = fma(x, x, np2);
-                            if (f & 4)
-                                nq2 = fma(y, y, nq2);
-                        }
-                        if (f & 6) {  // CTA-uniform: the flag is in shared memory
-                            np2 = warp_sum(np2);
-                            nq2 = warp_sum(nq2);
-                            __shared__ double rp[2][kPairThreads / 32];
-                            if (lane == 0) {
-                                rp[0][wid] = np2;
-                                rp[1][wid] = nq2;
-                            }
-                            __syncthreads();
-                            if (tid == 0) {
+                        if (wid == 0)
+                            for (int i = lane + 32 * RPL; i < m; i += 32) {
+                                const double x0 = __ldcg(wp + i), y0 = __ldcg(wq + i);
+                                const double x = rot_x(c, sn, x0, y0);
+                                const double y = rot_y(c, sn, x0, y0);
+                                __stcg(wp + i, x);
+                                __stcg(wq + i, y);
                                 if (f & 2)
-                                    w.nrm[p] = (rp[0][0] + rp[0][1]) + (rp[0][2] + rp[0][3]);
+                                    np2 = fma(x, x, np2);
                                 if (f & 4)
-                                    w.nrm[q] = (rp[1][0] + rp[1][1]) + (rp[1][2] + rp[1][3]);
+                                    nq2 = fma(y, y, nq2);
+                            }
+                        if (f & 6) {  // CTA-uniform: the flag is in shared memory
+                            __shared__ double rp[2][4][32];
+                            rp[0][wid][lane] = np2;
+                            rp[1][wid][lane] = nq2;
+                            __syncthreads();
+                            if (wid == 0) {
+                                if (f & 2) {
+                                    const double t = warp_sum((rp[0][0][lane] + rp[0][1][lane]) +
+                                                              (rp[0][2][lane] + rp[0][3][lane]));
+                                    if (lane == 0)
+                                        w.nrm[p] = t;
+                                }
+                                if (f & 4) {
+                                    const double t = warp_sum((rp[1][0][lane] + rp[1][1][lane]) +
+                                                              (rp[1][2][lane] + rp[1][3][lane]));
+                                    if (lane == 0)
+                                        w.nrm[q] = t;
+                                }
                             }
                         }
                     }
                 }
                 __syncthreads();
                 if (tid == 0) {
+                    // the CTA's stores are ordered before the flags by the
+                    // barrier above and this fence (a release pattern)
                     __threadfence();
                     st_relaxed(w.ver + p, R + 1u);
                     if (q < n)
@@ -727,15 +758,14 @@ jacobi_kernel(const SvdWork *works, const int *begin, int np)
     jacobi_body<RPT>(w, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
 }
 
-// At most 48 registers a thread (ten 128-thread CTAs per SM): the 384 pairs
-// of each of four 768-column problems run a CTA each, none serialised.
-template <int RPT>
+// At most 48 registers a thread (ten 128-thread CTAs per SM).
+template <int RPL>
 __global__ void __launch_bounds__(kPairThreads, 10)
 jacobi_lean_kernel(const SvdWork *works, const int *begin, int np)
 {
     const int p = problem_of(begin, np);
     const SvdWork w = works[p];
-    jacobi_lean_body<RPT>(w, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
+    jacobi_lean_body<RPL>(w, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
 }
 
 template <int RPL>
@@ -1452,16 +1482,13 @@ const void *jacobi_group_kernel_rpl(int rpl)
     }
 }
 
-const void *jacobi_lean_kernel_rpt(int rpt)
+const void *jacobi_lean_kernel_rpl(int rpl)
 {
-    switch (rpt) {
-    case 1: return reinterpret_cast<const void *>(&jacobi_lean_kernel<1>);
-    case 2: return reinterpret_cast<const void *>(&jacobi_lean_kernel<2>);
-    case 3: return reinterpret_cast<const void *>(&jacobi_lean_kernel<3>);
-    case 4: return reinterpret_cast<const void *>(&jacobi_lean_kernel<4>);
-    case 5: return reinterpret_cast<const void *>(&jacobi_lean_kernel<5>);
-    case 6: return reinterpret_cast<const void *>(&jacobi_lean_kernel<6>);
-    default: return reinterpret_cast<const void *>(&jacobi_lean_kernel<8>);
+    switch (rpl) {
+    case 8: return reinterpret_cast<const void *>(&jacobi_lean_kernel<8>);
+    case 16: return reinterpret_cast<const void *>(&jacobi_lean_kernel<16>);
+    case 24: return reinterpret_cast<const void *>(&jacobi_lean_kernel<24>);
+    default: return reinterpret_cast<const void *>(&jacobi_lean_kernel<32>);
     }
 }
 
@@ -1764,27 +1791,25 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         if (P[p].lean)
             lean_pairs += P[p].wj.n_pad / 2;
     const bool grouped = lean_pairs > 3LL * sms;
-    for (int cls = 0; cls < 18; ++cls) {
+    for (int cls = 0; cls < 11; ++cls) {
         if (e != cudaSuccess)
             break;
         static const int kRpts[7] = {1, 2, 3, 4, 5, 6, 8};
         static const int kRpls[4] = {8, 16, 24, 32};
-        // classes: 0-6 with V (rows per thread), 7-10 grouped (rows per
-        // lane), 11-17 a CTA per pair without V (rows per thread)
+        // classes: 0-6 with V (rows per thread), 7-10 without V (rows per
+        // lane of the canonical order): grouped or a CTA per pair
         const bool lean = cls >= 7;
-        const bool group = cls >= 7 && cls < 11;
-        if (lean && group != grouped)
-            continue;
-        const int rpt = group ? kRpls[cls - 7] : kRpts[cls < 7 ? cls : cls - 11];
+        const bool group = lean && grouped;
+        const int rpt = lean ? kRpls[cls - 7] : kRpts[cls];
         std::vector<int> idx;
         for (int p = 0; p < np; ++p)
             if (!P[p].cl && P[p].lean == lean &&
-                (group ? rpl_of(P[p].wj.m) : rpt_of(P[p].wj.m)) == rpt)
+                (lean ? rpl_of(P[p].wj.m) : rpt_of(P[p].wj.m)) == rpt)
                 idx.push_back(p);
         if (idx.empty())
             continue;
         const void *jk = group ? jacobi_group_kernel_rpl(rpt)
-                               : lean ? jacobi_lean_kernel_rpt(rpt) : jacobi_kernel_rpt(rpt);
+                               : lean ? jacobi_lean_kernel_rpl(rpt) : jacobi_kernel_rpt(rpt);
         const int threads = group ? kGroupThreads : kPairThreads;
         int bps = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, jk, threads, 0);

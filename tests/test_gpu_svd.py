@@ -198,13 +198,20 @@ def test_svd_is_deterministic(shape, svd_path):
             assert torch.equal(a, b), rep
 
 
-def test_batched_svd_equals_single_calls(svd_path):
+@pytest.mark.parametrize("large", [False, True], ids=["mixed", "without-V"])
+def test_batched_svd_equals_single_calls(svd_path, large):
     """wos_op_svd_batched: problems of different shapes and orientations
     (direct path n < 32 and preconditioned n >= 32), and a batch larger than
     the co-resident CTAs of one launch, give each problem's single-call
-    results bit for bit."""
-    shapes = [(256, 256, 128), (96, 300, 200), (40, 60, 20), (64, 96, 48), (300, 400, 150)]
-    shapes += [(128, 200, 96)] * 24
+    results bit for bit.  Problems of more than 256 columns (sweeps without
+    V) in a batch large enough for four pairs per CTA, against single calls
+    with a CTA per pair: the two kernels' canonical summation order."""
+    if large:
+        shapes = [(600, 900, 300), (300, 900, 600), (520, 800, 400), (700, 1000, 350)]
+    else:
+        shapes = [(256, 256, 128), (96, 300, 200), (40, 60, 20), (64, 96, 48),
+                  (300, 400, 150)]
+        shapes += [(128, 200, 96)] * 24
     items, refs = [], []
     for q, (M_D, M_tot, M_1) in enumerate(shapes):
         C = W.synthetic_counts(M_D, M_tot, 50_000, seed=q + 11)
