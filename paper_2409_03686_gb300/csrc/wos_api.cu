@@ -33,6 +33,9 @@ struct wos_context {
     int max_smem_optin = 0;
     std::atomic<int> svd_path{WOS_SVD_AUTO};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // streams of the batched build's kernel classes (created on first use)
+    std::mutex class_mu;
+    cudaStream_t class_streams[wos::kClassStreams] = {};
 };
 
 namespace wos {
@@ -51,6 +54,15 @@ void count_launches(wos_context *c, int n) { c->launches += uint64_t(n); }
 int ctx_sm_count(const wos_context *c) { return c->sm_count; }
 int ctx_max_smem(const wos_context *c) { return c->max_smem_optin; }
 int ctx_svd_path(const wos_context *c) { return c->svd_path.load(); }
+
+cudaStream_t ctx_class_stream(wos_context *c, int i)
+{
+    std::lock_guard<std::mutex> lock(c->class_mu);
+    if (!c->class_streams[i] &&
+        cudaStreamCreateWithFlags(&c->class_streams[i], cudaStreamNonBlocking) != cudaSuccess)
+        c->class_streams[i] = nullptr;
+    return c->class_streams[i];
+}
 
 static int tune_key(int precision, int dim, int kind) { return (precision << 8) | (dim << 4) | kind; }
 
@@ -107,6 +119,9 @@ extern "C" wos_status wos_destroy(wos_context *c)
     cudaSetDevice(c->device);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
+    for (cudaStream_t st : c->class_streams)
+        if (st)
+            cudaStreamDestroy(st);
     delete c;
     return WOS_OK;
 }

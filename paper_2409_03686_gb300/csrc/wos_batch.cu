@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -237,26 +238,80 @@ extern "C" wos_status wos_build_operators_batched(wos_context *ctx, int32_t n,
     cudaSetDevice(ctx_device(ctx));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned long long w[2 * kNumKinds][5] = {};
-    for (int dd = 0; dd < 2; ++dd) {
-        for (int kk = 0; kk < kNumKinds; ++kk) {
-            const std::vector<int> &cls = by_class[dd][kk];
-            if (cls.empty())
-                continue;
-            wos_status st;
-            unsigned long long *wo = stats ? w[dd * kNumKinds + kk] : nullptr;
-            if (o.precision == WOS_FP64)
-                st = dd == 0 ? launch_class<double, 2>(ctx, cls, problems, S, seed, o, s, wo)
-                             : launch_class<double, 3>(ctx, cls, problems, S, seed, o, s, wo);
-            else
-                st = dd == 0 ? launch_class<float, 2>(ctx, cls, problems, S, seed, o, s, wo)
-                             : launch_class<float, 3>(ctx, cls, problems, S, seed, o, s, wo);
-            if (st != WOS_OK)
-                return st;
-        }
+    // Within a class the instances go longest walks first (smallest eps:
+    // E[N_eps] grows with log 1/eps, then the most walks), so that the tiles
+    // drawn last are short and the launch drains quickly.  The order of the
+    // tiles changes no walk: each walk's random numbers are fixed by its
+    // counter.
+    auto work_of = [&](int q) {
+        const wos_problem &pb = problems[q];
+        const uint32_t k1 = pb.k1 ? pb.k1 : pb.N;
+        return double(pb.M_D) * double(k1 - pb.k0) * std::log(1.0 / pb.eps);
+    };
+    std::vector<int> order;  // classes, the most work first
+    std::vector<double> cwork(2 * kNumKinds, 0.0);
+    for (int c = 0; c < 2 * kNumKinds; ++c) {
+        std::vector<int> &cls = by_class[c / kNumKinds][c % kNumKinds];
+        if (cls.empty())
+            continue;
+        std::stable_sort(cls.begin(), cls.end(), [&](int a, int b) {
+            if (problems[a].eps != problems[b].eps)
+                return problems[a].eps < problems[b].eps;
+            return work_of(a) > work_of(b);
+        });
+        for (int q : cls)
+            cwork[c] += work_of(q);
+        order.push_back(c);
     }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return cwork[a] > cwork[b]; });
+    // The classes run concurrently, each on a stream of the context forked
+    // from `stream` and joined back to it: the persistent launches queue in
+    // order of their work, and each one's blocks take the SMs the previous
+    // one frees as it drains (one stream when the caller times the kernel).
+    const bool concurrent = order.size() > 1 && !o.kernel_events[0] && !o.kernel_events[1];
+    cudaEvent_t fork = nullptr;
+    if (concurrent && (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventRecord(fork, s) != cudaSuccess))
+        return WOS_CUDA_ERROR;
+    wos_status st = WOS_OK;
+    for (int c : order) {
+        const int dd = c / kNumKinds, kk = c % kNumKinds;
+        const std::vector<int> &cls = by_class[dd][kk];
+        cudaStream_t cs = s;
+        if (concurrent) {
+            cs = ctx_class_stream(ctx, c);
+            if (!cs || cudaStreamWaitEvent(cs, fork, 0) != cudaSuccess) {
+                st = WOS_CUDA_ERROR;
+                break;
+            }
+        }
+        unsigned long long *wo = stats ? w[c] : nullptr;
+        if (o.precision == WOS_FP64)
+            st = dd == 0 ? launch_class<double, 2>(ctx, cls, problems, S, seed, o, cs, wo)
+                         : launch_class<double, 3>(ctx, cls, problems, S, seed, o, cs, wo);
+        else
+            st = dd == 0 ? launch_class<float, 2>(ctx, cls, problems, S, seed, o, cs, wo)
+                         : launch_class<float, 3>(ctx, cls, problems, S, seed, o, cs, wo);
+        if (concurrent) {
+            cudaEvent_t join = nullptr;
+            if (cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventRecord(join, cs) != cudaSuccess ||
+                cudaStreamWaitEvent(s, join, 0) != cudaSuccess)
+                st = st == WOS_OK ? WOS_CUDA_ERROR : st;
+            if (join)
+                cudaEventDestroy(join);
+        }
+        if (st != WOS_OK)
+            break;
+    }
+    if (fork)
+        cudaEventDestroy(fork);
+    if (st != WOS_OK)
+        return st;
     if (!stats)
         return WOS_OK;
-    wos_status st = cuda_status(cudaStreamSynchronize(s));
+    st = cuda_status(cudaStreamSynchronize(s));
     std::memset(stats, 0, sizeof(*stats));
     for (int c = 0; c < 2 * kNumKinds; ++c) {
         stats->steps += w[c][1];

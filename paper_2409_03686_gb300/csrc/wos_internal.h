@@ -14,6 +14,10 @@ int ctx_sm_count(const wos_context *c);
 void count_launches(wos_context *c, int n);
 int ctx_max_smem(const wos_context *c);
 int ctx_svd_path(const wos_context *c);  // WOS_SVD_AUTO / _GRID / _CLUSTER
+// Stream i (< kClassStreams) of the context for a batched build's kernel
+// classes, created non-blocking on first use; null if creation failed.
+constexpr int kClassStreams = 18;
+cudaStream_t ctx_class_stream(wos_context *c, int i);
 // Launch fields of opts replaced by the context's tuned configuration for the
 // class (precision, dim, kind) when they are all zero.
 void apply_tuning(const wos_context *c, int precision, int dim, int kind, wos_opts *o);
