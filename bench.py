@@ -311,11 +311,12 @@ def jacobi_flop(m: int, n: int, sweeps: int) -> int:
     """FP64 flop of the Jacobi sweeps of one SVD of an m x n worked matrix
     (m >= n) as the library runs it (on X = R^T, n x n, when n >= 32): every
     pair visit counted as rotated.  Up to 256 columns the sweeps accumulate V
-    (three dot products 6l, column updates 6l + 6n); above, they do not and
-    carry the norms (one dot product 2l, column updates 6l)."""
+    (three dot products 6l, column updates 6l + 6n); above, they do not,
+    carry the norms and scale the columns (one dot product 2l, column
+    updates 4l: one FMA per row and column)."""
     rows = n if n >= 32 else m
     if n > 256:
-        return sweeps * (n * (n - 1) // 2) * (8 * rows)
+        return sweeps * (n * (n - 1) // 2) * (6 * rows)
     return sweeps * (n * (n - 1) // 2) * (12 * rows + 6 * n)
 
 
@@ -610,7 +611,7 @@ def run_gpu(args, rank: int, world: int, dist):
                                "per chip) x 2 flop x 2070 MHz",
                 "unit_of_work": "one factorisation: the pivoted Householder QR (2mn^2 - "
                                 "2n^3/3 flop, n >= 32) and every pair visit of every sweep "
-                                "(12 l + 6n flop with V accumulated, n <= 256; 8 l without, "
+                                "(12 l + 6n flop with V accumulated, n <= 256; 6 l without, "
                                 "n > 256; l = rows of the matrix Jacobi works on: n after the "
                                 "QR, m without; every visit counted as rotated)",
                 "sweeps": [p["sweeps"] for p in prep],

@@ -50,6 +50,8 @@ struct SvdWork {
                       // had cos^2 > kLast^2
     unsigned *ver;    // n_pad column versions (rounds finished per column)
     double *nrm;      // n squared column norms (kernels without V only)
+    double *dsc, *dinv; // n column scales d_j and 1 / d_j (kernels without V:
+                        // the column is d_j times the stored one)
 };
 
 __device__ __forceinline__ double warp_sum(double v)
@@ -173,19 +175,6 @@ __device__ __forceinline__ void jacobi_rotation(double al, double be, double ga,
     s = gy * z;
 }
 
-// The rotation of jacobi_rotation together with its tangent t = s / c.
-__device__ __forceinline__ void jacobi_rotation_t(double al, double be, double ga, double &c,
-                                                  double &s, double &t)
-{
-    const double h = 0.5 * (be - al);
-    const double y = rsqrt(fma(h, h, ga * ga));  // 1 / r
-    const double c2 = fma(fabs(h) * y, 0.5, 0.5);
-    const double gy = copysign(0.5, h) * ga * y;
-    const double z = rsqrt(c2);                  // 1 / c
-    c = c2 * z;
-    s = gy * z;
-    t = s * z;
-}
 
 // Jacobi without the accumulated V, for the large problems (worked matrices
 // of more than 256 columns, where the FP64 work of the sweeps bounds the
@@ -216,24 +205,101 @@ __device__ __forceinline__ void jacobi_rotation_t(double al, double be, double g
 constexpr double kRecompute = 1.0 / 64.0;
 constexpr int kGroupPairs = 4;             // pairs (warps) per CTA
 
-// The rotated pair (c x - s y, s x + c y), each output one product and one
-// FMA in a fixed order, so that every kernel without V forms the same bits.
-__device__ __forceinline__ double rot_x(double c, double s, double x, double y)
+// Scaled rotations (the square-root-free form of plane rotations, after
+// Gentleman, and Anda & Park's dynamic scaling): column j is stored as xt_j
+// with x_j = d_j xt_j.  The rotation (c, s) of the pair, t = s / c, becomes
+//     xt_p' = xt_p - tau_p xt_q,  tau_p = t d_q / d_p,   d_p' = c d_p,
+//     xt_q' = xt_q + tau_q xt_p,  tau_q = t d_p / d_q,   d_q' = c d_q,
+// one FMA per row and column instead of a product and an FMA; the scales
+// only shrink (c <= 1), so a column whose scale falls below 2^-80 has it
+// folded into the stored values in the same pass (d = 1 again).  Its Gram
+// entries: x_p . x_q = d_p d_q (xt_p . xt_q); the squared norms of x are
+// carried as before.  Every kernel without V calls this on one lane per
+// pair and applies the result in the same arithmetic, so they form the same
+// bits.  f: 1 rotate, 2 / 4 recompute the norm of p / q, 8 / 16 fold the
+// scale of p / q (multiply the new values by mp / mq).
+struct ScaledRot {
+    double tp, tq;   // tau_p, tau_q
+    double mp, mq;   // fold multipliers (the new scales)
+    double sp, sq;   // factor of a recomputed stored norm: d'^2, or 1 after a fold
+    int f;
+};
+
+constexpr double kFoldBelow = 8.271806125530277e-25;  // 2^-80
+
+__device__ __forceinline__ ScaledRot scaled_rotation(const SvdWork &w, int p, int q, double gh,
+                                                     bool *big)
 {
-    return fma(c, x, -(s * y));
+    ScaledRot r = {0.0, 0.0, 1.0, 1.0, 1.0, 1.0, 0};
+    const double al = __ldcg(w.nrm + p), be = __ldcg(w.nrm + q);
+    const double dp = __ldcg(w.dsc + p), dq = __ldcg(w.dsc + q);
+    const double ep = __ldcg(w.dinv + p), eq = __ldcg(w.dinv + q);
+    const double g = gh * dp * dq;
+    const double ab = al * be, g2 = g * g;
+    if (!(al != 0.0 && be != 0.0 && g2 > (kTol * kTol) * ab))
+        return r;
+    // the rotation of jacobi_rotation, with z = 1 / c and t = s / c
+    const double h = 0.5 * (be - al);
+    const double y = rsqrt(fma(h, h, g * g));
+    const double c2 = fma(fabs(h) * y, 0.5, 0.5);
+    const double gy = copysign(0.5, h) * g * y;
+    const double z = rsqrt(c2);
+    const double c = c2 * z, t = gy * z * z;
+    *big = *big || g2 > (kLast * kLast) * ab;
+    r.f = 1;
+    r.tp = t * dq * ep;
+    r.tq = t * dp * eq;
+    double ndp = c * dp, ndq = c * dq, nep = z * ep, neq = z * eq;
+    if (ndp < kFoldBelow) {
+        r.f |= 8;
+        r.mp = ndp;
+        ndp = 1.0;
+        nep = 1.0;
+    }
+    if (ndq < kFoldBelow) {
+        r.f |= 16;
+        r.mq = ndq;
+        ndq = 1.0;
+        neq = 1.0;
+    }
+    w.dsc[p] = ndp;
+    w.dinv[p] = nep;
+    w.dsc[q] = ndq;
+    w.dinv[q] = neq;
+    r.sp = ndp * ndp;
+    r.sq = ndq * ndq;
+    const double tg = t * g;
+    const double an = al - tg, bn = be + tg;
+    const double scale = al + be + fabs(tg);
+    if (!(an > kRecompute * scale))
+        r.f |= 2;
+    else
+        w.nrm[p] = an;
+    if (!(bn > kRecompute * scale))
+        r.f |= 4;
+    else
+        w.nrm[q] = bn;
+    return r;
 }
-__device__ __forceinline__ double rot_y(double c, double s, double x, double y)
+
+// The rotated stored values of a row (x, y) under r.
+__device__ __forceinline__ void scaled_update(const ScaledRot &r, double x, double y, double &xn,
+                                              double &yn)
 {
-    return fma(s, x, c * y);
+    xn = fma(-r.tp, y, x);
+    yn = fma(r.tq, x, y);
+    if (r.f & 8)
+        xn *= r.mp;
+    if (r.f & 16)
+        yn *= r.mq;
 }
 constexpr int kGroupThreads = 32 * kGroupPairs;
 
 template <int RPL>
 __device__ void jacobi_group_body(const SvdWork &w, const int bid, const int nblk)
 {
-    __shared__ double gk[kGroupPairs];       // x_p . x_q of each pair
-    __shared__ double prm[kGroupPairs][2];   // c, s
-    __shared__ int flg[kGroupPairs];         // 1 rotate, 2 / 4 recompute |x_p|^2 / |x_q|^2
+    __shared__ double gk[kGroupPairs];       // xt_p . xt_q of each pair
+    __shared__ ScaledRot prm[kGroupPairs];   // each pair's scaled rotation
     __shared__ int s_rot, s_big;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int half = w.n_pad / 2;
@@ -299,50 +365,47 @@ __device__ void jacobi_group_body(const SvdWork &w, const int bid, const int nbl
                 // warp 0 forms the rotations of the CTA's pairs, lane k for pair k
                 if (wid == 0 && lane < kGroupPairs) {
                     const int prk = gi * kGroupPairs + lane;
-                    int f = 0;
-                    double c = 1.0, sn = 0.0;
+                    ScaledRot sr = {0.0, 0.0, 1.0, 1.0, 1.0, 1.0, 0};
                     if (prk < half) {
                         const int a = rr_player(prk, r, w.n_pad);
                         const int b = rr_player(w.n_pad - 1 - prk, r, w.n_pad);
                         const int pk = min(a, b), qk = max(a, b);
                         if (qk < n) {
-                            const double g = gk[lane];
-                            const double al = __ldcg(w.nrm + pk), be = __ldcg(w.nrm + qk);
-                            const double ab = al * be, gg = g * g;
-                            if (al != 0.0 && be != 0.0 && gg > (kTol * kTol) * ab) {
-                                double t;
-                                jacobi_rotation_t(al, be, g, c, sn, t);
-                                f = 1;
-                                my_big = my_big || gg > (kLast * kLast) * ab;
-                                ++my_rot;
-                                const double tg = t * g;
-                                const double an = al - tg, bn = be + tg;
-                                const double scale = al + be + fabs(tg);
-                                if (!(an > kRecompute * scale))
-                                    f |= 2;
-                                else
-                                    w.nrm[pk] = an;
-                                if (!(bn > kRecompute * scale))
-                                    f |= 4;
-                                else
-                                    w.nrm[qk] = bn;
-                            }
+                            sr = scaled_rotation(w, pk, qk, gk[lane], &my_big);
+                            my_rot += sr.f & 1;
                         }
                     }
-                    prm[lane][0] = c;
-                    prm[lane][1] = sn;
-                    flg[lane] = f;
+                    prm[lane] = sr;
                 }
                 __syncthreads();
-                const int f = flg[wid];
-                if (live && (f & 1)) {
-                    const double c = prm[wid][0], sn = prm[wid][1];
+                const ScaledRot sr = prm[wid];
+                const int f = sr.f;
+                if (live && f == 1) {
+                    // the common case: two FMAs a row, no predicated FP64
+                    // work (a warp FP64 instruction holds the unit for 64
+                    // cycles even with its lanes predicated off)
+#pragma unroll
+                    for (int k = 0; k < RPL; ++k) {
+                        const int i = lane + 32 * k;
+                        const double x = fma(-sr.tp, yr[k], xr[k]);
+                        const double y = fma(sr.tq, xr[k], yr[k]);
+                        if (i < m) {
+                            __stcg(wp + i, x);
+                            __stcg(wq + i, y);
+                        }
+                    }
+                    for (int i = lane + 32 * RPL; i < m; i += 32) {
+                        const double x0 = __ldcg(wp + i), y0 = __ldcg(wq + i);
+                        __stcg(wp + i, fma(-sr.tp, y0, x0));
+                        __stcg(wq + i, fma(sr.tq, x0, y0));
+                    }
+                } else if (live && (f & 1)) {
                     double np2[4] = {0.0, 0.0, 0.0, 0.0}, nq2[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
                     for (int k = 0; k < RPL; ++k) {
                         const int i = lane + 32 * k;
-                        const double x = rot_x(c, sn, xr[k], yr[k]);
-                        const double y = rot_y(c, sn, xr[k], yr[k]);
+                        double x, y;
+                        scaled_update(sr, xr[k], yr[k], x, y);
                         if (i < m) {
                             __stcg(wp + i, x);
                             __stcg(wq + i, y);
@@ -353,8 +416,8 @@ __device__ void jacobi_group_body(const SvdWork &w, const int bid, const int nbl
                         }
                     }
                     for (int i = lane + 32 * RPL; i < m; i += 32) {
-                        const double x0 = __ldcg(wp + i), y0 = __ldcg(wq + i);
-                        const double x = rot_x(c, sn, x0, y0), y = rot_y(c, sn, x0, y0);
+                        double x, y;
+                        scaled_update(sr, __ldcg(wp + i), __ldcg(wq + i), x, y);
                         __stcg(wp + i, x);
                         __stcg(wq + i, y);
                         if (f & 2)
@@ -365,12 +428,12 @@ __device__ void jacobi_group_body(const SvdWork &w, const int bid, const int nbl
                     if (f & 2) {  // warp-uniform
                         const double t = warp_sum((np2[0] + np2[1]) + (np2[2] + np2[3]));
                         if (lane == 0)
-                            w.nrm[p] = t;
+                            w.nrm[p] = t * sr.sp;
                     }
                     if (f & 4) {
                         const double t = warp_sum((nq2[0] + nq2[1]) + (nq2[2] + nq2[3]));
                         if (lane == 0)
-                            w.nrm[q] = t;
+                            w.nrm[q] = t * sr.sq;
                     }
                 }
                 __syncthreads();
@@ -430,8 +493,7 @@ __device__ void jacobi_lean_body(const SvdWork &w, const int bid, const int nblk
     constexpr int J = RPL / 4;  // rows a thread
     static_assert(kPairThreads == 128, "four warps: the four chains of the canonical order");
     __shared__ double part[4][32];
-    __shared__ double prm[2];
-    __shared__ int flag;
+    __shared__ ScaledRot prm;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int half = w.n_pad / 2;
     const int m = w.m, n = w.n;
@@ -479,43 +541,38 @@ __device__ void jacobi_lean_body(const SvdWork &w, const int bid, const int nblk
                     if (wid == 0) {
                         g = warp_sum((part[0][lane] + part[1][lane]) +
                                      (part[2][lane] + part[3][lane]));
-                        if (lane == 0) {
-                            const double al = __ldcg(w.nrm + p), be = __ldcg(w.nrm + q);
-                            double c = 1.0, sn = 0.0, t = 0.0;
-                            int f = 0;
-                            const double ab = al * be, g2 = g * g;
-                            if (al != 0.0 && be != 0.0 && g2 > (kTol * kTol) * ab) {
-                                jacobi_rotation_t(al, be, g, c, sn, t);
-                                f = 1;
-                                my_big = my_big || g2 > (kLast * kLast) * ab;
-                                const double tg = t * g;
-                                const double an = al - tg, bn = be + tg;
-                                const double scale = al + be + fabs(tg);
-                                if (!(an > kRecompute * scale))
-                                    f |= 2;
-                                else
-                                    w.nrm[p] = an;
-                                if (!(bn > kRecompute * scale))
-                                    f |= 4;
-                                else
-                                    w.nrm[q] = bn;
-                            }
-                            prm[0] = c;
-                            prm[1] = sn;
-                            flag = f;
-                        }
+                        if (lane == 0)
+                            prm = scaled_rotation(w, p, q, g, &my_big);
                     }
                     __syncthreads();
-                    const int f = flag;
-                    if (f & 1) {
+                    const ScaledRot sr = prm;
+                    const int f = sr.f;
+                    if (f == 1) {  // the common case, as in the grouped kernel
                         rotated = true;
-                        const double c = prm[0], sn = prm[1];
+#pragma unroll
+                        for (int j = 0; j < J; ++j) {
+                            const int i = lane + 32 * (4 * j + wid);
+                            const double x = fma(-sr.tp, yr[j], xr[j]);
+                            const double y = fma(sr.tq, xr[j], yr[j]);
+                            if (i < m) {
+                                __stcg(wp + i, x);
+                                __stcg(wq + i, y);
+                            }
+                        }
+                        if (wid == 0)
+                            for (int i = lane + 32 * RPL; i < m; i += 32) {
+                                const double x0 = __ldcg(wp + i), y0 = __ldcg(wq + i);
+                                __stcg(wp + i, fma(-sr.tp, y0, x0));
+                                __stcg(wq + i, fma(sr.tq, x0, y0));
+                            }
+                    } else if (f & 1) {
+                        rotated = true;
                         double np2 = 0.0, nq2 = 0.0;
 #pragma unroll
                         for (int j = 0; j < J; ++j) {
                             const int i = lane + 32 * (4 * j + wid);
-                            const double x = rot_x(c, sn, xr[j], yr[j]);
-                            const double y = rot_y(c, sn, xr[j], yr[j]);
+                            double x, y;
+                            scaled_update(sr, xr[j], yr[j], x, y);
                             if (i < m) {
                                 __stcg(wp + i, x);
                                 __stcg(wq + i, y);
@@ -527,9 +584,8 @@ __device__ void jacobi_lean_body(const SvdWork &w, const int bid, const int nblk
                         }
                         if (wid == 0)
                             for (int i = lane + 32 * RPL; i < m; i += 32) {
-                                const double x0 = __ldcg(wp + i), y0 = __ldcg(wq + i);
-                                const double x = rot_x(c, sn, x0, y0);
-                                const double y = rot_y(c, sn, x0, y0);
+                                double x, y;
+                                scaled_update(sr, __ldcg(wp + i), __ldcg(wq + i), x, y);
                                 __stcg(wp + i, x);
                                 __stcg(wq + i, y);
                                 if (f & 2)
@@ -547,13 +603,13 @@ __device__ void jacobi_lean_body(const SvdWork &w, const int bid, const int nblk
                                     const double t = warp_sum((rp[0][0][lane] + rp[0][1][lane]) +
                                                               (rp[0][2][lane] + rp[0][3][lane]));
                                     if (lane == 0)
-                                        w.nrm[p] = t;
+                                        w.nrm[p] = t * sr.sp;
                                 }
                                 if (f & 4) {
                                     const double t = warp_sum((rp[1][0][lane] + rp[1][1][lane]) +
                                                               (rp[1][2][lane] + rp[1][3][lane]));
                                     if (lane == 0)
-                                        w.nrm[q] = t;
+                                        w.nrm[q] = t * sr.sq;
                                 }
                             }
                         }
@@ -790,9 +846,21 @@ __global__ void column_sq_norms_kernel(SvdWork w)
         for (int i = lane; i < w.m; i += 32)
             s = fma(c[i], c[i], s);
         s = warp_sum(s);
-        if (lane == 0)
+        if (lane == 0) {
             w.nrm[j] = s;
+            w.dsc[j] = 1.0;
+            w.dinv[j] = 1.0;
+        }
     }
+}
+
+// X[:, j] *= d_j: the stored columns of the sweeps without V back to X.
+__global__ void fold_scales_kernel(SvdWork w)
+{
+    const size_t nn = size_t(w.n) * w.m;
+    for (size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nn;
+         t += size_t(gridDim.x) * blockDim.x)
+        w.W[t] *= w.dsc[t / w.m];
 }
 
 // Z = P X: row perm[k] of Z is row k of X (n x n, column-major), so that the
@@ -1640,7 +1708,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         }
         if (b.lean) {
             o.W0 = take(size_t(w.m) * w.n * 8);
-            o.nrm = take(size_t(w.n) * 8);
+            o.nrm = take(size_t(w.n) * 8 * 3);  // norms, scales, inverse scales
         }
     }
     const size_t o_jrec = take(sizeof(SvdWork) * np), o_qrec = take(sizeof(QrWork) * np);
@@ -1679,6 +1747,8 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         }
         b.wj = w;
         b.wj.nrm = b.lean ? reinterpret_cast<double *>(base + o.nrm) : nullptr;
+        b.wj.dsc = b.lean ? b.wj.nrm + w.n : nullptr;
+        b.wj.dinv = b.lean ? b.wj.nrm + 2 * size_t(w.n) : nullptr;
         if (b.pre) {
             QrWork &q = b.q;
             q.A = w.W;
@@ -1836,11 +1906,12 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         if (P[p].lean) {
             SvdProb &b = P[p];
             const int m = b.w.m, n = b.w.n;
+            fold_scales_kernel<<<sms * 4, 256, 0, st>>>(b.wj);  // X = d_j xt_j
             permute_rows_kernel<<<sms * 4, 256, 0, st>>>(b.wj.W, b.q.perm, n, b.wj.Vw);
             dim3 gg(unsigned((m + kGemmTile - 1) / kGemmTile),
                     unsigned((n + kGemmTile - 1) / kGemmTile));
             dgemm_nn_kernel<<<gg, 256, 0, st>>>(m, n, n, b.W0, b.wj.Vw, b.Lb);
-            launches += 2;
+            launches += 3;
         }
     if (e == cudaSuccess) {  // left vectors of every other preconditioned problem
         std::vector<LeftJob> jobs;
