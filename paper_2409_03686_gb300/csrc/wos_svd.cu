@@ -227,13 +227,29 @@ struct ScaledRot {
 
 constexpr double kFoldBelow = 8.271806125530277e-25;  // 2^-80
 
-__device__ __forceinline__ ScaledRot scaled_rotation(const SvdWork &w, int p, int q, double gh,
-                                                     bool *big)
+// A pair's carried quantities: squared norms, scales and inverse scales of
+// columns p and q (read at the start of a round, off the rotation's path).
+struct PairState {
+    double al, be, dp, dq, ep, eq;
+};
+
+__device__ __forceinline__ PairState load_pair_state(const SvdWork &w, int p, int q)
+{
+    PairState s;
+    s.al = __ldcg(w.nrm + p);
+    s.be = __ldcg(w.nrm + q);
+    s.dp = __ldcg(w.dsc + p);
+    s.dq = __ldcg(w.dsc + q);
+    s.ep = __ldcg(w.dinv + p);
+    s.eq = __ldcg(w.dinv + q);
+    return s;
+}
+
+__device__ __forceinline__ ScaledRot scaled_rotation(const SvdWork &w, int p, int q,
+                                                     const PairState &ps, double gh, bool *big)
 {
     ScaledRot r = {0.0, 0.0, 1.0, 1.0, 1.0, 1.0, 0};
-    const double al = __ldcg(w.nrm + p), be = __ldcg(w.nrm + q);
-    const double dp = __ldcg(w.dsc + p), dq = __ldcg(w.dsc + q);
-    const double ep = __ldcg(w.dinv + p), eq = __ldcg(w.dinv + q);
+    const double al = ps.al, be = ps.be, dp = ps.dp, dq = ps.dq, ep = ps.ep, eq = ps.eq;
     const double g = gh * dp * dq;
     const double ab = al * be, g2 = g * g;
     if (!(al != 0.0 && be != 0.0 && g2 > (kTol * kTol) * ab))
@@ -338,6 +354,21 @@ __device__ void jacobi_group_body(const SvdWork &w, const int bid, const int nbl
                     ok = wait_version(w.ver, q, R, status);
                 if (!__syncthreads_and(ok))
                     return;
+                // lane k of warp 0 reads pair k's carried state now (its
+                // rotation needs it after the dot products)
+                PairState ps = {0.0, 0.0, 1.0, 1.0, 1.0, 1.0};
+                int pk = n, qk = n;
+                if (wid == 0 && lane < kGroupPairs) {
+                    const int prk = gi * kGroupPairs + lane;
+                    if (prk < half) {
+                        const int a = rr_player(prk, r, w.n_pad);
+                        const int b = rr_player(w.n_pad - 1 - prk, r, w.n_pad);
+                        pk = min(a, b);
+                        qk = max(a, b);
+                        if (qk < n)
+                            ps = load_pair_state(w, pk, qk);
+                    }
+                }
                 double xr[RPL], yr[RPL];
                 double *wp = w.W + size_t(live ? p : 0) * m, *wq = w.W + size_t(live ? q : 0) * m;
                 double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
@@ -364,16 +395,10 @@ __device__ void jacobi_group_body(const SvdWork &w, const int bid, const int nbl
                 __syncthreads();
                 // warp 0 forms the rotations of the CTA's pairs, lane k for pair k
                 if (wid == 0 && lane < kGroupPairs) {
-                    const int prk = gi * kGroupPairs + lane;
                     ScaledRot sr = {0.0, 0.0, 1.0, 1.0, 1.0, 1.0, 0};
-                    if (prk < half) {
-                        const int a = rr_player(prk, r, w.n_pad);
-                        const int b = rr_player(w.n_pad - 1 - prk, r, w.n_pad);
-                        const int pk = min(a, b), qk = max(a, b);
-                        if (qk < n) {
-                            sr = scaled_rotation(w, pk, qk, gk[lane], &my_big);
-                            my_rot += sr.f & 1;
-                        }
+                    if (qk < n) {
+                        sr = scaled_rotation(w, pk, qk, ps, gk[lane], &my_big);
+                        my_rot += sr.f & 1;
                     }
                     prm[lane] = sr;
                 }
@@ -522,6 +547,9 @@ __device__ void jacobi_lean_body(const SvdWork &w, const int bid, const int nblk
                 bool rotated = false;
                 if (q < n) {
                     double *wp = w.W + size_t(p) * m, *wq = w.W + size_t(q) * m;
+                    PairState ps = {0.0, 0.0, 1.0, 1.0, 1.0, 1.0};
+                    if (tid == 0)
+                        ps = load_pair_state(w, p, q);
                     double xr[J], yr[J];
                     double g = 0.0;
 #pragma unroll
@@ -542,7 +570,7 @@ __device__ void jacobi_lean_body(const SvdWork &w, const int bid, const int nblk
                         g = warp_sum((part[0][lane] + part[1][lane]) +
                                      (part[2][lane] + part[3][lane]));
                         if (lane == 0)
-                            prm = scaled_rotation(w, p, q, g, &my_big);
+                            prm = scaled_rotation(w, p, q, ps, g, &my_big);
                     }
                     __syncthreads();
                     const ScaledRot sr = prm;
