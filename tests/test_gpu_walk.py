@@ -218,6 +218,22 @@ def test_closed_form_disc_fp32():
     assert ok, info
 
 
+def test_closed_form_disc_fp32_large_n():
+    """The FP32 chain's random-number map (Philox words, 23-bit windows, the
+    FMA angle) at N = 1e6 walks per point on config 1's disc: every arc of
+    every point within the Bonferroni band of the Poisson kernel, whose
+    statistical width is now ten times narrower than at N = 1e5 -- a defect
+    of the direction map (a bias of the angle of 1e-3 or a lost window) would
+    leave it."""
+    inst = W.disc_config(N=1_000_000, fp64=False)
+    r = gpu_build(inst, trace=False)
+    assert (r["counts"].sum(1) + r["unterm"] == inst.N).all()
+    A = r["counts"] / inst.N
+    P = np.array([CF.disc_row(x, 32) for x in inst.points])
+    ok, info = check_band(A, P, inst.N, beta_eps(inst.eps, 0.75 / (2 * math.pi * 0.25)))
+    assert ok, info
+
+
 def test_closed_form_ball_fp32():
     inst = W.ball_config(N=100_000, n_points=16, nb=4, ns=6, K=np.eye(3))
     r = gpu_build(inst, trace=False)
