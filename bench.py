@@ -298,7 +298,7 @@ def run_reference(args, rank: int, world: int):
 # ----------------------------------------------------------------------------
 # the GPU arm
 # ----------------------------------------------------------------------------
-SVD_PATHS = {"auto": 0, "grid": 1}
+SVD_PATHS = {"auto": 0, "grid": 1, "fp64-sweeps": 3}
 
 
 def qr_flop(m: int, n: int) -> int:

@@ -481,7 +481,15 @@ wos_status wos_op_svd_batched(wos_context *ctx, int32_t n,
  *   WOS_SVD_GRID     always the grid-wide kernels (cooperative QR and Jacobi
  *                    launches synchronised through global memory);
  *   WOS_SVD_CLUSTER  as AUTO (a problem that does not fit still runs on the
- *                    grid-wide kernels).
+ *                    grid-wide kernels);
+ *   WOS_SVD_FP64_SWEEPS  as AUTO, but a problem of more than 256 columns
+ *                    runs every Jacobi sweep in FP64.  By default (up to 896
+ *                    columns) its sweeps first run on an FP32 copy of
+ *                    X = R^T in one thread-block cluster, and the FP64 sweeps
+ *                    start from X Q, Q the product of those rotations made
+ *                    orthogonal to FP64 rounding by Newton-Schulz steps: the
+ *                    same singular values and vectors to FP64 rounding, in a
+ *                    few FP64 sweeps instead of about ten.
  * The cluster kernel factors one problem in one thread-block cluster of up
  * to 16 CTAs: the matrix stays in distributed shared memory and the Jacobi
  * rounds are ordered by cluster barriers.  Both compute the same
@@ -489,7 +497,7 @@ wos_status wos_op_svd_batched(wos_context *ctx, int32_t n,
  * the same round-robin order) with different summation orders, so their
  * results agree to rounding, not bit for bit; each is deterministic.
  * Errors: WOS_INVALID_ARG (unknown path or NULL ctx). */
-enum { WOS_SVD_AUTO = 0, WOS_SVD_GRID = 1, WOS_SVD_CLUSTER = 2 };
+enum { WOS_SVD_AUTO = 0, WOS_SVD_GRID = 1, WOS_SVD_CLUSTER = 2, WOS_SVD_FP64_SWEEPS = 3 };
 wos_status wos_set_svd_path(wos_context *ctx, int32_t path);
 
 /* Measured throughput of the execution pipes the kernels lean on, from

@@ -133,7 +133,7 @@ extern "C" uint64_t wos_kernel_launches(const wos_context *c)
 
 extern "C" wos_status wos_set_svd_path(wos_context *c, int32_t path)
 {
-    if (!c || path < WOS_SVD_AUTO || path > WOS_SVD_CLUSTER)
+    if (!c || path < WOS_SVD_AUTO || path > WOS_SVD_FP64_SWEEPS)
         return WOS_INVALID_ARG;
     c->svd_path.store(path);
     return WOS_OK;

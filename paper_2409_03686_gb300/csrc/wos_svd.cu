@@ -819,6 +819,193 @@ __device__ void jacobi_body(const SvdWork &w, const int bid, const int nblk)
         atomicExch(w.bar + 5, unsigned(WOS_NO_CONVERGENCE));
 }
 
+// ---------------------------------------------------------------------------
+// FP32 preconditioning of the sweeps without V.  FP64 is scarce on this part
+// (an FP64 warp instruction holds its sub-partition's unit for 64 cycles, 2
+// FMA/clk/SM against 128 in FP32), and the FP64 sweeps on X = R^T are the
+// bulk of a large factorisation.  So sweeps first run on an FP32 copy of X,
+// which only steers the angles; the product J of their rotations, made
+// orthogonal to FP64 rounding by two Newton-Schulz steps (Q = J (3 I -
+// J^T J) / 2, whose error is quadratic in that of J; Higham, "Functions of
+// Matrices", Sec. 8.3), gives the FP64 sweeps' start X Q: the same singular
+// values and left vectors as X (Q is orthogonal), with columns already
+// orthogonal to about FP32 precision, so quadratic convergence sets in at
+// once and a few FP64 sweeps remain (the mixed-precision preconditioned
+// one-sided Jacobi SVD of Higham, Tisseur, Webb & Zhang, with the
+// low-precision factor taken from Jacobi itself).  The results keep the FP64
+// sweeps' accuracy.
+//
+// The FP32 sweeps run in one thread-block cluster of kPc32Ctas CTAs per
+// problem, X in the CTAs' shared memory: block-cyclic one-sided Jacobi (the
+// columns in kPc32Blocks blocks of b, two per CTA; the blocks meet in the
+// round-robin order, every pair of columns once a sweep: the pairs inside
+// each block in the sweep's first block round, then those across the two
+// blocks), a warp per pair, the sub-rounds of a block round separated by
+// CTA barriers only and the block rounds by cluster barriers (the blocks
+// move through L2).  Across the blocks, warp w keeps column w of its CTA's
+// first block in registers and meets the second block's columns in turn,
+// which pass from warp to warp through shared memory.  Each CTA also forms
+// the 2b x 2b product G of a block round's rotations of its 2b columns; J is
+// rebuilt from those afterwards by pc32_replay_kernel (J <- J G for each
+// block round in order, rows of J independent), so the sweeps carry no V.
+// ---------------------------------------------------------------------------
+constexpr float kTol32 = 1e-6f;   // rotate when |cos| > kTol32 (FP32 dots)
+constexpr float kLast32 = 1e-3f;  // stop after a sweep with every |cos| <= this
+constexpr int kMaxSweeps32 = 16;  // then stop anyway (preconditioning only)
+constexpr int kPc32Ctas = 16;
+constexpr int kPc32Blocks = 2 * kPc32Ctas;
+constexpr int kPc32MaxB = 24;     // widest block: 768 columns
+constexpr int kPc32Chunks = 6;    // float4 rows a lane holds: columns of <= 768 rows
+
+struct Pc32Job {
+    float *X;         // m x n, column-major (FP32 copy of X), rotated in place
+    float *G;         // per sweep, block round and CTA: the 2b x 2b product of
+                      // its rotations (column-major)
+    unsigned *bar;    // [6] sweeps, [8..10] per sweep mod 3: a |cos| > kLast32
+    double *J;        // n x n: the product of the rotations (replay)
+    int m, n, b;      // b a multiple of 4, n <= kPc32Blocks b
+    int ms;           // m rounded up to 128: the shared-memory column stride
+};
+
+// Error-free product (Dekker): a b = p + e.
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+// cos and sin of the rotation with tangent t (|t| <= 1), each within about
+// half an FP32 ulp: c = (1 + t^2)^{-1/2} from the FP32 reciprocal square
+// root and one Newton step y (1 + (1 - u y^2) / 2), u = 1 + t^2 and the
+// residual 1 - u y^2 formed in float-float, then rounded; s = t c.
+__device__ __forceinline__ void accurate_cos_sin(float t, float &c, float &s)
+{
+    float p, pe;
+    two_prod(t, t, p, pe);
+    const float uh = 1.0f + p;             // |p| <= 1: fast two-sum
+    const float ul = ((1.0f - uh) + p) + pe;
+    const float y = rsqrtf(uh);
+    float q, qe, w, we;
+    two_prod(y, y, q, qe);
+    two_prod(uh, q, w, we);
+    const float res = (1.0f - w) - (we + fmaf(uh, qe, ul * q));  // 1 - u y^2
+    c = fmaf(0.5f * y, res, y);
+    s = t * c;
+}
+
+// Sums over the warp by xor butterflies: every lane gets the same sums.
+__device__ __forceinline__ void warp_sum3f(float &a, float &b, float &g)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(FULL, a, o);
+        b += __shfl_xor_sync(FULL, b, o);
+        g += __shfl_xor_sync(FULL, g, o);
+    }
+}
+
+// The rotation of a pair from al = |x|^2, be = |y|^2, ga = x.y: false when
+// it is not rotated (|cos| <= kTol32, or a zero or non-finite norm); *big
+// when |cos| > kLast32.  Rutishauser's smaller angle, t = sign(h) g /
+// (|h| + sqrt(h^2 + g^2)), h = (be - al) / 2, scale-free.
+__device__ __forceinline__ bool pc32_rotation(float al, float be, float ga, float &c, float &sn,
+                                              bool &big)
+{
+    c = 1.0f;
+    sn = 0.0f;
+    big = false;
+    if (!(al > 0.0f && be > 0.0f && al <= 3.0e38f && be <= 3.0e38f))
+        return false;
+    const float sc = 1.0f / fmaxf(al, be);  // al, be <= 1 and |ga| <= 1 after it
+    const float a1 = al * sc, b1 = be * sc, g1 = ga * sc;
+    const float ab = a1 * b1, g2 = g1 * g1;
+    if (!(g2 > (kTol32 * kTol32) * ab))
+        return false;
+    const float h = 0.5f * (b1 - a1);
+    const float t = copysignf(1.0f, h) * g1 / (fabsf(h) + sqrtf(fmaf(h, h, g2)));
+    accurate_cos_sin(t, c, sn);
+    big = g2 > (kLast32 * kLast32) * ab;
+    return true;
+}
+
+// Columns la, lb of G (b2 x b2, shared memory) rotated like the pair.
+__device__ __forceinline__ void pc32_rotate_g(float *G, int b2, int la, int lb, float c,
+                                              float sn, int lane)
+{
+    for (int k = lane; k < b2; k += 32) {
+        const float ga = G[la * b2 + k], gb = G[lb * b2 + k];
+        G[la * b2 + k] = fmaf(c, ga, -sn * gb);
+        G[lb * b2 + k] = fmaf(sn, ga, c * gb);
+    }
+}
+
+// One warp orthogonalises the FP32 columns x, y (ms rows, shared memory)
+// and rotates G's columns la, lb with them; returns whether |cos| > kLast32.
+__device__ __forceinline__ bool pc32_pair_smem(float *x, float *y, int ms, float *G, int b2,
+                                               int la, int lb, int lane)
+{
+    float al = 0.0f, be = 0.0f, ga = 0.0f;
+    for (int i = lane; i < ms; i += 32) {
+        const float xv = x[i], yv = y[i];
+        al = fmaf(xv, xv, al);
+        be = fmaf(yv, yv, be);
+        ga = fmaf(xv, yv, ga);
+    }
+    warp_sum3f(al, be, ga);
+    float c, sn;
+    bool big;
+    if (pc32_rotation(al, be, ga, c, sn, big)) {
+        for (int i = lane; i < ms; i += 32) {
+            const float xv = x[i], yv = y[i];
+            x[i] = fmaf(c, xv, -sn * yv);
+            y[i] = fmaf(sn, xv, c * yv);
+        }
+        pc32_rotate_g(G, b2, la, lb, c, sn, lane);
+    }
+    return big;
+}
+
+// Columns [blk b, blk b + b) of X between global memory (ld m, through L2)
+// and shared memory (ld ms; zeros past row m and past column n).
+__device__ void pc32_load(const Pc32Job &J, int blk, float *dst)
+{
+    const int m = J.m, ms = J.ms, b = J.b, c0 = blk * b;
+    const int nc = min(b, max(0, J.n - c0));
+    if ((m & 3) == 0) {
+        const int m4 = m / 4, ms4 = ms / 4;
+        for (int e = threadIdx.x; e < b * ms4; e += blockDim.x) {
+            const int c = e / ms4, i4 = e - c * ms4;
+            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (c < nc && i4 < m4)
+                v = __ldcg(reinterpret_cast<const float4 *>(J.X + size_t(c0 + c) * m) + i4);
+            reinterpret_cast<float4 *>(dst + size_t(c) * ms)[i4] = v;
+        }
+    } else {
+        for (int e = threadIdx.x; e < b * ms; e += blockDim.x) {
+            const int c = e / ms, i = e - c * ms;
+            dst[e] = (c < nc && i < m) ? __ldcg(J.X + size_t(c0 + c) * m + i) : 0.0f;
+        }
+    }
+}
+__device__ void pc32_store(const Pc32Job &J, int blk, const float *src)
+{
+    const int m = J.m, ms = J.ms, b = J.b, c0 = blk * b;
+    const int nc = min(b, max(0, J.n - c0));
+    if ((m & 3) == 0) {
+        const int m4 = m / 4, ms4 = ms / 4;
+        for (int e = threadIdx.x; e < nc * m4; e += blockDim.x) {
+            const int c = e / m4, i4 = e - c * m4;
+            __stcg(reinterpret_cast<float4 *>(J.X + size_t(c0 + c) * m) + i4,
+                   reinterpret_cast<const float4 *>(src + size_t(c) * ms)[i4]);
+        }
+    } else {
+        for (int e = threadIdx.x; e < nc * m; e += blockDim.x) {
+            const int c = e / m, i = e - c * m;
+            __stcg(J.X + size_t(c0 + c) * m + i, src[size_t(c) * ms + i]);
+        }
+    }
+}
+
 // The CTAs of a launch are split among np problems: problem p owns CTAs
 // [begin[p], begin[p + 1]) and synchronises only among them (its own
 // flags and barrier words).
@@ -859,6 +1046,195 @@ jacobi_group_kernel(const SvdWork *works, const int *begin, int np)
     const int p = problem_of(begin, np);
     const SvdWork w = works[p];
     jacobi_group_body<RPL>(w, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
+}
+
+// The FP32 sweeps: one cluster of kPc32Ctas CTAs per problem (blockIdx.x /
+// kPc32Ctas), b warps a CTA; dynamic shared memory: the two blocks (b ms
+// floats each) and G.  Lane l of a warp holds rows 128 k + 4 l .. + 3 of a
+// column.  Every CTA takes the same branches (cluster barriers).
+__global__ void __launch_bounds__(32 * kPc32MaxB, 1)
+pc32_cluster_kernel(const Pc32Job *jobs)
+{
+    cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
+    extern __shared__ float4 pc32_sm[];
+    const Pc32Job J = jobs[blockIdx.x / kPc32Ctas];
+    const int cta = int(cluster.block_rank());
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int b = J.b, ms = J.ms, b2 = 2 * b, nk = ms / 128;
+    float *R0 = reinterpret_cast<float *>(pc32_sm), *R1 = R0 + size_t(b) * ms;
+    float *G = R1 + size_t(b) * ms;
+    __shared__ int s_big;
+    unsigned *flags = J.bar + 8;
+    const float4 zero4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    for (int sweep = 0; sweep < kMaxSweeps32; ++sweep) {
+        if (cta == 0 && threadIdx.x == 0)
+            flags[(sweep + 1) % 3] = 0u;
+        if (threadIdx.x == 0)
+            s_big = 0;
+        bool big = false;
+        for (int r = 0; r < kPc32Blocks - 1; ++r) {
+            const int bA = rr_player(cta, r, kPc32Blocks);
+            const int bB = rr_player(kPc32Blocks - 1 - cta, r, kPc32Blocks);
+            pc32_load(J, bA, R0);
+            pc32_load(J, bB, R1);
+            for (int e = threadIdx.x; e < b2 * b2; e += blockDim.x)
+                G[e] = (e / b2 == e % b2) ? 1.0f : 0.0f;
+            __syncthreads();
+            if (r == 0) {
+                // pairs inside each block: round-robin on its b columns,
+                // warps [0, b/2) on block A and [b/2, b) on block B
+                const int hb = b / 2, w2 = wid < hb ? wid : wid - hb;
+                float *blk = wid < hb ? R0 : R1;
+                const int l0 = wid < hb ? 0 : b;
+                for (int u = 0; u < b - 1; ++u) {
+                    const int i = rr_player(w2, u, b), j = rr_player(b - 1 - w2, u, b);
+                    const int lo = min(i, j), hi = max(i, j);
+                    big |= pc32_pair_smem(blk + size_t(lo) * ms, blk + size_t(hi) * ms, ms, G, b2,
+                                          l0 + lo, l0 + hi, lane);
+                    __syncthreads();
+                }
+            }
+            // pairs across the blocks: A[w] (registers) with B[(w + u) mod b];
+            // slot k of the current buffer holds B[(k + u) mod b]
+            float4 xr[kPc32Chunks], yr[kPc32Chunks];
+#pragma unroll
+            for (int k = 0; k < kPc32Chunks; ++k)
+                xr[k] = k < nk ? reinterpret_cast<const float4 *>(R0 + size_t(wid) * ms)[32 * k + lane]
+                               : zero4;
+            __syncthreads();  // R0 is free: the next buffer
+            float *cur = R1, *nxt = R0;
+            for (int u = 0; u < b; ++u) {
+                const float4 *y4 = reinterpret_cast<const float4 *>(cur + size_t(wid) * ms);
+                float al = 0.0f, be = 0.0f, ga = 0.0f;
+#pragma unroll
+                for (int k = 0; k < kPc32Chunks; ++k) {
+                    yr[k] = k < nk ? y4[32 * k + lane] : zero4;
+                    al = fmaf(xr[k].x, xr[k].x, fmaf(xr[k].y, xr[k].y, fmaf(xr[k].z, xr[k].z, fmaf(xr[k].w, xr[k].w, al))));
+                    be = fmaf(yr[k].x, yr[k].x, fmaf(yr[k].y, yr[k].y, fmaf(yr[k].z, yr[k].z, fmaf(yr[k].w, yr[k].w, be))));
+                    ga = fmaf(xr[k].x, yr[k].x, fmaf(xr[k].y, yr[k].y, fmaf(xr[k].z, yr[k].z, fmaf(xr[k].w, yr[k].w, ga))));
+                }
+                warp_sum3f(al, be, ga);
+                float c, sn;
+                bool bg;
+                if (pc32_rotation(al, be, ga, c, sn, bg)) {
+                    big |= bg;
+#pragma unroll
+                    for (int k = 0; k < kPc32Chunks; ++k) {
+                        const float4 x = xr[k], y = yr[k];
+                        xr[k] = make_float4(fmaf(c, x.x, -sn * y.x), fmaf(c, x.y, -sn * y.y),
+                                            fmaf(c, x.z, -sn * y.z), fmaf(c, x.w, -sn * y.w));
+                        yr[k] = make_float4(fmaf(sn, x.x, c * y.x), fmaf(sn, x.y, c * y.y),
+                                            fmaf(sn, x.z, c * y.z), fmaf(sn, x.w, c * y.w));
+                    }
+                    pc32_rotate_g(G, b2, wid, b + (wid + u) % b, c, sn, lane);
+                }
+                float4 *o4 = reinterpret_cast<float4 *>(nxt + size_t((wid + b - 1) % b) * ms);
+#pragma unroll
+                for (int k = 0; k < kPc32Chunks; ++k)
+                    if (k < nk)
+                        o4[32 * k + lane] = yr[k];
+                __syncthreads();
+                float *t = cur;
+                cur = nxt;
+                nxt = t;
+            }
+            // b is even: cur is R1 again, B in order; A back into R0
+#pragma unroll
+            for (int k = 0; k < kPc32Chunks; ++k)
+                if (k < nk)
+                    reinterpret_cast<float4 *>(R0 + size_t(wid) * ms)[32 * k + lane] = xr[k];
+            __syncthreads();
+            pc32_store(J, bA, R0);
+            pc32_store(J, bB, R1);
+            float *gl = J.G + ((size_t(sweep) * (kPc32Blocks - 1) + r) * kPc32Ctas + cta) *
+                                  size_t(b2) * b2;
+            for (int e = threadIdx.x; e < b2 * b2; e += blockDim.x)
+                __stcg(gl + e, G[e]);
+            cluster.sync();  // the blocks' stores before any CTA loads them
+        }
+        if (big && lane == 0)
+            atomicOr(&s_big, 1);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_big)
+            atomicOr(flags + sweep % 3, 1u);
+        cluster.sync();
+        const bool done = *(volatile unsigned *)(flags + sweep % 3) == 0u;
+        if (cta == 0 && threadIdx.x == 0)
+            J.bar[6] = unsigned(sweep + 1);
+        if (done)
+            break;
+    }
+}
+
+// J = the product of the block rounds' G in their order: J <- J G_c on the
+// 2b columns of CTA c's two blocks, for every c of each block round.  Each
+// CTA owns kRpRows rows of J (independent) in shared memory, double
+// buffered; a thread forms output column j of one G for all kRpRows rows.
+constexpr int kRpRows = 8;
+
+// The CTAs of a launch serve np problems: problem p owns CTAs [begin[p],
+// begin[p + 1]).
+__global__ void __launch_bounds__(256)
+pc32_replay_kernel(const Pc32Job *jobs, const int *begin, int np)
+{
+    extern __shared__ float4 rp_smem[];
+    const int pb = problem_of(begin, np);
+    const Pc32Job J = jobs[pb];
+    const int n = J.n, b = J.b, b2 = 2 * b, L = kPc32Blocks * b;
+    float *cur = reinterpret_cast<float *>(rp_smem), *nxt = cur + size_t(kRpRows) * L;
+    const int r0 = (int(blockIdx.x) - begin[pb]) * kRpRows;
+    for (int e = threadIdx.x; e < kRpRows * L; e += blockDim.x) {
+        const int rr = e / L, j = e - rr * L;
+        cur[e] = (r0 + rr == j) ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    const int nsw = int(*(volatile unsigned *)(J.bar + 6));
+    const int tasks = kPc32Ctas * b2;
+    for (int z = 0; z < nsw; ++z)
+        for (int r = 0; r < kPc32Blocks - 1; ++r) {
+            const float *gr = J.G + (size_t(z) * (kPc32Blocks - 1) + r) * kPc32Ctas * size_t(b2) * b2;
+            for (int t = threadIdx.x; t < tasks; t += blockDim.x) {
+                const int c = t / b2, j = t - c * b2;
+                const int bA = rr_player(c, r, kPc32Blocks);
+                const int bB = rr_player(kPc32Blocks - 1 - c, r, kPc32Blocks);
+                const float4 *g4 = reinterpret_cast<const float4 *>(gr + (size_t(c) * b2 + j) * b2);
+                float acc[kRpRows];
+#pragma unroll
+                for (int rr = 0; rr < kRpRows; ++rr)
+                    acc[rr] = 0.0f;
+                for (int k4 = 0; k4 < b2 / 4; ++k4) {
+                    const float4 g = __ldcg(g4 + k4);
+                    const int k = 4 * k4;
+                    const int col = k < b ? bA * b + k : bB * b + (k - b);
+#pragma unroll
+                    for (int rr = 0; rr < kRpRows; ++rr) {
+                        const float4 v = *reinterpret_cast<const float4 *>(cur + size_t(rr) * L + col);
+                        acc[rr] = fmaf(v.x, g.x, fmaf(v.y, g.y, fmaf(v.z, g.z, fmaf(v.w, g.w, acc[rr]))));
+                    }
+                }
+                const int oc = j < b ? bA * b + j : bB * b + (j - b);
+#pragma unroll
+                for (int rr = 0; rr < kRpRows; ++rr)
+                    nxt[size_t(rr) * L + oc] = acc[rr];
+            }
+            __syncthreads();
+            float *tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+    for (int e = threadIdx.x; e < kRpRows * n; e += blockDim.x) {
+        const int rr = e / n, j = e - rr * n;
+        if (r0 + rr < n)
+            J.J[size_t(j) * n + r0 + rr] = double(cur[size_t(rr) * L + j]);  // J[i][j]
+    }
+}
+
+// X32 = X rounded to FP32 (m x n, both ld m).
+__global__ void to32_kernel(const double *X, size_t mn, float *X32)
+{
+    for (size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x; t < mn;
+         t += size_t(gridDim.x) * blockDim.x)
+        X32[t] = float(X[t]);
 }
 
 // Squared norms of the n columns (length m) of w.W into w.nrm, a warp per
@@ -903,13 +1279,16 @@ __global__ void permute_rows_kernel(const double *X, const int *perm, int n, dou
     }
 }
 
-// C = A B in FP64, column-major: A m x k (lda = m), B k x n (ldb = k), C m x n
-// (ldc = m).  64 x 64 tiles of C per block of 256 threads, 4 x 4 per thread,
-// k in steps of 16 through shared memory.
+// C = alpha op(A) B + beta D in FP64, column-major: op(A) = A (m x k, lda)
+// or A^T (A k x m, lda); B k x n (ldb); C and D m x n (ldc); no D when it is
+// null.  64 x 64 tiles of C per block of 256 threads, 4 x 4 per thread, k in
+// steps of 16 through shared memory.
 constexpr int kGemmTile = 64, kGemmK = 16;
 
+template <bool TA>
 __global__ void __launch_bounds__(256)
-dgemm_nn_kernel(int m, int n, int k, const double *A, const double *B, double *C)
+dgemm_kernel(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+             double *C, int ldc, double alpha, double beta, const double *D)
 {
     __shared__ double As[kGemmK][kGemmTile + 1];
     __shared__ double Bs[kGemmK][kGemmTile + 1];
@@ -918,14 +1297,20 @@ dgemm_nn_kernel(int m, int n, int k, const double *A, const double *B, double *C
     const int i0 = blockIdx.x * kGemmTile, j0 = blockIdx.y * kGemmTile;
     double acc[4][4] = {};
     for (int l0 = 0; l0 < k; l0 += kGemmK) {
-        // A tile: 64 rows x 16 columns; B tile: 16 rows x 64 columns
+        // A tile: 64 rows x 16 columns of op(A); B tile: 16 rows x 64 columns
         for (int e = tid; e < kGemmTile * kGemmK; e += 256) {
-            const int ii = e % kGemmTile, ll = e / kGemmTile;
-            const int gi = i0 + ii, gl = l0 + ll;
-            As[ll][ii] = (gi < m && gl < k) ? A[size_t(gl) * m + gi] : 0.0;
+            if (TA) {  // consecutive threads along k (A's columns are contiguous)
+                const int ll = e % kGemmK, ii = e / kGemmK;
+                const int gi = i0 + ii, gl = l0 + ll;
+                As[ll][ii] = (gi < m && gl < k) ? A[size_t(gi) * lda + gl] : 0.0;
+            } else {
+                const int ii = e % kGemmTile, ll = e / kGemmTile;
+                const int gi = i0 + ii, gl = l0 + ll;
+                As[ll][ii] = (gi < m && gl < k) ? A[size_t(gl) * lda + gi] : 0.0;
+            }
             const int lb = e % kGemmK, jj = e / kGemmK;
             const int gl2 = l0 + lb, gj = j0 + jj;
-            Bs[lb][jj] = (gl2 < k && gj < n) ? B[size_t(gj) * k + gl2] : 0.0;
+            Bs[lb][jj] = (gl2 < k && gj < n) ? B[size_t(gj) * ldb + gl2] : 0.0;
         }
         __syncthreads();
 #pragma unroll
@@ -949,9 +1334,23 @@ dgemm_nn_kernel(int m, int n, int k, const double *A, const double *B, double *C
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int gi = i0 + tx + 16 * u, gj = j0 + ty + 16 * v;
-            if (gi < m && gj < n)
-                C[size_t(gj) * m + gi] = acc[u][v];
+            if (gi < m && gj < n) {
+                const size_t o = size_t(gj) * ldc + gi;
+                C[o] = D ? fma(alpha, acc[u][v], beta * D[o]) : alpha * acc[u][v];
+            }
         }
+}
+
+void dgemm(cudaStream_t st, bool ta, int m, int n, int k, const double *A, int lda,
+           const double *B, int ldb, double *C, int ldc, double alpha = 1.0, double beta = 0.0,
+           const double *D = nullptr)
+{
+    const dim3 gg(unsigned((m + kGemmTile - 1) / kGemmTile),
+                  unsigned((n + kGemmTile - 1) / kGemmTile));
+    if (ta)
+        dgemm_kernel<true><<<gg, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, alpha, beta, D);
+    else
+        dgemm_kernel<false><<<gg, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, alpha, beta, D);
 }
 
 
@@ -1538,6 +1937,9 @@ struct SvdProb {
     Lists L;
     bool pre;
     bool lean;       // grid-wide Jacobi without V (more than 256 columns)
+    bool mixed;      // lean, with the FP32 preconditioning sweeps first
+    double *X0;      // mixed: X = R^T (the FP64 sweeps start from X Q)
+    Pc32Job pc;      // mixed: the FP32 sweeps' work
     int cl;          // cluster size of the cluster kernel, 0 = grid-wide kernels
     SvdWork w, wj;   // W itself, and the matrix Jacobi works on (W or X = R^T)
     QrWork q;
@@ -1586,6 +1988,90 @@ const void *jacobi_lean_kernel_rpl(int rpl)
     case 24: return reinterpret_cast<const void *>(&jacobi_lean_kernel<24>);
     default: return reinterpret_cast<const void *>(&jacobi_lean_kernel<32>);
     }
+}
+
+// Block width of the FP32 sweeps for n columns (a multiple of 4, n <= 32 b),
+// the shared-memory column stride for m rows, and the shared memory of their
+// two kernels.
+int pc32_b(int n)
+{
+    return 4 * ((n + 4 * kPc32Blocks - 1) / (4 * kPc32Blocks));
+}
+int pc32_ms(int m)
+{
+    return (m + 127) / 128 * 128;
+}
+size_t pc32_smem(int n)
+{
+    const size_t b = size_t(pc32_b(n));
+    return (2 * b * pc32_ms(n) + 4 * b * b) * sizeof(float);
+}
+size_t pc32_replay_smem(int n)
+{
+    return size_t(2) * kRpRows * kPc32Blocks * pc32_b(n) * sizeof(float);
+}
+
+// Opts kfn in to the most dynamic shared memory a CTA may have next to its
+// static shared memory (always the same value, so that concurrent callers
+// never see a smaller limit); false if that fails.
+bool allow_max_smem(const void *kfn, const wos_context *ctx)
+{
+    cudaFuncAttributes fa = {};
+    if (cudaFuncGetAttributes(&fa, kfn) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int dyn = wos::ctx_max_smem(ctx) - int(fa.sharedSizeBytes);
+    if (dyn <= 0 ||
+        cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// Whether the FP32 sweeps take an n-column problem: its blocks fit the
+// warps and the shared memory of a CTA, and a cluster of kPc32Ctas such CTAs
+// can be resident.
+bool pc32_fits(const wos_context *ctx, int n)
+{
+    if (n < 2 * kPc32Blocks || pc32_b(n) > kPc32MaxB || pc32_ms(n) > 128 * kPc32Chunks)
+        return false;
+    const void *ck = reinterpret_cast<const void *>(&pc32_cluster_kernel);
+    const void *rk = reinterpret_cast<const void *>(&pc32_replay_kernel);
+    cudaFuncAttributes fc = {}, fr = {};
+    if (cudaFuncGetAttributes(&fc, ck) != cudaSuccess ||
+        cudaFuncGetAttributes(&fr, rk) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const size_t room = size_t(wos::ctx_max_smem(ctx));
+    if (pc32_smem(n) + fc.sharedSizeBytes > room || pc32_replay_smem(n) + fr.sharedSizeBytes > room)
+        return false;
+    if (cudaFuncSetAttribute(ck, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess ||
+        !allow_max_smem(ck, ctx) || !allow_max_smem(rk, ctx)) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(kPc32Ctas));
+    cfg.blockDim = dim3(unsigned(32 * pc32_b(n)));
+    cfg.dynamicSmemBytes = pc32_smem(n);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = unsigned(kPc32Ctas);
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, pc32_cluster_kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return nc >= 1;
 }
 
 const void *jacobi_kernel_rpt(int rpt)
@@ -1703,7 +2189,10 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     std::vector<size_t> o_base(np);
     size_t off = 0;
     auto take = [&](size_t b) { size_t o = off; off += al(b); return o; };
-    struct Off { size_t W, V, sv, bar, ver, g1, X, L, tau, perm, cn, cn0, done, pv, pi, qbar, W0, nrm; };
+    struct Off {
+        size_t W, V, sv, bar, ver, g1, X, L, tau, perm, cn, cn0, done, pv, pi, qbar, W0, nrm;
+        size_t J, J2, X32, G, bar32;
+    };
     std::vector<Off> O(np);
     for (int p = 0; p < np; ++p) {
         SvdProb &b = P[p];
@@ -1714,6 +2203,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         b.pre = w.n >= kPrecondMinN;
         b.cl = wos::ctx_svd_path(ctx) == WOS_SVD_GRID ? 0 : cluster_fit(ctx, w.m, w.n, b.pre);
         b.lean = b.pre && !b.cl && w.n >= kLeanMinN;
+        b.mixed = b.lean && wos::ctx_svd_path(ctx) != WOS_SVD_FP64_SWEEPS && pc32_fits(ctx, w.n);
         b.qgrid = b.pre ? std::max(1, std::min({w.n, 2 * sms, qbudget})) : 0;
         Off &o = O[p];
         o.W = take(size_t(w.m) * w.n * 8);
@@ -1738,8 +2228,18 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
             o.W0 = take(size_t(w.m) * w.n * 8);
             o.nrm = take(size_t(w.n) * 8 * 3);  // norms, scales, inverse scales
         }
+        if (b.mixed) {
+            const size_t nn = size_t(w.n) * w.n, b2 = 2 * size_t(pc32_b(w.n));
+            o.J = take(nn * 8);
+            o.J2 = take(nn * 8);
+            o.X32 = take(nn * 4);
+            o.G = take(size_t(kMaxSweeps32) * (kPc32Blocks - 1) * kPc32Ctas * b2 * b2 * 4);
+            o.bar32 = take(64);
+        }
     }
     const size_t o_jrec = take(sizeof(SvdWork) * np), o_qrec = take(sizeof(QrWork) * np);
+    const size_t o_pcrec = take(sizeof(Pc32Job) * np);
+    const size_t o_rprec = take(sizeof(Pc32Job) * np + sizeof(int) * (np + 1));
     const size_t o_left = take(sizeof(LeftJob) * np);
     const size_t o_cjob = take(sizeof(ClusterJob) * np);
     const size_t o_begin = take(sizeof(int) * (2 * np + 2));
@@ -1769,6 +2269,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
                                               b.g1, b.M_1, b.nu, b.sigma, b.transposed);
         ++launches;
         b.W0 = nullptr;
+        b.X0 = nullptr;
         if (b.lean) {
             b.W0 = reinterpret_cast<double *>(base + o.W0);
             cudaMemcpyAsync(b.W0, w.W, size_t(w.m) * w.n * 8, cudaMemcpyDeviceToDevice, st);
@@ -1795,6 +2296,20 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
             b.wj.W = reinterpret_cast<double *>(base + o.X);
             b.wj.m = w.n;
             b.Lb = reinterpret_cast<double *>(base + o.L);
+            if (b.mixed) {  // X = R^T to X0; the FP64 sweeps work on X Q in J2's place
+                b.X0 = b.wj.W;
+                b.wj.W = reinterpret_cast<double *>(base + o.J2);
+                Pc32Job &v = b.pc;
+                v.X = reinterpret_cast<float *>(base + o.X32);
+                v.G = reinterpret_cast<float *>(base + o.G);
+                v.bar = reinterpret_cast<unsigned *>(base + o.bar32);
+                v.J = reinterpret_cast<double *>(base + o.J);
+                v.m = w.n;
+                v.n = w.n;
+                v.b = pc32_b(w.n);
+                v.ms = pc32_ms(w.n);
+                cudaMemsetAsync(v.bar, 0, 64, st);
+            }
             qrecs[p] = q;
             qgrids[p] = b.qgrid;
             pidx.push_back(p);
@@ -1829,7 +2344,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     if (jacobi_events && jacobi_events[0])
         cudaEventRecord(static_cast<cudaEvent_t>(jacobi_events[0]), st);
     // cluster kernel: one launch per cluster size, one cluster per problem
-    size_t cjobs_used = 0;
+    size_t cjobs_used = 0, pcjobs_used = 0;
     for (int CL = 1; e == cudaSuccess && CL <= kClMaxCtas; ++CL) {
         std::vector<ClusterJob> jobs;
         size_t smem = 0;
@@ -1870,12 +2385,83 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
                           qidx, qgrids, qrecs, dq, dbegin, st, &launches);
     for (int p = 0; e == cudaSuccess && p < np; ++p)
         if (P[p].pre && !P[p].cl) {
-            build_x_kernel<<<sms * 4, 256, 0, st>>>(P[p].q, P[p].wj.W, P[p].wj.Vw);
+            SvdProb &b = P[p];
+            build_x_kernel<<<sms * 4, 256, 0, st>>>(b.q, b.mixed ? b.X0 : b.wj.W, b.wj.Vw);
             ++launches;
-            if (P[p].lean) {  // the squared column norms the lean sweeps carry
-                column_sq_norms_kernel<<<sms * 2, 256, 0, st>>>(P[p].wj);
+            if (b.mixed) {
+                to32_kernel<<<sms * 4, 256, 0, st>>>(b.X0, size_t(b.pc.m) * b.pc.n, b.pc.X);
+                ++launches;
+            } else if (b.lean) {  // the squared column norms the lean sweeps carry
+                column_sq_norms_kernel<<<sms * 2, 256, 0, st>>>(b.wj);
                 ++launches;
             }
+        }
+    // FP32 preconditioning sweeps: one cluster per problem, one launch per
+    // block width; then J from each problem's log
+    for (int bw = 4; e == cudaSuccess && bw <= kPc32MaxB; bw += 4) {
+        std::vector<Pc32Job> jobs;
+        int nmax = 0;
+        for (int p = 0; p < np; ++p)
+            if (P[p].mixed && P[p].pc.b == bw) {
+                jobs.push_back(P[p].pc);
+                nmax = std::max(nmax, P[p].pc.n);
+            }
+        if (jobs.empty())
+            continue;
+        Pc32Job *dpc = reinterpret_cast<Pc32Job *>(base + o_pcrec) + pcjobs_used;
+        pcjobs_used += jobs.size();
+        cudaMemcpyAsync(dpc, jobs.data(), sizeof(Pc32Job) * jobs.size(), cudaMemcpyHostToDevice,
+                        st);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(kPc32Ctas * int(jobs.size())));
+        cfg.blockDim = dim3(unsigned(32 * bw));
+        cfg.dynamicSmemBytes = pc32_smem(nmax);
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = unsigned(kPc32Ctas);
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, pc32_cluster_kernel, const_cast<const Pc32Job *>(dpc));
+        ++launches;
+    }
+    if (e == cudaSuccess) {  // every problem's J in one launch
+        std::vector<Pc32Job> jobs;
+        std::vector<int> begin(1, 0);
+        size_t smem = 0;
+        for (int p = 0; p < np; ++p)
+            if (P[p].mixed) {
+                jobs.push_back(P[p].pc);
+                begin.push_back(begin.back() + (P[p].pc.n + kRpRows - 1) / kRpRows);
+                smem = std::max(smem, pc32_replay_smem(P[p].pc.n));
+            }
+        if (!jobs.empty()) {
+            Pc32Job *dj3 = reinterpret_cast<Pc32Job *>(base + o_rprec);
+            int *db3 = reinterpret_cast<int *>(dj3 + np);
+            cudaMemcpyAsync(dj3, jobs.data(), sizeof(Pc32Job) * jobs.size(),
+                            cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(db3, begin.data(), sizeof(int) * begin.size(), cudaMemcpyHostToDevice,
+                            st);
+            pc32_replay_kernel<<<begin.back(), 256, smem, st>>>(dj3, db3, int(jobs.size()));
+            ++launches;
+        }
+    }
+    // two Newton-Schulz steps Q <- Q (3 I - Q^T Q) / 2 from Q = J, and the
+    // FP64 sweeps' start X Q (M in V's place: free until the left vectors)
+    for (int p = 0; e == cudaSuccess && p < np; ++p)
+        if (P[p].mixed) {
+            SvdProb &b = P[p];
+            const int n = b.w.n;
+            double *J = b.pc.J, *J2 = b.wj.W, *M = b.wj.Vw;
+            dgemm(st, true, n, n, n, J, n, J, n, M, n);                   // M = J^T J
+            dgemm(st, false, n, n, n, J, n, M, n, J2, n, -0.5, 1.5, J);   // J2 = 1.5 J - 0.5 J M
+            dgemm(st, true, n, n, n, J2, n, J2, n, M, n);                 // M = J2^T J2
+            dgemm(st, false, n, n, n, J2, n, M, n, J, n, -0.5, 1.5, J2);  // J = 1.5 J2 - 0.5 J2 M
+            dgemm(st, false, n, n, n, b.X0, n, J, n, J2, n);              // X Q
+            column_sq_norms_kernel<<<sms * 2, 256, 0, st>>>(b.wj);
+            launches += 6;
         }
     // Jacobi: one cooperative launch per class of rows per thread (and per
     // group of co-resident problems); the CTAs are shared in proportion to
@@ -1936,9 +2522,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
             const int m = b.w.m, n = b.w.n;
             fold_scales_kernel<<<sms * 4, 256, 0, st>>>(b.wj);  // X = d_j xt_j
             permute_rows_kernel<<<sms * 4, 256, 0, st>>>(b.wj.W, b.q.perm, n, b.wj.Vw);
-            dim3 gg(unsigned((m + kGemmTile - 1) / kGemmTile),
-                    unsigned((n + kGemmTile - 1) / kGemmTile));
-            dgemm_nn_kernel<<<gg, 256, 0, st>>>(m, n, n, b.W0, b.wj.Vw, b.Lb);
+            dgemm(st, false, m, n, n, b.W0, m, b.wj.Vw, n, b.Lb, m);
             launches += 3;
         }
     if (e == cudaSuccess) {  // left vectors of every other preconditioned problem

@@ -612,7 +612,7 @@ def wos_autotune_reset(ctx: Context) -> None:
     _check(load().wos_autotune_reset(ctx.h), "wos_autotune_reset", False)
 
 
-SVD_AUTO, SVD_GRID, SVD_CLUSTER = 0, 1, 2
+SVD_AUTO, SVD_GRID, SVD_CLUSTER, SVD_FP64_SWEEPS = 0, 1, 2, 3
 PIPES = ("ffma", "mufu", "imad_wide", "lop3", "dfma", "issue")
 
 
@@ -626,7 +626,9 @@ def wos_measure_pipes(ctx: Context, stream=None) -> dict:
 
 def wos_set_svd_path(ctx: Context, path: int) -> None:
     """Kernels that factor SVD problems: SVD_AUTO (cluster kernel when the
-    worked matrix fits it), SVD_GRID (grid-wide kernels) or SVD_CLUSTER."""
+    worked matrix fits it), SVD_GRID (grid-wide kernels), SVD_CLUSTER, or
+    SVD_FP64_SWEEPS (as SVD_AUTO without the FP32 preconditioning sweeps of
+    problems of more than 256 columns)."""
     _check(load().wos_set_svd_path(ctx.h, int(path)), "wos_set_svd_path", False)
 
 

@@ -296,8 +296,50 @@ def test_degenerate_shapes(shape, svd_path):
     np.testing.assert_allclose(V.T @ V, np.eye(k), atol=1e-12)
 
 
+@pytest.mark.parametrize("shape", [(1024, 1536, 768), (300, 900, 600), (600, 900, 300),
+                                   (520, 800, 257)])
+def test_fp32_preconditioned_sweeps_agree_with_fp64_sweeps(shape):
+    """Problems of more than 256 columns: the default path (FP32 sweeps on X
+    in a thread-block cluster, their rotations replayed into J, two
+    Newton-Schulz steps in FP64, then FP64 sweeps from X Q) and FP64 sweeps
+    alone both match LAPACK's singular values of the same FP64 matrix (the
+    default path to 1e-13 relative, every value; FP64 sweeps alone, whose
+    ten-odd sweeps of scaled rotations round more, to 1e-12), give the same
+    singular subspaces at gaps and orthonormal vectors; the preconditioned
+    FP64 sweeps are at most half as many."""
+    M_D, M_tot, M_1 = shape
+    N = 100_000
+    C = W.synthetic_counts(M_D, M_tot, N, seed=M_D + 3 * M_1)
+    g1 = np.zeros(M_tot, np.uint8)
+    g1[:M_1] = 1
+    Ct = torch.as_tensor(C.astype(np.int32), device=DEV)
+    sg = torch.full((M_tot,), 2 * np.pi / M_tot, dtype=torch.float64, device=DEV)
+    c = ctx()
+    out = {}
+    for path in (wos.SVD_FP64_SWEEPS, wos.SVD_AUTO):
+        wos.wos_set_svd_path(c, path)
+        U, S, V, sw = wos.wos_op_svd(c, Ct, N, g1, sg)
+        out[path] = (U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy(), sw)
+    wos.wos_set_svd_path(c, wos.SVD_AUTO)
+    (U0, s0, V0, sw0), (U1, s1, V1, sw1) = out[wos.SVD_FP64_SWEEPS], out[wos.SVD_AUTO]
+    B = O.operator_B(C, N, g1, np.full(M_D, 1 / np.sqrt(M_D)), np.full(M_tot, 2 * np.pi / M_tot))
+    s_lapack = np.linalg.svd(B, compute_uv=False)
+    assert np.max(np.abs(s1 / s_lapack - 1)) <= 1e-13, np.max(np.abs(s1 / s_lapack - 1))
+    assert np.max(np.abs(s0 / s_lapack - 1)) <= 1e-12, np.max(np.abs(s0 / s_lapack - 1))
+    assert 2 * sw1 <= sw0, (sw0, sw1)
+    k = len(s1)
+    for U in (U1, V1):
+        G = U.T @ U
+        tol = _orth_tol(s1)
+        assert np.all(np.abs(G - np.eye(k)) <= tol), np.max(np.abs(G - np.eye(k)) / tol)
+    for r in _gaps(s0, 40):
+        for A, B2 in ((U0, U1), (V0, V1)):
+            P0, P1 = A[:, :r] @ A[:, :r].T, B2[:, :r] @ B2[:, :r].T
+            assert np.abs(P0 - P1).max() <= 1e-9, r
+
+
 def test_svd_path_setting_is_checked():
-    for bad in (-1, 3, 100):
+    for bad in (-1, 4, 100):
         with pytest.raises(wos.WosError) as e:
             wos.wos_set_svd_path(ctx(), bad)
         assert e.value.code == 1
