@@ -32,9 +32,9 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr double kTol = 1e-15;
 // A sweep whose pairs all had |cos| = |w_p . w_q| / (|w_p| |w_q|) <= kLast
 // rotated by angles that small; the cyclic sweep's quadratic convergence
-// leaves every cosine at O(kLast^2) = 1e-18 after it, below kTol, so no
+// leaves every cosine at O(kLast^2) = 1e-16 after it, below kTol, so no
 // verifying sweep without rotations follows it.
-constexpr double kLast = 1e-9;
+constexpr double kLast = 1e-8;
 constexpr int kMaxSweeps = 80;
 constexpr int kPairThreads = 128;
 static_assert(kPairThreads == 128, "the partial sums below assume four warps");
@@ -1096,7 +1096,7 @@ pc32_cluster_kernel(const Pc32Job *jobs)
             }
             // pairs across the blocks: A[w] (registers) with B[(w + u) mod b];
             // slot k of the current buffer holds B[(k + u) mod b]
-            float4 xr[kPc32Chunks], yr[kPc32Chunks];
+            float4 xr[kPc32Chunks];
 #pragma unroll
             for (int k = 0; k < kPc32Chunks; ++k)
                 xr[k] = k < nk ? reinterpret_cast<const float4 *>(R0 + size_t(wid) * ms)[32 * k + lane]
@@ -1108,31 +1108,35 @@ pc32_cluster_kernel(const Pc32Job *jobs)
                 float al = 0.0f, be = 0.0f, ga = 0.0f;
 #pragma unroll
                 for (int k = 0; k < kPc32Chunks; ++k) {
-                    yr[k] = k < nk ? y4[32 * k + lane] : zero4;
+                    const float4 y = k < nk ? y4[32 * k + lane] : zero4;
                     al = fmaf(xr[k].x, xr[k].x, fmaf(xr[k].y, xr[k].y, fmaf(xr[k].z, xr[k].z, fmaf(xr[k].w, xr[k].w, al))));
-                    be = fmaf(yr[k].x, yr[k].x, fmaf(yr[k].y, yr[k].y, fmaf(yr[k].z, yr[k].z, fmaf(yr[k].w, yr[k].w, be))));
-                    ga = fmaf(xr[k].x, yr[k].x, fmaf(xr[k].y, yr[k].y, fmaf(xr[k].z, yr[k].z, fmaf(xr[k].w, yr[k].w, ga))));
+                    be = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, be))));
+                    ga = fmaf(xr[k].x, y.x, fmaf(xr[k].y, y.y, fmaf(xr[k].z, y.z, fmaf(xr[k].w, y.w, ga))));
                 }
                 warp_sum3f(al, be, ga);
                 float c, sn;
                 bool bg;
-                if (pc32_rotation(al, be, ga, c, sn, bg)) {
-                    big |= bg;
-#pragma unroll
-                    for (int k = 0; k < kPc32Chunks; ++k) {
-                        const float4 x = xr[k], y = yr[k];
-                        xr[k] = make_float4(fmaf(c, x.x, -sn * y.x), fmaf(c, x.y, -sn * y.y),
-                                            fmaf(c, x.z, -sn * y.z), fmaf(c, x.w, -sn * y.w));
-                        yr[k] = make_float4(fmaf(sn, x.x, c * y.x), fmaf(sn, x.y, c * y.y),
-                                            fmaf(sn, x.z, c * y.z), fmaf(sn, x.w, c * y.w));
-                    }
-                    pc32_rotate_g(G, b2, wid, b + (wid + u) % b, c, sn, lane);
-                }
+                const bool rot = pc32_rotation(al, be, ga, c, sn, bg);
+                big |= bg;
+                // y again from shared memory (not held across the rotation's
+                // arithmetic: registers), rotated on its way to the next warp
                 float4 *o4 = reinterpret_cast<float4 *>(nxt + size_t((wid + b - 1) % b) * ms);
 #pragma unroll
                 for (int k = 0; k < kPc32Chunks; ++k)
-                    if (k < nk)
-                        o4[32 * k + lane] = yr[k];
+                    if (k < nk) {
+                        const float4 x = xr[k], y = y4[32 * k + lane];
+                        if (rot) {
+                            xr[k] = make_float4(fmaf(c, x.x, -sn * y.x), fmaf(c, x.y, -sn * y.y),
+                                                fmaf(c, x.z, -sn * y.z), fmaf(c, x.w, -sn * y.w));
+                            o4[32 * k + lane] =
+                                make_float4(fmaf(sn, x.x, c * y.x), fmaf(sn, x.y, c * y.y),
+                                            fmaf(sn, x.z, c * y.z), fmaf(sn, x.w, c * y.w));
+                        } else {
+                            o4[32 * k + lane] = y;
+                        }
+                    }
+                if (rot)
+                    pc32_rotate_g(G, b2, wid, b + (wid + u) % b, c, sn, lane);
                 __syncthreads();
                 float *t = cur;
                 cur = nxt;
@@ -1282,14 +1286,18 @@ __global__ void permute_rows_kernel(const double *X, const int *perm, int n, dou
 // C = alpha op(A) B + beta D in FP64, column-major: op(A) = A (m x k, lda)
 // or A^T (A k x m, lda); B k x n (ldb); C and D m x n (ldc); no D when it is
 // null.  64 x 64 tiles of C per block of 256 threads, 4 x 4 per thread, k in
-// steps of 16 through shared memory.
+// steps of 16 through shared memory.  SYM (C = A^T A, m = n): only the tiles
+// on and above the diagonal, each written to both triangles (element (i, j)
+// and (j, i) are the same products in the same order).
 constexpr int kGemmTile = 64, kGemmK = 16;
 
-template <bool TA>
+template <bool TA, bool SYM = false>
 __global__ void __launch_bounds__(256)
 dgemm_kernel(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
              double *C, int ldc, double alpha, double beta, const double *D)
 {
+    if (SYM && blockIdx.x > blockIdx.y)
+        return;
     __shared__ double As[kGemmK][kGemmTile + 1];
     __shared__ double Bs[kGemmK][kGemmTile + 1];
     const int tid = threadIdx.x;
@@ -1337,6 +1345,63 @@ dgemm_kernel(int m, int n, int k, const double *A, int lda, const double *B, int
             if (gi < m && gj < n) {
                 const size_t o = size_t(gj) * ldc + gi;
                 C[o] = D ? fma(alpha, acc[u][v], beta * D[o]) : alpha * acc[u][v];
+                if (SYM)
+                    C[size_t(gi) * ldc + gj] = C[o];
+            }
+        }
+}
+
+// C = D + alpha fl32(A) fl32(B - I) with FP32 products and sums (A, B, C, D
+// FP64, n x n, column-major, ld n; C may not alias A or B): the correction
+// terms of the Newton-Schulz steps, Q (Q^T Q - I), whose size (1e-4 and
+// below) makes FP32's relative rounding negligible next to FP64's.  The
+// tiling of dgemm_kernel.
+__global__ void __launch_bounds__(256)
+ns_correction_kernel(int n, const double *A, const double *B, double *C, double alpha,
+                     const double *D)
+{
+    __shared__ float As[kGemmK][kGemmTile + 1];
+    __shared__ float Bs[kGemmK][kGemmTile + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int i0 = blockIdx.x * kGemmTile, j0 = blockIdx.y * kGemmTile;
+    float acc[4][4] = {};
+    for (int l0 = 0; l0 < n; l0 += kGemmK) {
+        for (int e = tid; e < kGemmTile * kGemmK; e += 256) {
+            const int ii = e % kGemmTile, ll = e / kGemmTile;
+            const int gi = i0 + ii, gl = l0 + ll;
+            As[ll][ii] = (gi < n && gl < n) ? float(A[size_t(gl) * n + gi]) : 0.0f;
+            const int lb = e % kGemmK, jj = e / kGemmK;
+            const int gl2 = l0 + lb, gj = j0 + jj;
+            Bs[lb][jj] = (gl2 < n && gj < n)
+                             ? float(B[size_t(gj) * n + gl2] - (gl2 == gj ? 1.0 : 0.0))
+                             : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ll = 0; ll < kGemmK; ++ll) {
+            float a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = As[ll][tx + 16 * u];
+                b[u] = Bs[ll][ty + 16 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int gi = i0 + tx + 16 * u, gj = j0 + ty + 16 * v;
+            if (gi < n && gj < n) {
+                const size_t o = size_t(gj) * n + gi;
+                C[o] = fma(alpha, double(acc[u][v]), D[o]);
             }
         }
 }
@@ -1351,6 +1416,21 @@ void dgemm(cudaStream_t st, bool ta, int m, int n, int k, const double *A, int l
         dgemm_kernel<true><<<gg, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, alpha, beta, D);
     else
         dgemm_kernel<false><<<gg, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, alpha, beta, D);
+}
+
+// M = A^T A (n x n from k x n A), both triangles.
+void dsyrk(cudaStream_t st, int n, int k, const double *A, double *M)
+{
+    const dim3 gg(unsigned((n + kGemmTile - 1) / kGemmTile), unsigned((n + kGemmTile - 1) / kGemmTile));
+    dgemm_kernel<true, true><<<gg, 256, 0, st>>>(n, n, k, A, k, A, k, M, n, 1.0, 0.0, nullptr);
+}
+
+// C = D - (1/2) fl32(A) fl32(B - I), n x n.
+void ns_correction(cudaStream_t st, int n, const double *A, const double *B, const double *D,
+                   double *C)
+{
+    const dim3 gg(unsigned((n + kGemmTile - 1) / kGemmTile), unsigned((n + kGemmTile - 1) / kGemmTile));
+    ns_correction_kernel<<<gg, 256, 0, st>>>(n, A, B, C, -0.5, D);
 }
 
 
@@ -2448,18 +2528,23 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
             ++launches;
         }
     }
-    // two Newton-Schulz steps Q <- Q (3 I - Q^T Q) / 2 from Q = J, and the
-    // FP64 sweeps' start X Q (M in V's place: free until the left vectors)
+    // two Newton-Schulz steps Q <- Q - Q (Q^T Q - I) / 2 from Q = J, then the
+    // FP64 sweeps' start X Q: Q^T Q in FP64 (its departure from I, about
+    // 1e-4 and then 1e-8, must be exact to FP64 rounding), the correction
+    // products in FP32 (their rounding, scaled by that departure, leaves Q
+    // orthogonal to about 1e-15), X Q in FP64 (a right-multiplicative
+    // rounding: relative accuracy kept).  M sits in V's place (free until
+    // the left vectors); J2 holds Q after one step, then X Q.
     for (int p = 0; e == cudaSuccess && p < np; ++p)
         if (P[p].mixed) {
             SvdProb &b = P[p];
             const int n = b.w.n;
             double *J = b.pc.J, *J2 = b.wj.W, *M = b.wj.Vw;
-            dgemm(st, true, n, n, n, J, n, J, n, M, n);                   // M = J^T J
-            dgemm(st, false, n, n, n, J, n, M, n, J2, n, -0.5, 1.5, J);   // J2 = 1.5 J - 0.5 J M
-            dgemm(st, true, n, n, n, J2, n, J2, n, M, n);                 // M = J2^T J2
-            dgemm(st, false, n, n, n, J2, n, M, n, J, n, -0.5, 1.5, J2);  // J = 1.5 J2 - 0.5 J2 M
-            dgemm(st, false, n, n, n, b.X0, n, J, n, J2, n);              // X Q
+            dsyrk(st, n, n, J, M);                            // M = J^T J
+            ns_correction(st, n, J, M, J, J2);                // J2 = J - J (M - I) / 2
+            dsyrk(st, n, n, J2, M);                           // M = J2^T J2
+            ns_correction(st, n, J2, M, J2, J);               // Q = J2 - J2 (M - I) / 2
+            dgemm(st, false, n, n, n, b.X0, n, J, n, J2, n);  // X Q
             column_sq_norms_kernel<<<sms * 2, 256, 0, st>>>(b.wj);
             launches += 6;
         }
