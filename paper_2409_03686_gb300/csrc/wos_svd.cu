@@ -1741,6 +1741,142 @@ qrcp_kernel(const QrWork *works, const int *begin, int np)
     qrcp_body(q, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
 }
 
+// Householder QR without pivoting of the columns taken in a fixed order
+// (perm: decreasing norm, sort_columns_kernel), for the problems whose
+// sweeps start from FP32 ones: those sweeps, not the pivoting, precondition
+// the FP64 sweeps, and the singular values' relative accuracy rests on the
+// column-wise backward stability of Householder QR, pivoted or not.  With
+// the order fixed there is no pivot search, so no grid-wide step per
+// column: CTA b owns positions k = b (mod G); the owner of position k forms
+// reflector k (xLARFG, as qrcp_body) once the k reflectors before it have
+// reached its column, and publishes it with a flag (done[k]); every CTA
+// applies the reflectors in order to its later columns, the owner of
+// position k + 1 first to that column, so that the next reflector follows
+// after one flag latency, one column update and one reflector (look-ahead).
+// The waits are bounded (WOS_DEVICE_TIMEOUT).
+__device__ void qrs_reflect(const QrWork &q, int k, double *red)
+{
+    const int tid = threadIdx.x, m = q.m;
+    double *c = q.A + size_t(q.perm[k]) * m;
+    double xn2 = 0.0;
+    for (int i = k + 1 + tid; i < m; i += blockDim.x)
+        xn2 = fma(c[i], c[i], xn2);
+    xn2 = block_sum(xn2, red);
+    const double alpha = c[k];
+    if (xn2 > 0.0 && (tid == 0 || tid == 32)) {
+        const double bt = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
+        if (tid == 0) {
+            red[33] = bt;
+            red[34] = (bt - alpha) / bt;
+        } else {
+            red[35] = 1.0 / (alpha - bt);
+        }
+    }
+    __syncthreads();
+    if (xn2 > 0.0) {
+        const double scal = red[35];
+        for (int i = k + 1 + tid; i < m; i += blockDim.x)
+            c[i] *= scal;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        c[k] = xn2 > 0.0 ? red[33] : alpha;
+        q.tau[k] = xn2 > 0.0 ? red[34] : 0.0;
+        __threadfence();  // the block's column writes (ordered by the barrier above)
+        st_relaxed(reinterpret_cast<unsigned *>(q.done) + k, 1u);
+    }
+    __syncthreads();
+}
+
+// Column at position pos <- H_k (column): w = c_k + v . c (v_k = 1), c -= tau w v.
+__device__ void qrs_apply(const QrWork &q, int k, int pos, double tau, double *red)
+{
+    const int tid = threadIdx.x, m = q.m;
+    if (tau == 0.0)
+        return;
+    const double *v = q.A + size_t(q.perm[k]) * m;
+    double *c = q.A + size_t(q.perm[pos]) * m;
+    double w = 0.0;
+    for (int i = k + 1 + tid; i < m; i += blockDim.x)
+        w = fma(__ldcg(v + i), c[i], w);
+    w = block_sum(w, red) + c[k];
+    const double tw = tau * w;
+    for (int i = k + 1 + tid; i < m; i += blockDim.x)
+        c[i] = fma(-tw, __ldcg(v + i), c[i]);
+    __syncthreads();
+    if (tid == 0)
+        c[k] -= tw;
+    __syncthreads();
+}
+
+__device__ void qrs_body(const QrWork &q, const int b, const int G)
+{
+    __shared__ double red[36];
+    __shared__ int go;
+    const int n = q.n;
+    const unsigned *flag = reinterpret_cast<const unsigned *>(q.done);
+    if (b == 0)
+        qrs_reflect(q, 0, red);
+    for (int k = 0; k < n - 1; ++k) {
+        if (k % G != b) {
+            if (threadIdx.x == 0)
+                go = wait_version(flag, k, 1u, q.bar + 5);
+            __syncthreads();
+            if (!go)
+                return;
+        }
+        const double tau = __ldcg(q.tau + k);
+        int pos = k + 1 + ((b - (k + 1)) % G + G) % G;  // this CTA's first position > k
+        if (pos == k + 1) {  // look-ahead: the next reflector first
+            qrs_apply(q, k, pos, tau, red);
+            qrs_reflect(q, k + 1, red);
+            pos += G;
+        }
+        for (; pos < n; pos += G)
+            qrs_apply(q, k, pos, tau, red);
+    }
+}
+
+__global__ void __launch_bounds__(kQrThreads)
+qrs_kernel(const QrWork *works, const int *begin, int np)
+{
+    const int p = problem_of(begin, np);
+    const QrWork q = works[p];
+    qrs_body(q, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
+}
+
+// perm = the columns of A (m x n) in decreasing order of their squared norms
+// cn (lowest index on ties): a thread per column counts the columns before it.
+__global__ void sort_columns_kernel(const QrWork q)
+{
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q.n; j += gridDim.x * blockDim.x) {
+        const double v = q.cn[j];
+        int rank = 0;
+        for (int i = 0; i < q.n; ++i) {
+            const double u = q.cn[i];
+            rank += (u > v || (u == v && i < j)) ? 1 : 0;
+        }
+        q.perm[rank] = j;
+    }
+}
+
+// Squared norms of A's n columns (length m) into cn, a warp per column.
+__global__ void qr_col_norms_kernel(const QrWork q)
+{
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int j = gw; j < q.n; j += nw) {
+        const double *c = q.A + size_t(j) * q.m;
+        double s = 0.0;
+        for (int i = lane; i < q.m; i += 32)
+            s = fma(c[i], c[i], s);
+        s = warp_sum(s);
+        if (lane == 0)
+            q.cn[j] = s;
+    }
+}
+
 // X = R^T (n x n column-major): column i of X = row i of R, R[i][j] =
 // A[i][perm[j]] for j >= i; V_X = I.
 __global__ void build_x_kernel(const QrWork q, double *X, double *Vx)
@@ -2322,7 +2458,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     const size_t o_rprec = take(sizeof(Pc32Job) * np + sizeof(int) * (np + 1));
     const size_t o_left = take(sizeof(LeftJob) * np);
     const size_t o_cjob = take(sizeof(ClusterJob) * np);
-    const size_t o_begin = take(sizeof(int) * (2 * np + 2));
+    const size_t o_begin = take(sizeof(int) * (2 * np + 3));
     char *base = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&base), off, st);
     if (e != cudaSuccess)
@@ -2460,9 +2596,26 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         e = cudaLaunchKernelEx(&cfg, svd_cluster_kernel, const_cast<const ClusterJob *>(dj2), CL);
         ++launches;
     }
-    if (e == cudaSuccess && !qidx.empty())
-        e = launch_groups(reinterpret_cast<const void *>(qrcp_kernel), kQrThreads, qbudget,
-                          qidx, qgrids, qrecs, dq, dbegin, st, &launches);
+    {
+        // the FP32-preconditioned problems: column order by norm, QR without
+        // pivoting; the others: QR with column pivoting
+        std::vector<int> piv, srt;
+        for (int p : qidx)
+            (P[p].mixed ? srt : piv).push_back(p);
+        for (int p = 0; e == cudaSuccess && p < int(srt.size()); ++p) {
+            const QrWork &q = P[srt[p]].q;
+            qr_col_norms_kernel<<<sms * 2, 256, 0, st>>>(q);
+            sort_columns_kernel<<<(q.n + 255) / 256, 256, 0, st>>>(q);
+            launches += 2;
+        }
+        if (e == cudaSuccess && !srt.empty())
+            e = launch_groups(reinterpret_cast<const void *>(qrs_kernel), kQrThreads, qbudget,
+                              srt, qgrids, qrecs, dq, dbegin, st, &launches);
+        if (e == cudaSuccess && !piv.empty())
+            e = launch_groups(reinterpret_cast<const void *>(qrcp_kernel), kQrThreads, qbudget,
+                              piv, qgrids, qrecs, dq + srt.size(), dbegin + srt.size() + 1, st,
+                              &launches);
+    }
     for (int p = 0; e == cudaSuccess && p < np; ++p)
         if (P[p].pre && !P[p].cl) {
             SvdProb &b = P[p];
@@ -2593,7 +2746,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         if (want > budget)
             for (int p : idx)
                 jgrids[p] = std::max(1, int(jgrids[p] * (long long)budget / want));
-        e = launch_groups(jk, threads, budget, idx, jgrids, jrecs, dj, dbegin + np + 1, st,
+        e = launch_groups(jk, threads, budget, idx, jgrids, jrecs, dj, dbegin + np + 2, st,
                           &launches);
     }
     if (jacobi_events && jacobi_events[1])
