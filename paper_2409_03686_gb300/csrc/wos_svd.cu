@@ -835,26 +835,24 @@ __device__ void jacobi_body(const SvdWork &w, const int bid, const int nblk)
 // low-precision factor taken from Jacobi itself).  The results keep the FP64
 // sweeps' accuracy.
 //
-// The FP32 sweeps run in one thread-block cluster of kPc32Ctas CTAs per
-// problem, X in the CTAs' shared memory: block-cyclic one-sided Jacobi (the
-// columns in kPc32Blocks blocks of b, two per CTA; the blocks meet in the
-// round-robin order, every pair of columns once a sweep: the pairs inside
-// each block in the sweep's first block round, then those across the two
-// blocks), a warp per pair, the sub-rounds of a block round separated by
-// CTA barriers only and the block rounds by cluster barriers (the blocks
-// move through L2).  Across the blocks, warp w keeps column w of its CTA's
-// first block in registers and meets the second block's columns in turn,
-// which pass from warp to warp through shared memory.  Each CTA also forms
-// the 2b x 2b product G of a block round's rotations of its 2b columns; J is
+// The FP32 sweeps run on C CTAs per problem (C about n / 24, at most 32),
+// X in their shared memory: block-cyclic one-sided Jacobi (the columns in
+// 2C blocks of b, two per CTA; the blocks meet in the round-robin order,
+// every pair of columns once a sweep: the pairs inside each block in the
+// sweep's first block round, then those across the two blocks), a warp per
+// pair, the sub-rounds of a block round separated by CTA barriers only and
+// the block rounds by a grid barrier of the problem's CTAs (the blocks move
+// through L2).  Across the blocks, warp w keeps column w of its CTA's first
+// block in registers and meets the second block's columns in turn, which
+// pass from warp to warp through shared memory.  Each CTA also forms the
+// 2b x 2b product G of a block round's rotations of its 2b columns; J is
 // rebuilt from those afterwards by pc32_replay_kernel (J <- J G for each
 // block round in order, rows of J independent), so the sweeps carry no V.
-// ---------------------------------------------------------------------------
 constexpr float kTol32 = 1e-6f;   // rotate when |cos| > kTol32 (FP32 dots)
 constexpr float kLast32 = 1e-3f;  // stop after a sweep with every |cos| <= this
 constexpr int kMaxSweeps32 = 16;  // then stop anyway (preconditioning only)
-constexpr int kPc32Ctas = 16;
-constexpr int kPc32Blocks = 2 * kPc32Ctas;
-constexpr int kPc32MaxB = 24;     // widest block: 768 columns
+constexpr int kPc32MaxCtas = 32;  // CTAs per problem, at most
+constexpr int kPc32MaxB = 16;     // widest block (warps of a CTA)
 constexpr int kPc32Chunks = 6;    // float4 rows a lane holds: columns of <= 768 rows
 
 struct Pc32Job {
@@ -863,7 +861,8 @@ struct Pc32Job {
                       // its rotations (column-major)
     unsigned *bar;    // [6] sweeps, [8..10] per sweep mod 3: a |cos| > kLast32
     double *J;        // n x n: the product of the rotations (replay)
-    int m, n, b;      // b a multiple of 4, n <= kPc32Blocks b
+    int m, n, b;      // b a multiple of 4, n <= 2 C b
+    int C;            // CTAs (2C blocks)
     int ms;           // m rounded up to 128: the shared-memory column stride
 };
 
@@ -1048,17 +1047,18 @@ jacobi_group_kernel(const SvdWork *works, const int *begin, int np)
     jacobi_group_body<RPL>(w, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
 }
 
-// The FP32 sweeps: one cluster of kPc32Ctas CTAs per problem (blockIdx.x /
-// kPc32Ctas), b warps a CTA; dynamic shared memory: the two blocks (b ms
-// floats each) and G.  Lane l of a warp holds rows 128 k + 4 l .. + 3 of a
-// column.  Every CTA takes the same branches (cluster barriers).
-__global__ void __launch_bounds__(32 * kPc32MaxB, 1)
-pc32_cluster_kernel(const Pc32Job *jobs)
+// The FP32 sweeps: a cooperative launch, problem p on CTAs [begin[p],
+// begin[p + 1]) (J.C of them), b warps a CTA; dynamic shared memory: the
+// two blocks (b ms floats each) and G.  Lane l of a warp holds rows 128 k +
+// 4 l .. + 3 of a column.  Every CTA of a problem takes the same branches
+// (its grid barriers; bounded: WOS_DEVICE_TIMEOUT in bar[5] and an exit).
+__global__ void __launch_bounds__(32 * kPc32MaxB)
+pc32_sweeps_kernel(const Pc32Job *jobs, const int *begin, int np)
 {
-    cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
     extern __shared__ float4 pc32_sm[];
-    const Pc32Job J = jobs[blockIdx.x / kPc32Ctas];
-    const int cta = int(cluster.block_rank());
+    const int pb = problem_of(begin, np);
+    const Pc32Job J = jobs[pb];
+    const int cta = int(blockIdx.x) - begin[pb], C = J.C, NB = 2 * C;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int b = J.b, ms = J.ms, b2 = 2 * b, nk = ms / 128;
     float *R0 = reinterpret_cast<float *>(pc32_sm), *R1 = R0 + size_t(b) * ms;
@@ -1072,9 +1072,9 @@ pc32_cluster_kernel(const Pc32Job *jobs)
         if (threadIdx.x == 0)
             s_big = 0;
         bool big = false;
-        for (int r = 0; r < kPc32Blocks - 1; ++r) {
-            const int bA = rr_player(cta, r, kPc32Blocks);
-            const int bB = rr_player(kPc32Blocks - 1 - cta, r, kPc32Blocks);
+        for (int r = 0; r < NB - 1; ++r) {
+            const int bA = rr_player(cta, r, NB);
+            const int bB = rr_player(NB - 1 - cta, r, NB);
             pc32_load(J, bA, R0);
             pc32_load(J, bB, R1);
             for (int e = threadIdx.x; e < b2 * b2; e += blockDim.x)
@@ -1096,7 +1096,7 @@ pc32_cluster_kernel(const Pc32Job *jobs)
             }
             // pairs across the blocks: A[w] (registers) with B[(w + u) mod b];
             // slot k of the current buffer holds B[(k + u) mod b]
-            float4 xr[kPc32Chunks];
+            float4 xr[kPc32Chunks], yr[kPc32Chunks];
 #pragma unroll
             for (int k = 0; k < kPc32Chunks; ++k)
                 xr[k] = k < nk ? reinterpret_cast<const float4 *>(R0 + size_t(wid) * ms)[32 * k + lane]
@@ -1109,6 +1109,7 @@ pc32_cluster_kernel(const Pc32Job *jobs)
 #pragma unroll
                 for (int k = 0; k < kPc32Chunks; ++k) {
                     const float4 y = k < nk ? y4[32 * k + lane] : zero4;
+                    yr[k] = y;
                     al = fmaf(xr[k].x, xr[k].x, fmaf(xr[k].y, xr[k].y, fmaf(xr[k].z, xr[k].z, fmaf(xr[k].w, xr[k].w, al))));
                     be = fmaf(y.x, y.x, fmaf(y.y, y.y, fmaf(y.z, y.z, fmaf(y.w, y.w, be))));
                     ga = fmaf(xr[k].x, y.x, fmaf(xr[k].y, y.y, fmaf(xr[k].z, y.z, fmaf(xr[k].w, y.w, ga))));
@@ -1118,13 +1119,12 @@ pc32_cluster_kernel(const Pc32Job *jobs)
                 bool bg;
                 const bool rot = pc32_rotation(al, be, ga, c, sn, bg);
                 big |= bg;
-                // y again from shared memory (not held across the rotation's
-                // arithmetic: registers), rotated on its way to the next warp
+                // y rotated on its way to the next warp
                 float4 *o4 = reinterpret_cast<float4 *>(nxt + size_t((wid + b - 1) % b) * ms);
 #pragma unroll
                 for (int k = 0; k < kPc32Chunks; ++k)
                     if (k < nk) {
-                        const float4 x = xr[k], y = y4[32 * k + lane];
+                        const float4 x = xr[k], y = yr[k];
                         if (rot) {
                             xr[k] = make_float4(fmaf(c, x.x, -sn * y.x), fmaf(c, x.y, -sn * y.y),
                                                 fmaf(c, x.z, -sn * y.z), fmaf(c, x.w, -sn * y.w));
@@ -1150,18 +1150,20 @@ pc32_cluster_kernel(const Pc32Job *jobs)
             __syncthreads();
             pc32_store(J, bA, R0);
             pc32_store(J, bB, R1);
-            float *gl = J.G + ((size_t(sweep) * (kPc32Blocks - 1) + r) * kPc32Ctas + cta) *
-                                  size_t(b2) * b2;
+            float *gl = J.G + ((size_t(sweep) * (NB - 1) + r) * C + cta) * size_t(b2) * b2;
             for (int e = threadIdx.x; e < b2 * b2; e += blockDim.x)
                 __stcg(gl + e, G[e]);
-            cluster.sync();  // the blocks' stores before any CTA loads them
+            // the blocks' stores before any CTA loads them
+            if (!grid_barrier(J.bar, unsigned(C)))
+                return;
         }
         if (big && lane == 0)
             atomicOr(&s_big, 1);
         __syncthreads();
         if (threadIdx.x == 0 && s_big)
             atomicOr(flags + sweep % 3, 1u);
-        cluster.sync();
+        if (!grid_barrier(J.bar, unsigned(C)))
+            return;
         const bool done = *(volatile unsigned *)(flags + sweep % 3) == 0u;
         if (cta == 0 && threadIdx.x == 0)
             J.bar[6] = unsigned(sweep + 1);
@@ -1184,7 +1186,7 @@ pc32_replay_kernel(const Pc32Job *jobs, const int *begin, int np)
     extern __shared__ float4 rp_smem[];
     const int pb = problem_of(begin, np);
     const Pc32Job J = jobs[pb];
-    const int n = J.n, b = J.b, b2 = 2 * b, L = kPc32Blocks * b;
+    const int n = J.n, b = J.b, b2 = 2 * b, C = J.C, NB = 2 * C, L = NB * b;
     float *cur = reinterpret_cast<float *>(rp_smem), *nxt = cur + size_t(kRpRows) * L;
     const int r0 = (int(blockIdx.x) - begin[pb]) * kRpRows;
     for (int e = threadIdx.x; e < kRpRows * L; e += blockDim.x) {
@@ -1193,14 +1195,14 @@ pc32_replay_kernel(const Pc32Job *jobs, const int *begin, int np)
     }
     __syncthreads();
     const int nsw = int(*(volatile unsigned *)(J.bar + 6));
-    const int tasks = kPc32Ctas * b2;
+    const int tasks = C * b2;
     for (int z = 0; z < nsw; ++z)
-        for (int r = 0; r < kPc32Blocks - 1; ++r) {
-            const float *gr = J.G + (size_t(z) * (kPc32Blocks - 1) + r) * kPc32Ctas * size_t(b2) * b2;
+        for (int r = 0; r < NB - 1; ++r) {
+            const float *gr = J.G + (size_t(z) * (NB - 1) + r) * C * size_t(b2) * b2;
             for (int t = threadIdx.x; t < tasks; t += blockDim.x) {
                 const int c = t / b2, j = t - c * b2;
-                const int bA = rr_player(c, r, kPc32Blocks);
-                const int bB = rr_player(kPc32Blocks - 1 - c, r, kPc32Blocks);
+                const int bA = rr_player(c, r, NB);
+                const int bB = rr_player(NB - 1 - c, r, NB);
                 const float4 *g4 = reinterpret_cast<const float4 *>(gr + (size_t(c) * b2 + j) * b2);
                 float acc[kRpRows];
 #pragma unroll
@@ -2206,12 +2208,17 @@ const void *jacobi_lean_kernel_rpl(int rpl)
     }
 }
 
-// Block width of the FP32 sweeps for n columns (a multiple of 4, n <= 32 b),
-// the shared-memory column stride for m rows, and the shared memory of their
-// two kernels.
+// The FP32 sweeps' CTAs for n columns (blocks of about 12 columns), their
+// block width (a multiple of 4, n <= 2 C b), the shared-memory column stride
+// for m rows, and the shared memory of their two kernels.
+int pc32_ctas(int n)
+{
+    return std::min(kPc32MaxCtas, std::max(2, (n + 23) / 24));
+}
 int pc32_b(int n)
 {
-    return 4 * ((n + 4 * kPc32Blocks - 1) / (4 * kPc32Blocks));
+    const int nb = 2 * pc32_ctas(n);
+    return 4 * ((n + 4 * nb - 1) / (4 * nb));
 }
 int pc32_ms(int m)
 {
@@ -2224,7 +2231,7 @@ size_t pc32_smem(int n)
 }
 size_t pc32_replay_smem(int n)
 {
-    return size_t(2) * kRpRows * kPc32Blocks * pc32_b(n) * sizeof(float);
+    return size_t(2) * kRpRows * 2 * pc32_ctas(n) * pc32_b(n) * sizeof(float);
 }
 
 // Opts kfn in to the most dynamic shared memory a CTA may have next to its
@@ -2247,47 +2254,30 @@ bool allow_max_smem(const void *kfn, const wos_context *ctx)
     return true;
 }
 
-// Whether the FP32 sweeps take an n-column problem: its blocks fit the
-// warps and the shared memory of a CTA, and a cluster of kPc32Ctas such CTAs
-// can be resident.
+// Whether the FP32 sweeps take an n-column problem (n x n X): its blocks
+// fit the warps and the shared memory of a CTA, its columns a lane's
+// registers, and its CTAs the GPU.
 bool pc32_fits(const wos_context *ctx, int n)
 {
-    if (n < 2 * kPc32Blocks || pc32_b(n) > kPc32MaxB || pc32_ms(n) > 128 * kPc32Chunks)
+    if (n < 32 || pc32_b(n) > kPc32MaxB || pc32_ms(n) > 128 * kPc32Chunks)
         return false;
-    const void *ck = reinterpret_cast<const void *>(&pc32_cluster_kernel);
+    const void *sk = reinterpret_cast<const void *>(&pc32_sweeps_kernel);
     const void *rk = reinterpret_cast<const void *>(&pc32_replay_kernel);
-    cudaFuncAttributes fc = {}, fr = {};
-    if (cudaFuncGetAttributes(&fc, ck) != cudaSuccess ||
-        cudaFuncGetAttributes(&fr, rk) != cudaSuccess) {
+    if (!allow_max_smem(sk, ctx) || !allow_max_smem(rk, ctx))
+        return false;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sk, 32 * pc32_b(n), pc32_smem(n)) !=
+        cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    const size_t room = size_t(wos::ctx_max_smem(ctx));
-    if (pc32_smem(n) + fc.sharedSizeBytes > room || pc32_replay_smem(n) + fr.sharedSizeBytes > room)
-        return false;
-    if (cudaFuncSetAttribute(ck, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-            cudaSuccess ||
-        !allow_max_smem(ck, ctx) || !allow_max_smem(rk, ctx)) {
+    cudaFuncAttributes fr = {};
+    if (cudaFuncGetAttributes(&fr, rk) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(unsigned(kPc32Ctas));
-    cfg.blockDim = dim3(unsigned(32 * pc32_b(n)));
-    cfg.dynamicSmemBytes = pc32_smem(n);
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = unsigned(kPc32Ctas);
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, pc32_cluster_kernel, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return nc >= 1;
+    return bps >= 1 && pc32_ctas(n) <= bps * wos::ctx_sm_count(ctx) &&
+           pc32_replay_smem(n) + fr.sharedSizeBytes <= size_t(wos::ctx_max_smem(ctx));
 }
 
 const void *jacobi_kernel_rpt(int rpt)
@@ -2309,7 +2299,8 @@ const void *jacobi_kernel_rpt(int rpt)
 template <typename Rec>
 cudaError_t launch_groups(const void *kfn, int threads, int budget, const std::vector<int> &idx,
                           const std::vector<int> &grids, const std::vector<Rec> &recs,
-                          Rec *dev_recs, int *dev_begin, cudaStream_t st, int *launches)
+                          Rec *dev_recs, int *dev_begin, cudaStream_t st, int *launches,
+                          size_t smem = 0)
 {
     size_t at = 0;
     while (at < idx.size()) {
@@ -2332,7 +2323,8 @@ cudaError_t launch_groups(const void *kfn, int threads, int budget, const std::v
         const int *cdb = db;
         int cnp = np;
         void *args[] = {&cdr, &cdb, &cnp};
-        cudaError_t e = cudaLaunchCooperativeKernel(kfn, dim3(total), dim3(threads), args, 0, st);
+        cudaError_t e =
+            cudaLaunchCooperativeKernel(kfn, dim3(total), dim3(threads), args, smem, st);
         ++*launches;
         if (e != cudaSuccess)
             return e;
@@ -2449,7 +2441,8 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
             o.J = take(nn * 8);
             o.J2 = take(nn * 8);
             o.X32 = take(nn * 4);
-            o.G = take(size_t(kMaxSweeps32) * (kPc32Blocks - 1) * kPc32Ctas * b2 * b2 * 4);
+            const size_t C = size_t(pc32_ctas(w.n));
+            o.G = take(size_t(kMaxSweeps32) * (2 * C - 1) * C * b2 * b2 * 4);
             o.bar32 = take(64);
         }
     }
@@ -2458,7 +2451,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     const size_t o_rprec = take(sizeof(Pc32Job) * np + sizeof(int) * (np + 1));
     const size_t o_left = take(sizeof(LeftJob) * np);
     const size_t o_cjob = take(sizeof(ClusterJob) * np);
-    const size_t o_begin = take(sizeof(int) * (2 * np + 3));
+    const size_t o_begin = take(sizeof(int) * (3 * np + 4));
     char *base = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&base), off, st);
     if (e != cudaSuccess)
@@ -2523,6 +2516,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
                 v.m = w.n;
                 v.n = w.n;
                 v.b = pc32_b(w.n);
+                v.C = pc32_ctas(w.n);
                 v.ms = pc32_ms(w.n);
                 cudaMemsetAsync(v.bar, 0, 64, st);
             }
@@ -2560,7 +2554,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     if (jacobi_events && jacobi_events[0])
         cudaEventRecord(static_cast<cudaEvent_t>(jacobi_events[0]), st);
     // cluster kernel: one launch per cluster size, one cluster per problem
-    size_t cjobs_used = 0, pcjobs_used = 0;
+    size_t cjobs_used = 0;
     for (int CL = 1; e == cudaSuccess && CL <= kClMaxCtas; ++CL) {
         std::vector<ClusterJob> jobs;
         size_t smem = 0;
@@ -2629,36 +2623,33 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
                 ++launches;
             }
         }
-    // FP32 preconditioning sweeps: one cluster per problem, one launch per
-    // block width; then J from each problem's log
-    for (int bw = 4; e == cudaSuccess && bw <= kPc32MaxB; bw += 4) {
-        std::vector<Pc32Job> jobs;
-        int nmax = 0;
+    // FP32 preconditioning sweeps: cooperative launches of the problems'
+    // CTAs, one per block width; then J from each problem's G products
+    {
+        std::vector<Pc32Job> recs(np);
         for (int p = 0; p < np; ++p)
-            if (P[p].mixed && P[p].pc.b == bw) {
-                jobs.push_back(P[p].pc);
-                nmax = std::max(nmax, P[p].pc.n);
-            }
-        if (jobs.empty())
-            continue;
-        Pc32Job *dpc = reinterpret_cast<Pc32Job *>(base + o_pcrec) + pcjobs_used;
-        pcjobs_used += jobs.size();
-        cudaMemcpyAsync(dpc, jobs.data(), sizeof(Pc32Job) * jobs.size(), cudaMemcpyHostToDevice,
-                        st);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(unsigned(kPc32Ctas * int(jobs.size())));
-        cfg.blockDim = dim3(unsigned(32 * bw));
-        cfg.dynamicSmemBytes = pc32_smem(nmax);
-        cfg.stream = st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = unsigned(kPc32Ctas);
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, pc32_cluster_kernel, const_cast<const Pc32Job *>(dpc));
-        ++launches;
+            if (P[p].mixed)
+                recs[p] = P[p].pc;
+        const void *sk = reinterpret_cast<const void *>(&pc32_sweeps_kernel);
+        for (int bw = 4; e == cudaSuccess && bw <= kPc32MaxB; bw += 4) {
+            std::vector<int> idx;
+            std::vector<int> grids(np, 0);
+            int nmax = 0;
+            for (int p = 0; p < np; ++p)
+                if (P[p].mixed && P[p].pc.b == bw) {
+                    idx.push_back(p);
+                    grids[p] = P[p].pc.C;
+                    nmax = std::max(nmax, P[p].pc.n);
+                }
+            if (idx.empty())
+                continue;
+            const size_t smem = pc32_smem(nmax);
+            int bps = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, sk, 32 * bw, smem);
+            e = launch_groups(sk, 32 * bw, std::max(1, bps) * sms, idx, grids, recs,
+                              reinterpret_cast<Pc32Job *>(base + o_pcrec), dbegin + 2 * np + 3,
+                              st, &launches, smem);
+        }
     }
     if (e == cudaSuccess) {  // every problem's J in one launch
         std::vector<Pc32Job> jobs;
@@ -2806,6 +2797,9 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
             if (P[p].pre)
                 cudaMemcpyAsync(hb.data() + p * 14 + 7, P[p].q.bar, 7 * 4, cudaMemcpyDeviceToHost,
                                 st);
+            if (P[p].mixed)  // the FP32 sweeps' barrier status in place of q.bar[6]
+                cudaMemcpyAsync(hb.data() + p * 14 + 13, P[p].pc.bar + 5, 4,
+                                cudaMemcpyDeviceToHost, st);
         }
         e = cudaStreamSynchronize(st);
         status = wos::cuda_status(e);
@@ -2815,6 +2809,8 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
                 status = wos_status(hb[p * 14 + 7 + 5]);
             if (status == WOS_OK && hb[p * 14 + 5] != 0u)
                 status = wos_status(hb[p * 14 + 5]);
+            if (status == WOS_OK && P[p].mixed && hb[p * 14 + 13] != 0u)
+                status = wos_status(hb[p * 14 + 13]);
         }
     }
     cudaFreeAsync(base, st);
