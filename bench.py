@@ -307,6 +307,29 @@ def qr_flop(m: int, n: int) -> int:
     return 2 * m * n * n - (2 * n ** 3) // 3
 
 
+def fp32_preconditioned(n: int, svd_path: str) -> bool:
+    """Whether the library runs FP32 sweeps before the FP64 ones for a worked
+    matrix of n columns: above 256 (the sizes the cluster kernel cannot take)
+    and up to 768 columns (a lane's registers), unless FP64 sweeps alone are
+    asked for."""
+    return 256 < n <= 768 and svd_path != "fp64-sweeps"
+
+
+def ns_flop(n: int) -> int:
+    """FP64 flop between the FP32 and the FP64 sweeps: two symmetric products
+    Q^T Q (n^3 each, one triangle) and X Q (2 n^3); the two correction
+    products run in FP32."""
+    return 4 * n ** 3
+
+
+def svd_fp64_flop(m: int, n: int, sweeps: int, svd_path: str) -> int:
+    """FP64 flop of one factorisation of an m x n worked matrix: the QR
+    (n >= 32), the Newton-Schulz products of the FP32-preconditioned path,
+    and the FP64 sweeps (sweeps = the FP64 sweeps the library reports)."""
+    fl = jacobi_flop(m, n, sweeps) + (qr_flop(m, n) if n >= 32 else 0)
+    return fl + (ns_flop(n) if fp32_preconditioned(n, svd_path) else 0)
+
+
 def jacobi_flop(m: int, n: int, sweeps: int) -> int:
     """FP64 flop of the Jacobi sweeps of one SVD of an m x n worked matrix
     (m >= n) as the library runs it (on X = R^T, n x n, when n >= 32): every
@@ -592,15 +615,18 @@ def run_gpu(args, rank: int, world: int, dist):
     jac_ms_ov = float(np.mean([a.elapsed_time(b) for (a, b) in jev]))
     jac_ms = float(np.median([a.elapsed_time(b) for (a, b) in lat_jev]))
     walk_ms_sum = float(np.mean([sum(a.elapsed_time(b) for (a, b) in row) for row in kev]))
-    flop = sum(jacobi_flop(p["svd_mn"][0], p["svd_mn"][1], p["sweeps"]) +
-               (qr_flop(*p["svd_mn"]) if p["svd_mn"][1] >= 32 else 0) for p in prep)
+    flop = sum(svd_fp64_flop(p["svd_mn"][0], p["svd_mn"][1], p["sweeps"], args.svd_path)
+               for p in prep)
+    mixed = all(fp32_preconditioned(p["svd_mn"][1], args.svd_path) for p in prep)
     svd_achieved = flop / (jac_ms / 1e3) / 1e9
     svd_achieved_ov = flop / (jac_ms_ov / 1e3) / 1e9
+    sweeps64 = ("jacobi_group_kernel" if sum(p["svd_mn"][1] for p in prep) > 2 * 3 * 152
+                else "jacobi_lean_kernel")
     svd_roof = {"kernel": ("svd_cluster_kernel" if args.svd_path == "auto" and
                            all(p["svd_mn"][1] <= 256 for p in prep)
-                           else ("qrcp_kernel + jacobi_group_kernel"
-                                 if sum(p["svd_mn"][1] for p in prep) > 2 * 3 * 152
-                                 else "qrcp_kernel + jacobi_lean_kernel")
+                           else ("qrs_kernel + pc32_sweeps_kernel + pc32_replay_kernel + "
+                                 "dgemm_kernel + " + sweeps64 if mixed
+                                 else "qrcp_kernel + " + sweeps64)
                            if all(p["svd_mn"][1] > 256 for p in prep)
                            else "qrcp_kernel + jacobi_kernel"),
                 "bound": "alu", "pipe": "fp64", "achieved": svd_achieved,
@@ -609,11 +635,15 @@ def run_gpu(args, rank: int, world: int, dist):
                 "traffic": svd_traffic() if args.workload == "config3" else None,
                 "peak_source": "152 SMs x 2 FP64 FMA/clk (ncu dfma peak_sustained 304 "
                                "per chip) x 2 flop x 2070 MHz",
-                "unit_of_work": "one factorisation: the pivoted Householder QR (2mn^2 - "
-                                "2n^3/3 flop, n >= 32) and every pair visit of every sweep "
-                                "(12 l + 6n flop with V accumulated, n <= 256; 6 l without, "
-                                "n > 256; l = rows of the matrix Jacobi works on: n after the "
-                                "QR, m without; every visit counted as rotated)",
+                "unit_of_work": "one factorisation's FP64 flop: the Householder QR (2mn^2 - "
+                                "2n^3/3, n >= 32; pivoted, or in decreasing-norm order "
+                                "before FP32 sweeps), the Newton-Schulz and X Q products "
+                                "after FP32 sweeps (4 n^3; 256 < n <= 768), and every pair "
+                                "visit of every FP64 sweep (12 l + 6n flop with V "
+                                "accumulated, n <= 256; 6 l without, n > 256; l = rows of "
+                                "the matrix Jacobi works on: n after the QR, m without; every "
+                                "visit counted as rotated).  The FP32 sweeps run on the FP32 "
+                                "pipe and are not counted",
                 "sweeps": [p["sweeps"] for p in prep],
                 "problems_per_launch": len(prep),
                 "timing": "the factorisation launches (QR and sweeps) of the steps run "
@@ -1020,9 +1050,10 @@ def run_svd(args, rank: int, world: int, dist):
     """The FP64 SVD alone (QR preconditioning + Jacobi on R^T + left vectors)
     on seeded operator-shaped count matrices of the two operator sizes of
     the paper's 2-D experiments (M_D x M_1 = 256 x 128 and 1024 x 768),
-    one wos_op_svd call per shape per step.  factorisation = the QR with
-    pivoting and the Jacobi sweeps (the cluster kernel, or the grid-wide
-    QR, X and Jacobi launches)."""
+    one wos_op_svd call per shape per step.  factorisation = the QR and the
+    Jacobi sweeps (the cluster kernel; or the grid-wide QR, X and Jacobi
+    launches, with the FP32 sweeps, their replay and the Newton-Schulz
+    products between them above 256 columns)."""
     import torch
     from paper_2409_03686_gb300 import build as B
     from paper_2409_03686_gb300 import workloads as W
@@ -1067,7 +1098,7 @@ def run_svd(args, rank: int, world: int, dist):
     per = []
     for (M_D, M_tot, M_1), r in zip(shapes, res):
         call, jac = float(np.median(r["call"])), float(np.median(r["jac"]))
-        fl = jacobi_flop(M_D, M_1, r["sweeps"]) + qr_flop(M_D, M_1)
+        fl = svd_fp64_flop(M_D, M_1, r["sweeps"], args.svd_path)
         per.append({"shape": f"{M_D}x{M_1}", "ms_per_call": call, "factorisation_ms": jac,
                     "sweeps": r["sweeps"], "factorisation_gflops": fl / jac / 1e6,
                     "factorisation_frac_fp64_peak": fl / jac / 1e6 / FP64_PEAK_GFLOPS})
