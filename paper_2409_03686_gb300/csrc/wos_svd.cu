@@ -1285,26 +1285,38 @@ __global__ void permute_rows_kernel(const double *X, const int *perm, int n, dou
     }
 }
 
-// C = alpha op(A) B + beta D in FP64, column-major: op(A) = A (m x k, lda)
-// or A^T (A k x m, lda); B k x n (ldb); C and D m x n (ldc); no D when it is
-// null.  64 x 64 tiles of C per block of 256 threads, 4 x 4 per thread, k in
-// steps of 16 through shared memory.  SYM (C = A^T A, m = n): only the tiles
-// on and above the diagonal, each written to both triangles (element (i, j)
-// and (j, i) are the same products in the same order).
+// One product of a batched GEMM launch (blockIdx.z = the job): C = alpha
+// op(A) B + beta D in FP64, column-major: op(A) = A (m x k, lda) or A^T (A
+// k x m, lda); B k x n (ldb); C and D m x n (ldc); no D when it is null.
+struct GemmJob {
+    const double *A, *B, *D;
+    double *C;
+    int m, n, k, lda, ldb, ldc;
+    double alpha, beta;
+};
+
+// 64 x 64 tiles of C per block of 256 threads, 4 x 4 per thread, k in steps
+// of 16 through shared memory; the launch's x, y cover the largest job (the
+// tiles outside a smaller one return).  SYM (C = A^T A, m = n): only the
+// tiles on and above the diagonal, each written to both triangles (element
+// (i, j) and (j, i) are the same products in the same order).
 constexpr int kGemmTile = 64, kGemmK = 16;
 
 template <bool TA, bool SYM = false>
 __global__ void __launch_bounds__(256)
-dgemm_kernel(int m, int n, int k, const double *A, int lda, const double *B, int ldb,
-             double *C, int ldc, double alpha, double beta, const double *D)
+dgemm_kernel(const GemmJob *jobs)
 {
-    if (SYM && blockIdx.x > blockIdx.y)
+    const GemmJob g = jobs[blockIdx.z];
+    const int m = g.m, n = g.n, k = g.k;
+    const int i0 = blockIdx.x * kGemmTile, j0 = blockIdx.y * kGemmTile;
+    if ((SYM && blockIdx.x > blockIdx.y) || i0 >= m || j0 >= n)
         return;
     __shared__ double As[kGemmK][kGemmTile + 1];
     __shared__ double Bs[kGemmK][kGemmTile + 1];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;  // 16 x 16 threads, 4 x 4 each
-    const int i0 = blockIdx.x * kGemmTile, j0 = blockIdx.y * kGemmTile;
+    const double *A = g.A, *B = g.B;
+    const int lda = g.lda, ldb = g.ldb;
     double acc[4][4] = {};
     for (int l0 = 0; l0 < k; l0 += kGemmK) {
         // A tile: 64 rows x 16 columns of op(A); B tile: 16 rows x 64 columns
@@ -1345,28 +1357,32 @@ dgemm_kernel(int m, int n, int k, const double *A, int lda, const double *B, int
         for (int v = 0; v < 4; ++v) {
             const int gi = i0 + tx + 16 * u, gj = j0 + ty + 16 * v;
             if (gi < m && gj < n) {
-                const size_t o = size_t(gj) * ldc + gi;
-                C[o] = D ? fma(alpha, acc[u][v], beta * D[o]) : alpha * acc[u][v];
+                const size_t o = size_t(gj) * g.ldc + gi;
+                g.C[o] = g.D ? fma(g.alpha, acc[u][v], g.beta * g.D[o]) : g.alpha * acc[u][v];
                 if (SYM)
-                    C[size_t(gi) * ldc + gj] = C[o];
+                    g.C[size_t(gi) * g.ldc + gj] = g.C[o];
             }
         }
 }
 
 // C = D + alpha fl32(A) fl32(B - I) with FP32 products and sums (A, B, C, D
-// FP64, n x n, column-major, ld n; C may not alias A or B): the correction
-// terms of the Newton-Schulz steps, Q (Q^T Q - I), whose size (1e-4 and
-// below) makes FP32's relative rounding negligible next to FP64's.  The
-// tiling of dgemm_kernel.
+// FP64, n x n, column-major, ld n; C may not alias A or B; job fields m = n,
+// D, alpha): the correction terms of the Newton-Schulz steps, Q (Q^T Q - I),
+// whose size (1e-4 and below) makes FP32's relative rounding negligible next
+// to FP64's.  The tiling of dgemm_kernel.
 __global__ void __launch_bounds__(256)
-ns_correction_kernel(int n, const double *A, const double *B, double *C, double alpha,
-                     const double *D)
+ns_correction_kernel(const GemmJob *jobs)
 {
+    const GemmJob g = jobs[blockIdx.z];
+    const int n = g.n;
+    const int i0 = blockIdx.x * kGemmTile, j0 = blockIdx.y * kGemmTile;
+    if (i0 >= n || j0 >= n)
+        return;
     __shared__ float As[kGemmK][kGemmTile + 1];
     __shared__ float Bs[kGemmK][kGemmTile + 1];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int i0 = blockIdx.x * kGemmTile, j0 = blockIdx.y * kGemmTile;
+    const double *A = g.A, *B = g.B;
     float acc[4][4] = {};
     for (int l0 = 0; l0 < n; l0 += kGemmK) {
         for (int e = tid; e < kGemmTile * kGemmK; e += 256) {
@@ -1403,36 +1419,49 @@ ns_correction_kernel(int n, const double *A, const double *B, double *C, double 
             const int gi = i0 + tx + 16 * u, gj = j0 + ty + 16 * v;
             if (gi < n && gj < n) {
                 const size_t o = size_t(gj) * n + gi;
-                C[o] = fma(alpha, double(acc[u][v]), D[o]);
+                g.C[o] = fma(g.alpha, double(acc[u][v]), g.D[o]);
             }
         }
 }
 
-void dgemm(cudaStream_t st, bool ta, int m, int n, int k, const double *A, int lda,
-           const double *B, int ldb, double *C, int ldc, double alpha = 1.0, double beta = 0.0,
-           const double *D = nullptr)
+enum GemmKind { kGemmNN = 0, kGemmSyrk = 1, kGemmNsCorrection = 2 };
+
+// One launch for every job (dev: room for jobs.size() records; stream order
+// lets consecutive launches reuse it).
+cudaError_t gemm_batch(cudaStream_t st, GemmKind kind, const std::vector<GemmJob> &jobs,
+                       GemmJob *dev, int *launches)
 {
-    const dim3 gg(unsigned((m + kGemmTile - 1) / kGemmTile),
-                  unsigned((n + kGemmTile - 1) / kGemmTile));
-    if (ta)
-        dgemm_kernel<true><<<gg, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, alpha, beta, D);
+    if (jobs.empty())
+        return cudaSuccess;
+    int mm = 1, nn = 1;
+    for (const GemmJob &g : jobs) {
+        mm = std::max(mm, g.m);
+        nn = std::max(nn, g.n);
+    }
+    cudaMemcpyAsync(dev, jobs.data(), sizeof(GemmJob) * jobs.size(), cudaMemcpyHostToDevice, st);
+    const dim3 gg(unsigned((mm + kGemmTile - 1) / kGemmTile),
+                  unsigned((nn + kGemmTile - 1) / kGemmTile), unsigned(jobs.size()));
+    if (kind == kGemmNN)
+        dgemm_kernel<false><<<gg, 256, 0, st>>>(dev);
+    else if (kind == kGemmSyrk)
+        dgemm_kernel<true, true><<<gg, 256, 0, st>>>(dev);
     else
-        dgemm_kernel<false><<<gg, 256, 0, st>>>(m, n, k, A, lda, B, ldb, C, ldc, alpha, beta, D);
+        ns_correction_kernel<<<gg, 256, 0, st>>>(dev);
+    ++*launches;
+    return cudaGetLastError();
 }
 
-// M = A^T A (n x n from k x n A), both triangles.
-void dsyrk(cudaStream_t st, int n, int k, const double *A, double *M)
+GemmJob gemm_nn(int m, int n, int k, const double *A, const double *B, double *C)
 {
-    const dim3 gg(unsigned((n + kGemmTile - 1) / kGemmTile), unsigned((n + kGemmTile - 1) / kGemmTile));
-    dgemm_kernel<true, true><<<gg, 256, 0, st>>>(n, n, k, A, k, A, k, M, n, 1.0, 0.0, nullptr);
+    return GemmJob{A, B, nullptr, C, m, n, k, m, k, m, 1.0, 0.0};
 }
-
-// C = D - (1/2) fl32(A) fl32(B - I), n x n.
-void ns_correction(cudaStream_t st, int n, const double *A, const double *B, const double *D,
-                   double *C)
+GemmJob gemm_syrk(int n, int k, const double *A, double *M)  // M = A^T A
 {
-    const dim3 gg(unsigned((n + kGemmTile - 1) / kGemmTile), unsigned((n + kGemmTile - 1) / kGemmTile));
-    ns_correction_kernel<<<gg, 256, 0, st>>>(n, A, B, C, -0.5, D);
+    return GemmJob{A, A, nullptr, M, n, n, k, k, k, n, 1.0, 0.0};
+}
+GemmJob gemm_ns(int n, const double *A, const double *M, const double *D, double *C)
+{
+    return GemmJob{A, M, D, C, n, n, n, n, n, n, -0.5, 0.0};  // C = D - A (M - I) / 2
 }
 
 
@@ -2448,6 +2477,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     }
     const size_t o_jrec = take(sizeof(SvdWork) * np), o_qrec = take(sizeof(QrWork) * np);
     const size_t o_pcrec = take(sizeof(Pc32Job) * np);
+    const size_t o_gemm = take(sizeof(GemmJob) * np);
     const size_t o_rprec = take(sizeof(Pc32Job) * np + sizeof(int) * (np + 1));
     const size_t o_left = take(sizeof(LeftJob) * np);
     const size_t o_cjob = take(sizeof(ClusterJob) * np);
@@ -2679,19 +2709,31 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     // orthogonal to about 1e-15), X Q in FP64 (a right-multiplicative
     // rounding: relative accuracy kept).  M sits in V's place (free until
     // the left vectors); J2 holds Q after one step, then X Q.
-    for (int p = 0; e == cudaSuccess && p < np; ++p)
-        if (P[p].mixed) {
-            SvdProb &b = P[p];
-            const int n = b.w.n;
-            double *J = b.pc.J, *J2 = b.wj.W, *M = b.wj.Vw;
-            dsyrk(st, n, n, J, M);                            // M = J^T J
-            ns_correction(st, n, J, M, J, J2);                // J2 = J - J (M - I) / 2
-            dsyrk(st, n, n, J2, M);                           // M = J2^T J2
-            ns_correction(st, n, J2, M, J2, J);               // Q = J2 - J2 (M - I) / 2
-            dgemm(st, false, n, n, n, b.X0, n, J, n, J2, n);  // X Q
-            column_sq_norms_kernel<<<sms * 2, 256, 0, st>>>(b.wj);
-            launches += 6;
-        }
+    {
+        std::vector<GemmJob> s1, c1, s2, c2, xq;
+        for (int p = 0; p < np; ++p)
+            if (P[p].mixed) {
+                SvdProb &b = P[p];
+                const int n = b.w.n;
+                double *J = b.pc.J, *J2 = b.wj.W, *M = b.wj.Vw;
+                s1.push_back(gemm_syrk(n, n, J, M));             // M = J^T J
+                c1.push_back(gemm_ns(n, J, M, J, J2));           // J2 = J - J (M - I) / 2
+                s2.push_back(gemm_syrk(n, n, J2, M));            // M = J2^T J2
+                c2.push_back(gemm_ns(n, J2, M, J2, J));          // Q = J2 - J2 (M - I) / 2
+                xq.push_back(gemm_nn(n, n, n, b.X0, J, J2));     // X Q
+            }
+        GemmJob *dg = reinterpret_cast<GemmJob *>(base + o_gemm);
+        if (e == cudaSuccess) e = gemm_batch(st, kGemmSyrk, s1, dg, &launches);
+        if (e == cudaSuccess) e = gemm_batch(st, kGemmNsCorrection, c1, dg, &launches);
+        if (e == cudaSuccess) e = gemm_batch(st, kGemmSyrk, s2, dg, &launches);
+        if (e == cudaSuccess) e = gemm_batch(st, kGemmNsCorrection, c2, dg, &launches);
+        if (e == cudaSuccess) e = gemm_batch(st, kGemmNN, xq, dg, &launches);
+        for (int p = 0; e == cudaSuccess && p < np; ++p)
+            if (P[p].mixed) {
+                column_sq_norms_kernel<<<sms * 2, 256, 0, st>>>(P[p].wj);
+                ++launches;
+            }
+    }
     // Jacobi: one cooperative launch per class of rows per thread (and per
     // group of co-resident problems); the CTAs are shared in proportion to
     // the pairs when the batch is larger than the GPU
@@ -2745,15 +2787,20 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     // left vectors without V: L = W P X_final (an FP64 GEMM of the saved W
     // with the row-permuted final X; its columns are sigma^2 times the unit
     // left vectors, scaled in finalize)
-    for (int p = 0; e == cudaSuccess && p < np; ++p)
-        if (P[p].lean) {
-            SvdProb &b = P[p];
-            const int m = b.w.m, n = b.w.n;
-            fold_scales_kernel<<<sms * 4, 256, 0, st>>>(b.wj);  // X = d_j xt_j
-            permute_rows_kernel<<<sms * 4, 256, 0, st>>>(b.wj.W, b.q.perm, n, b.wj.Vw);
-            dgemm(st, false, m, n, n, b.W0, m, b.wj.Vw, n, b.Lb, m);
-            launches += 3;
-        }
+    {
+        std::vector<GemmJob> lv;
+        for (int p = 0; e == cudaSuccess && p < np; ++p)
+            if (P[p].lean) {
+                SvdProb &b = P[p];
+                const int m = b.w.m, n = b.w.n;
+                fold_scales_kernel<<<sms * 4, 256, 0, st>>>(b.wj);  // X = d_j xt_j
+                permute_rows_kernel<<<sms * 4, 256, 0, st>>>(b.wj.W, b.q.perm, n, b.wj.Vw);
+                launches += 2;
+                lv.push_back(gemm_nn(m, n, n, b.W0, b.wj.Vw, b.Lb));
+            }
+        if (e == cudaSuccess)
+            e = gemm_batch(st, kGemmNN, lv, reinterpret_cast<GemmJob *>(base + o_gemm), &launches);
+    }
     if (e == cudaSuccess) {  // left vectors of every other preconditioned problem
         std::vector<LeftJob> jobs;
         int ncols = 0;
