@@ -1868,7 +1868,9 @@ __device__ void qrs_body(const QrWork &q, const int b, const int G)
     }
 }
 
-__global__ void __launch_bounds__(kQrThreads)
+constexpr int kQrsThreads = 256;
+
+__global__ void __launch_bounds__(kQrsThreads)
 qrs_kernel(const QrWork *works, const int *begin, int np)
 {
     const int p = problem_of(begin, np);
@@ -2632,9 +2634,13 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
             sort_columns_kernel<<<(q.n + 255) / 256, 256, 0, st>>>(q);
             launches += 2;
         }
-        if (e == cudaSuccess && !srt.empty())
-            e = launch_groups(reinterpret_cast<const void *>(qrs_kernel), kQrThreads, qbudget,
-                              srt, qgrids, qrecs, dq, dbegin, st, &launches);
+        if (e == cudaSuccess && !srt.empty()) {
+            int sbps = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sbps, qrs_kernel, kQrsThreads, 0);
+            e = launch_groups(reinterpret_cast<const void *>(qrs_kernel), kQrsThreads,
+                              std::max(1, sbps) * sms, srt, qgrids, qrecs, dq, dbegin, st,
+                              &launches);
+        }
         if (e == cudaSuccess && !piv.empty())
             e = launch_groups(reinterpret_cast<const void *>(qrcp_kernel), kQrThreads, qbudget,
                               piv, qgrids, qrecs, dq + srt.size(), dbegin + srt.size() + 1, st,
@@ -2738,14 +2744,18 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
     // group of co-resident problems); the CTAs are shared in proportion to
     // the pairs when the batch is larger than the GPU
     // Without V: four pairs per CTA when the batch has pairs for more than
-    // three CTAs of one pair per SM (several large problems: the FP64 units
-    // bound the sweeps), else a CTA per pair (a lone problem: the round's
+    // three CTAs of one pair per SM and its sweeps are FP64 ones alone (ten
+    // or so sweeps: the FP64 units bound them), else a CTA per pair (a lone
+    // problem, or the two or three sweeps after FP32 ones: the round's
     // critical path bounds them)
     long long lean_pairs = 0;
+    bool any_mixed = false;
     for (int p = 0; p < np; ++p)
-        if (P[p].lean)
+        if (P[p].lean) {
             lean_pairs += P[p].wj.n_pad / 2;
-    const bool grouped = lean_pairs > 3LL * sms;
+            any_mixed = any_mixed || P[p].mixed;
+        }
+    const bool grouped = !any_mixed && lean_pairs > 3LL * sms;
     for (int cls = 0; cls < 11; ++cls) {
         if (e != cudaSuccess)
             break;

@@ -198,14 +198,18 @@ def test_svd_is_deterministic(shape, svd_path):
             assert torch.equal(a, b), rep
 
 
-@pytest.mark.parametrize("large", [False, True], ids=["mixed", "without-V"])
+@pytest.mark.parametrize("large", [False, True, "fp64"], ids=["mixed", "without-V", "fp64-sweeps"])
 def test_batched_svd_equals_single_calls(svd_path, large):
     """wos_op_svd_batched: problems of different shapes and orientations
     (direct path n < 32 and preconditioned n >= 32), and a batch larger than
     the co-resident CTAs of one launch, give each problem's single-call
     results bit for bit.  Problems of more than 256 columns (sweeps without
-    V) in a batch large enough for four pairs per CTA, against single calls
-    with a CTA per pair: the two kernels' canonical summation order."""
+    V): with the FP32 preconditioning (a CTA per pair alone and in the
+    batch), and with FP64 sweeps alone in a batch large enough for four
+    pairs per CTA against single calls with a CTA per pair (the two kernels'
+    canonical summation order)."""
+    if large == "fp64":
+        wos.wos_set_svd_path(ctx(), wos.SVD_FP64_SWEEPS)
     if large:
         shapes = [(600, 900, 300), (300, 900, 600), (520, 800, 400), (700, 1000, 350)]
     else:
@@ -223,6 +227,7 @@ def test_batched_svd_equals_single_calls(svd_path, large):
         refs.append(wos.wos_op_svd(ctx(), Ct, 50_000, g1, sg))
     got = wos.wos_op_svd_batched(ctx(), items)
     torch.cuda.synchronize()
+    wos.wos_set_svd_path(ctx(), svd_path)
     for q, (r, g) in enumerate(zip(refs, got)):
         for a, b in zip(r[:3], g[:3]):
             assert torch.equal(a, b), q
