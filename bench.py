@@ -399,6 +399,20 @@ def run_gpu(args, rank: int, world: int, dist):
     # of its walks, before anything is timed; later builds use it
     tunings = ({inst_p["inst"].name: wos.wos_autotune(ctx, inst_p["inst"])
                 for inst_p in prep} if not args.no_autotune else {})
+    # --walk-blocks-per-sm caps the walk launches' resident blocks per SM
+    # (the tuned configuration otherwise), leaving room beside them for the
+    # previous step's SVD kernels
+    walk_launch = {}
+    if args.walk_blocks_per_sm > 0:
+        for p in prep:
+            t = tunings.get(p["inst"].name, {})
+            walk_launch[p["inst"].name] = dict(
+                block_size=int(t.get("block_size", 256)),
+                blocks_per_sm=(min(int(t["blocks_per_sm"]), args.walk_blocks_per_sm)
+                               if t.get("blocks_per_sm", 0) > 0 else args.walk_blocks_per_sm),
+                tiles_per_warp=int(t.get("tiles_per_warp", 0)),
+                hist_slots=int(t.get("hist_slots", 0)),
+                refill_min=int(t.get("refill_min", 0)))
     # measured pipe throughputs of this GPU (microbenchmark kernels, a few ms)
     pipes = wos.wos_measure_pipes(ctx)
     # warm-up: truncation ranks from the spectra, step counts from stats
@@ -446,7 +460,8 @@ def run_gpu(args, rank: int, world: int, dist):
                 else:
                     pts, uD, u0 = p["points"], p["uD"], p["u0"]
                 opts = wos.make_opts(precision=0, stream_id=inst.stream,
-                                     kernel_events=timing[q] if timing else None)
+                                     kernel_events=timing[q] if timing else None,
+                                     **walk_launch.get(inst.name, {}))
                 c, _, _ = wos.wos_build_operator(ctx, inst.domain, inst.K, pts,
                                                  inst.partition, inst.N, inst.eps, inst.seed,
                                                  opts=opts, stats=False, stream=bs)
@@ -1200,6 +1215,8 @@ def main():
     ap.add_argument("--svd-path", choices=list(SVD_PATHS), default="auto",
                     help="SVD factorisation kernels: auto (cluster kernel when the "
                          "operator fits it) or grid (grid-wide kernels)")
+    ap.add_argument("--walk-blocks-per-sm", type=int, default=0,
+                    help="cap on the walk launches' resident blocks per SM (0: as tuned)")
     ap.add_argument("--svd-streams", type=int, default=4,
                     help="SVD streams the pipelined steps alternate over")
     ap.add_argument("--no-autotune", action="store_true",
