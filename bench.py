@@ -389,9 +389,13 @@ def run_gpu(args, rank: int, world: int, dist):
     # the SVD stream runs at high priority: when a step's walk launch drains,
     # the block scheduler places the SVD's clusters before the next step's
     # walk blocks, which fill the rest of the GPU (steps pipeline)
-    # several SVD streams (four by default), taken in turn by the steps, so
-    # that consecutive steps' SVDs (each a latency-bound cluster launch on a
-    # few SMs) overlap each other too
+    # several SVD streams, taken in turn by the steps, so that consecutive
+    # steps' SVDs overlap each other too: four for the 2-D configuration
+    # (each SVD a latency-bound cluster launch on a few SMs), two for the
+    # 3-D one (its SVDs take longer than its walks; more streams only pile
+    # them up: 3.36 / 3.37e9 walks/s with four against 3.50 / 3.54e9)
+    if args.svd_streams <= 0:
+        args.svd_streams = 2 if args.workload.startswith("config3") else 4
     streams = [torch.cuda.Stream(device=dev, priority=-1) for _ in range(args.svd_streams)]
     build_stream = torch.cuda.Stream(device=dev)
     # the project's autotuner picks the launch configuration of each
@@ -1217,8 +1221,10 @@ def main():
                          "operator fits it) or grid (grid-wide kernels)")
     ap.add_argument("--walk-blocks-per-sm", type=int, default=0,
                     help="cap on the walk launches' resident blocks per SM (0: as tuned)")
-    ap.add_argument("--svd-streams", type=int, default=4,
-                    help="SVD streams the pipelined steps alternate over")
+    ap.add_argument("--svd-streams", type=int, default=0,
+                    help="SVD streams the pipelined steps alternate over (0: two for the "
+                         "3-D configuration, whose SVDs take longer than its walks; four "
+                         "for the 2-D one)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="default launch configuration (profiling: no trial launches)")
     ap.add_argument("--batch-scale", type=float, default=1.0,
