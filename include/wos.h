@@ -441,17 +441,23 @@ wos_status wos_check_points(const wos_domain *domain, const double *points,
  *   nu       device, M_D doubles, or NULL for nu_i = 1/sqrt(M_D) (Sec. 5.2).
  *   sigma    device, M_tot doubles (wos_element_measures).
  *   U        device, M_D x k;  S  device, k;  V  device, M_1 x k.
- *   sweeps   host or NULL; if non-NULL the call waits and stores the sweep
- *            count, returning WOS_NO_CONVERGENCE if max sweeps were used.
- * Errors: WOS_INVALID_ARG, WOS_OOM, WOS_CUDA_ERROR, WOS_NO_CONVERGENCE. */
+ *   sweeps   host or NULL; if non-NULL the call waits and stores the FP64
+ *            sweep count (when FP32 sweeps ran first -- 257 to 768 columns,
+ *            see wos_set_svd_path -- only the FP64 sweeps after them), and
+ *            returns WOS_NO_CONVERGENCE if max sweeps were used, or
+ *            WOS_DEVICE_TIMEOUT if a grid-wide wait of the QR or of the
+ *            sweeps gave up.
+ * Errors: WOS_INVALID_ARG, WOS_OOM, WOS_CUDA_ERROR, WOS_NO_CONVERGENCE,
+ * WOS_DEVICE_TIMEOUT. */
 wos_status wos_op_svd(wos_context *ctx, const uint32_t *counts, int32_t M_D,
                       int32_t M_tot, uint32_t N, const uint8_t *gamma1,
                       const double *nu, const double *sigma, double *U,
                       double *S, double *V, int32_t *sweeps, void *stream);
 
-/* Many SVDs of wos_op_svd in one pass (one cooperative QR launch and one
- * Jacobi launch per class of problem size, their CTAs split among the
- * problems, each synchronising only its own CTAs): independent operators of
+/* Many SVDs of wos_op_svd in one pass (one cooperative QR launch, one FP32
+ * sweep launch, one launch per GEMM step and one Jacobi launch per class of
+ * problem size, their CTAs split among the problems, each synchronising
+ * only its own CTAs): independent operators of
  * a benchmark step or of the serving queue share the GPU instead of queueing
  * one latency-bound launch after another.  Every field as the argument of
  * the same name of wos_op_svd (counts, nu, sigma, U, S, V on the device;
@@ -470,8 +476,9 @@ wos_status wos_op_svd_batched(wos_context *ctx, int32_t n,
                               const wos_svd_problem *problems, int32_t *sweeps,
                               void *stream, void *const *jacobi_events);
 /* jacobi_events: NULL, or two cudaEvent_t recorded on the stream before the
- * first and after the last factorisation launch (the QR with pivoting and
- * the Jacobi sweeps; for profiling). */
+ * first and after the last factorisation launch (the QR, the FP32 sweeps
+ * and their Newton-Schulz products when they run, and the FP64 Jacobi
+ * sweeps; for profiling). */
 
 /* Which kernels factor an SVD problem (a setting of the context, read by
  * wos_op_svd, wos_op_svd_batched and the serving queue):

@@ -343,6 +343,30 @@ def test_fp32_preconditioned_sweeps_agree_with_fp64_sweeps(shape):
             assert np.abs(P0 - P1).max() <= 1e-9, r
 
 
+def test_svd_above_768_columns_runs_fp64_sweeps_alone():
+    """A worked matrix of more than 768 columns (more than the FP32 sweeps'
+    columns hold in a lane's registers) takes the FP64-only path by default:
+    the same sweep count as with WOS_SVD_FP64_SWEEPS, bit-identical results,
+    and singular values within 1e-12 of LAPACK's."""
+    M_D, M_tot, M_1 = 800, 1200, 780
+    N = 100_000
+    C = W.synthetic_counts(M_D, M_tot, N, seed=7)
+    g1 = np.zeros(M_tot, np.uint8)
+    g1[:M_1] = 1
+    Ct = torch.as_tensor(C.astype(np.int32), device=DEV)
+    sg = torch.full((M_tot,), 2 * np.pi / M_tot, dtype=torch.float64, device=DEV)
+    c = ctx()
+    U, S, V, sw = wos.wos_op_svd(c, Ct, N, g1, sg)
+    wos.wos_set_svd_path(c, wos.SVD_FP64_SWEEPS)
+    U0, S0, V0, sw0 = wos.wos_op_svd(c, Ct, N, g1, sg)
+    wos.wos_set_svd_path(c, wos.SVD_AUTO)
+    assert sw == sw0 and sw >= 5, (sw, sw0)
+    assert torch.equal(S, S0) and torch.equal(U, U0) and torch.equal(V, V0)
+    B = O.operator_B(C, N, g1, np.full(M_D, 1 / np.sqrt(M_D)), np.full(M_tot, 2 * np.pi / M_tot))
+    s_lapack = np.linalg.svd(B, compute_uv=False)
+    assert np.max(np.abs(S.cpu().numpy() / s_lapack - 1)) <= 1e-12
+
+
 def test_svd_path_setting_is_checked():
     for bad in (-1, 4, 100):
         with pytest.raises(wos.WosError) as e:
