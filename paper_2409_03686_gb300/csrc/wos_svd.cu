@@ -1028,9 +1028,12 @@ jacobi_kernel(const SvdWork *works, const int *begin, int np)
     jacobi_body<RPT>(w, int(blockIdx.x) - begin[p], begin[p + 1] - begin[p]);
 }
 
-// At most 48 registers a thread (ten 128-thread CTAs per SM).
-template <int RPL>
-__global__ void __launch_bounds__(kPairThreads, 10)
+// At most 48 registers a thread (ten 128-thread CTAs per SM), or 40 (twelve:
+// a CTA per pair for the four 1024 x 768 problems of a batch, which ten an
+// SM cannot hold -- a CTA with two pairs a round would set every round's
+// pace; the same arithmetic, some registers spilled).
+template <int RPL, int MINB = 10>
+__global__ void __launch_bounds__(kPairThreads, MINB)
 jacobi_lean_kernel(const SvdWork *works, const int *begin, int np)
 {
     const int p = problem_of(begin, np);
@@ -2229,8 +2232,15 @@ const void *jacobi_group_kernel_rpl(int rpl)
     }
 }
 
-const void *jacobi_lean_kernel_rpl(int rpl)
+const void *jacobi_lean_kernel_rpl(int rpl, bool dense = false)
 {
+    if (dense)
+        switch (rpl) {
+        case 8: return reinterpret_cast<const void *>(&jacobi_lean_kernel<8, 12>);
+        case 16: return reinterpret_cast<const void *>(&jacobi_lean_kernel<16, 12>);
+        case 24: return reinterpret_cast<const void *>(&jacobi_lean_kernel<24, 12>);
+        default: return reinterpret_cast<const void *>(&jacobi_lean_kernel<32, 12>);
+        }
     switch (rpl) {
     case 8: return reinterpret_cast<const void *>(&jacobi_lean_kernel<8>);
     case 16: return reinterpret_cast<const void *>(&jacobi_lean_kernel<16>);
@@ -2773,8 +2783,12 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
                 idx.push_back(p);
         if (idx.empty())
             continue;
+        long long cls_pairs = 0;
+        for (int p : idx)
+            cls_pairs += P[p].wj.n_pad / 2;
+        const bool dense = lean && !group && cls_pairs > 10LL * sms;
         const void *jk = group ? jacobi_group_kernel_rpl(rpt)
-                               : lean ? jacobi_lean_kernel_rpl(rpt) : jacobi_kernel_rpt(rpt);
+                               : lean ? jacobi_lean_kernel_rpl(rpt, dense) : jacobi_kernel_rpt(rpt);
         const int threads = group ? kGroupThreads : kPairThreads;
         int bps = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, jk, threads, 0);

@@ -198,7 +198,8 @@ def test_svd_is_deterministic(shape, svd_path):
             assert torch.equal(a, b), rep
 
 
-@pytest.mark.parametrize("large", [False, True, "fp64"], ids=["mixed", "without-V", "fp64-sweeps"])
+@pytest.mark.parametrize("large", [False, True, "fp64", "dense"],
+                         ids=["mixed", "without-V", "fp64-sweeps", "dense"])
 def test_batched_svd_equals_single_calls(svd_path, large):
     """wos_op_svd_batched: problems of different shapes and orientations
     (direct path n < 32 and preconditioned n >= 32), and a batch larger than
@@ -207,10 +208,13 @@ def test_batched_svd_equals_single_calls(svd_path, large):
     V): with the FP32 preconditioning (a CTA per pair alone and in the
     batch), and with FP64 sweeps alone in a batch large enough for four
     pairs per CTA against single calls with a CTA per pair (the two kernels'
-    canonical summation order)."""
+    canonical summation order); and four 1024 x 768 problems, whose FP64
+    sweeps take the twelve-CTAs-an-SM variant of the kernel."""
     if large == "fp64":
         wos.wos_set_svd_path(ctx(), wos.SVD_FP64_SWEEPS)
-    if large:
+    if large == "dense":
+        shapes = [(1024, 1536, 768)] * 4
+    elif large:
         shapes = [(600, 900, 300), (300, 900, 600), (520, 800, 400), (700, 1000, 350)]
     else:
         shapes = [(256, 256, 128), (96, 300, 200), (40, 60, 20), (64, 96, 48),
