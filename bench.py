@@ -639,8 +639,8 @@ def run_gpu(args, rank: int, world: int, dist):
     mixed = all(fp32_preconditioned(p["svd_mn"][1], args.svd_path) for p in prep)
     svd_achieved = flop / (jac_ms / 1e3) / 1e9
     svd_achieved_ov = flop / (jac_ms_ov / 1e3) / 1e9
-    sweeps64 = ("jacobi_group_kernel" if sum(p["svd_mn"][1] for p in prep) > 2 * 3 * 152
-                else "jacobi_lean_kernel")
+    sweeps64 = ("jacobi_group_kernel" if not mixed and
+                sum(p["svd_mn"][1] for p in prep) > 2 * 3 * 152 else "jacobi_lean_kernel")
     svd_roof = {"kernel": ("svd_cluster_kernel" if args.svd_path == "auto" and
                            all(p["svd_mn"][1] <= 256 for p in prep)
                            else ("qrs_kernel + pc32_sweeps_kernel + pc32_replay_kernel + "

@@ -1843,6 +1843,66 @@ __device__ void qrs_apply(const QrWork &q, int k, int pos, double tau, double *r
     __syncthreads();
 }
 
+// Columns at positions pos[0..cnt) (cnt <= 4) <- H_k (column), their dot
+// products with v reduced together: a transposed butterfly leaves column j's
+// warp sum in lanes 8j..8j+7 after 6 additions a lane (instead of 5 a
+// column), then one thread a column adds the warps' partials.
+__device__ void qrs_apply4(const QrWork &q, int k, const int *pos, int cnt, double tau,
+                           double *red)
+{
+    __shared__ double part[4][32];  // [column][warp]
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, m = q.m;
+    if (tau == 0.0)
+        return;
+    const double *v = q.A + size_t(q.perm[k]) * m;
+    double *c[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        c[j] = q.A + size_t(q.perm[pos[j < cnt ? j : 0]]) * m;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = k + 1 + tid; i < m; i += blockDim.x) {
+        const double vi = __ldcg(v + i);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j < cnt)
+                a[j] = fma(vi, c[j][i], a[j]);
+    }
+    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+    double k0 = hi16 ? a[2] : a[0], k1 = hi16 ? a[3] : a[1];
+    k0 += __shfl_xor_sync(FULL, hi16 ? a[0] : a[2], 16);
+    k1 += __shfl_xor_sync(FULL, hi16 ? a[1] : a[3], 16);
+    double t = hi8 ? k1 : k0;
+    t += __shfl_xor_sync(FULL, hi8 ? k0 : k1, 8);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1)
+        t += __shfl_xor_sync(FULL, t, o);
+    if ((lane & 7) == 0)
+        part[lane >> 3][wid] = t;  // lanes 0, 8, 16, 24: columns 0, 1, 2, 3
+    __syncthreads();
+    if (tid < cnt) {
+        double w = 0.0;
+        for (int g = 0; g < int(blockDim.x >> 5); ++g)
+            w += part[tid][g];
+        red[tid] = tau * (w + q.A[size_t(q.perm[pos[tid]]) * m + k]);  // tau w
+    }
+    __syncthreads();
+    double tw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        tw[j] = j < cnt ? red[j] : 0.0;
+    for (int i = k + 1 + tid; i < m; i += blockDim.x) {
+        const double vi = __ldcg(v + i);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j < cnt)
+                c[j][i] = fma(-tw[j], vi, c[j][i]);
+    }
+    __syncthreads();
+    if (tid < cnt)
+        q.A[size_t(q.perm[pos[tid]]) * m + k] -= red[tid];
+    __syncthreads();
+}
+
 __device__ void qrs_body(const QrWork &q, const int b, const int G)
 {
     __shared__ double red[36];
@@ -1866,8 +1926,12 @@ __device__ void qrs_body(const QrWork &q, const int b, const int G)
             qrs_reflect(q, k + 1, red);
             pos += G;
         }
-        for (; pos < n; pos += G)
-            qrs_apply(q, k, pos, tau, red);
+        while (pos < n) {  // the rest four columns at a time
+            int ps[4], cnt = 0;
+            for (; cnt < 4 && pos < n; pos += G)
+                ps[cnt++] = pos;
+            qrs_apply4(q, k, ps, cnt, tau, red);
+        }
     }
 }
 
@@ -2647,9 +2711,16 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         if (e == cudaSuccess && !srt.empty()) {
             int sbps = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sbps, qrs_kernel, kQrsThreads, 0);
-            e = launch_groups(reinterpret_cast<const void *>(qrs_kernel), kQrsThreads,
-                              std::max(1, sbps) * sms, srt, qgrids, qrecs, dq, dbegin, st,
-                              &launches);
+            const int sbudget = std::max(1, sbps) * sms;
+            std::vector<int> sgrids(qgrids);  // the problems' CTAs within this kernel's budget
+            long long want = 0;
+            for (int p : srt)
+                want += sgrids[p];
+            if (want > sbudget)
+                for (int p : srt)
+                    sgrids[p] = std::max(1, int(sgrids[p] * (long long)sbudget / want));
+            e = launch_groups(reinterpret_cast<const void *>(qrs_kernel), kQrsThreads, sbudget,
+                              srt, sgrids, qrecs, dq, dbegin, st, &launches);
         }
         if (e == cudaSuccess && !piv.empty())
             e = launch_groups(reinterpret_cast<const void *>(qrcp_kernel), kQrThreads, qbudget,
