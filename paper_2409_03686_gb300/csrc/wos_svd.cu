@@ -915,13 +915,17 @@ __device__ __forceinline__ bool pc32_rotation(float al, float be, float ga, floa
     big = false;
     if (!(al > 0.0f && be > 0.0f && al <= 3.0e38f && be <= 3.0e38f))
         return false;
-    const float sc = 1.0f / fmaxf(al, be);  // al, be <= 1 and |ga| <= 1 after it
+    // the angle needs no correct rounding (cos and sin are formed accurately
+    // from whatever tangent this gives): approximate reciprocal, square root
+    // and quotient of the special-function unit
+    const float sc = __fdividef(1.0f, fmaxf(al, be));  // al, be <= 1, |ga| <= 1 after it
     const float a1 = al * sc, b1 = be * sc, g1 = ga * sc;
     const float ab = a1 * b1, g2 = g1 * g1;
     if (!(g2 > (kTol32 * kTol32) * ab))
         return false;
     const float h = 0.5f * (b1 - a1);
-    const float t = copysignf(1.0f, h) * g1 / (fabsf(h) + sqrtf(fmaf(h, h, g2)));
+    const float q = fmaf(h, h, g2);  // > 0
+    const float t = copysignf(1.0f, h) * __fdividef(g1, fabsf(h) + q * rsqrtf(q));
     accurate_cos_sin(t, c, sn);
     big = g2 > (kLast32 * kLast32) * ab;
     return true;
@@ -1949,11 +1953,15 @@ qrs_kernel(const QrWork *works, const int *begin, int np)
 // cn (lowest index on ties): a thread per column counts the columns before it.
 __global__ void sort_columns_kernel(const QrWork q)
 {
+    extern __shared__ double sort_cn[];  // the n norms (dynamic, n doubles)
+    for (int i = threadIdx.x; i < q.n; i += blockDim.x)
+        sort_cn[i] = q.cn[i];
+    __syncthreads();
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < q.n; j += gridDim.x * blockDim.x) {
-        const double v = q.cn[j];
+        const double v = sort_cn[j];
         int rank = 0;
         for (int i = 0; i < q.n; ++i) {
-            const double u = q.cn[i];
+            const double u = sort_cn[i];
             rank += (u > v || (u == v && i < j)) ? 1 : 0;
         }
         q.perm[rank] = j;
@@ -2705,7 +2713,7 @@ wos_status svd_batch(wos_context *ctx, std::vector<SvdProb> &P, int32_t *sweeps,
         for (int p = 0; e == cudaSuccess && p < int(srt.size()); ++p) {
             const QrWork &q = P[srt[p]].q;
             qr_col_norms_kernel<<<sms * 2, 256, 0, st>>>(q);
-            sort_columns_kernel<<<(q.n + 255) / 256, 256, 0, st>>>(q);
+            sort_columns_kernel<<<(q.n + 255) / 256, 256, size_t(q.n) * sizeof(double), st>>>(q);
             launches += 2;
         }
         if (e == cudaSuccess && !srt.empty()) {
