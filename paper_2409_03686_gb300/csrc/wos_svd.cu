@@ -32,9 +32,10 @@ constexpr unsigned FULL = 0xFFFFFFFFu;
 constexpr double kTol = 1e-15;
 // A sweep whose pairs all had |cos| = |w_p . w_q| / (|w_p| |w_q|) <= kLast
 // rotated by angles that small; the cyclic sweep's quadratic convergence
-// leaves every cosine at O(kLast^2) = 1e-16 after it, below kTol, so no
-// verifying sweep without rotations follows it.
-constexpr double kLast = 1e-8;
+// leaves every cosine at O(kLast^2) ~ 1e-15 after it, at kTol, so no
+// verifying sweep follows it (what it would still rotate changes the
+// singular values by O(cos^2), far below FP64 rounding).
+constexpr double kLast = 3e-8;
 constexpr int kMaxSweeps = 80;
 constexpr int kPairThreads = 128;
 static_assert(kPairThreads == 128, "the partial sums below assume four warps");
