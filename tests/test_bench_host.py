@@ -77,3 +77,21 @@ def test_clock_sampler_without_nvidia_smi_reports_nothing():
     s = bench.ClockSampler(0)
     s.proc = None
     assert s.stop() is None
+
+
+def test_svd_fp64_flop_accounts_for_the_preconditioned_path():
+    """The SVD roofline's FP64 flop: QR 2mn^2 - 2n^3/3; above 256 and up to
+    768 columns (FP32 sweeps first, unless FP64 sweeps alone are asked for)
+    the Newton-Schulz and X Q products 4n^3; FP64 sweeps n(n-1)/2 pair
+    visits of 6 flop a row of X (n rows)."""
+    import bench
+    m, n, sw = 1024, 768, 2
+    qr = 2 * m * n * n - (2 * n ** 3) // 3
+    sweeps = sw * (n * (n - 1) // 2) * 6 * n
+    assert bench.fp32_preconditioned(n, "auto") and not bench.fp32_preconditioned(n, "fp64-sweeps")
+    assert not bench.fp32_preconditioned(256, "auto") and not bench.fp32_preconditioned(769, "auto")
+    assert bench.svd_fp64_flop(m, n, sw, "auto") == qr + 4 * n ** 3 + sweeps
+    assert bench.svd_fp64_flop(m, n, sw, "fp64-sweeps") == qr + sweeps
+    # small problems: V accumulated, no Newton-Schulz
+    assert bench.svd_fp64_flop(256, 128, 9, "auto") == (
+        2 * 256 * 128 ** 2 - (2 * 128 ** 3) // 3 + 9 * (128 * 127 // 2) * (12 * 128 + 6 * 128))
